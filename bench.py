@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Throughput benchmark: eigenpairs/s of polynomial preconditioned Arnoldi.
+
+A step is one full solve of the n = 1e6 workload (2-D convection-diffusion,
+N = 1000, beta = 100, 5-point, FP64): GMRES(50) polynomial build, then
+thick-restarted Arnoldi(50, 25) on pi(A) until the 20 smallest-real-part
+eigenpairs reach ||A x - lam x|| <= 1e-8 ||A||_1.  The metric is converged
+eigenpairs per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  ``value`` is timed with CUDA events on the
+library's stream with the matrix resident on the device; ``e2e`` times the
+same solve through the C-ABI from host buffers (matrix upload, start vectors,
+eigenvectors back to the host).  With N > 1 (torchrun) every rank solves its
+own seeded instance (weak scaling, no collective on the data path).
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload and extrapolates to a full solve.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1806_08020_gb300 import inputs  # noqa: E402
+
+METRIC = "eigenpairs/s at residual 1e-8 (FP64, n=1e6 2-D convection-diffusion)"
+UNIT = "eigenpairs/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+            self.f.close()
+
+    def summary(self) -> dict:
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for i, nm in enumerate(names):
+            if any("Active" in r[5 + i] for r in rows if len(r) > 5 + i):
+                reasons.append(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cu",):
+        h.update(open(os.path.join(ROOT, "paper_1806_08020_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def _profile_traffic(name: str) -> float | None:
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernels."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        kv = dict(line.split(":", 1) for line in open(path) if ":" in line)
+    except Exception:
+        return None
+    if kv.get("kernels_sha", "").strip() != _kernel_hash():
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def _step_bytes(n: int, nnz_padded: int, nslices: int, roots: np.ndarray, vbytes: int = 8) -> tuple[int, int]:
+    """Algorithmic bytes and launches of one pi(A) apply with SELL-32 (FP64 values, int32 columns).
+
+    Per launch: values + column indices + slice pointers, the input vector x
+    read once and the output written once (8n each); the second pass of a
+    conjugate pair also reads p (aux).
+    """
+    mat = nnz_padded * (vbytes + 4) + 4 * (nslices + 1)
+    tot, launches = 0, 0
+    i = 0
+    while i < roots.size:
+        if roots[i].imag == 0:
+            tot += mat + 2 * n * vbytes
+            launches += 1
+            i += 1
+        else:
+            tot += (mat + 2 * n * vbytes) + (mat + 3 * n * vbytes)
+            launches += 2
+            i += 2
+    return tot, launches
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1806_08020_gb300 import pp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = inputs.plain_large()
+    A = cfg["A"]
+    n, nnz = A.n, A.nnz
+    seed = cfg["seed"] + 7919 * rank  # each rank its own instance
+    b = inputs.start_vector(n, seed, 0)
+    v0 = inputs.start_vector(n, seed, 1)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = pp.pp_create(A, stream=stream.cuda_stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def one_solve():
+        poly = pp.pp_build_poly(ctx, cfg["d"], b)
+        res = pp.pp_eigs(ctx, poly, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=False)
+        return poly, res
+
+    for _ in range(args.warmup):
+        one_solve()
+    barrier()
+    launches0 = pp.pp_launch_count(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pairs, t_apply, apply_mvps, cycles, maxres = 0, 0.0, 0, [], 0.0
+    poly = None
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            poly, res = one_solve()
+            st = res.stats
+            pairs += int(np.sum(res.resid <= cfg["rtol"])) if res.status == 0 else 0
+            t_apply += st["t_apply"]
+            cycles.append(st["cycles"])
+            maxres = max(maxres, float(np.max(res.resid)))
+        ev1.record(stream)
+        barrier()
+    launches = pp.pp_launch_count(ctx) - launches0
+    t = ev0.elapsed_time(ev1) * 1e-3
+    if ws > 1:
+        tt = torch.tensor([t, pairs], dtype=torch.float64, device=dev)
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t, pairs = float(tmax[0]), int(tt[1])
+    value = pairs / t
+
+    # end to end through the C-ABI from host buffers: upload, solve, vectors back
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    h2d = A.rowptr.nbytes + A.colind.nbytes + A.vals.nbytes + b.nbytes + v0.nbytes
+    te0 = time.perf_counter()
+    e2e_pairs, d2h = 0, 0
+    for _ in range(e2e_steps):
+        c2 = pp.pp_create(A, stream=stream.cuda_stream)
+        p2 = pp.pp_build_poly(c2, cfg["d"], b)
+        r2 = pp.pp_eigs(c2, p2, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=True)
+        d2h = r2.X.nbytes + r2.lam.nbytes * 2 + r2.resid.nbytes
+        e2e_pairs += int(np.sum(r2.resid <= cfg["rtol"])) if r2.status == 0 else 0
+        p2.close()
+        c2.close()
+    barrier()
+    te = time.perf_counter() - te0
+    if ws > 1:
+        tt = torch.tensor([te, e2e_pairs], dtype=torch.float64, device=dev)
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        te, e2e_pairs = float(tmax[0]), int(tt[1])
+
+    # roofline of the dominant kernel (fused SELL root step), event-timed over the region
+    roots = pp.pp_poly_roots(poly)
+    nslices = (n + 31) // 32
+    row_len = np.diff(A.rowptr)
+    nnz_padded = int(np.sum(np.maximum.reduceat(row_len, np.arange(0, n, 32))) * 32)
+    bytes_apply, launches_apply = _step_bytes(n, nnz_padded, nslices, roots)
+    applies_total = sum(c for c in [0])  # placeholder replaced below
+    # number of applies per solve: m + (cycles - 1) (m - k); t_apply covers all of them
+    applies_total = sum(cfg["m"] + (c - 1) * (cfg["m"] - cfg["k"]) for c in cycles)
+    achieved_gbs = bytes_apply * applies_total / t_apply / 1e9
+    flops_apply = sum((2 * nnz + 2 * n) * (2 if z.imag != 0 else 1) for z in roots if z.imag >= 0)
+    achieved_tflops = flops_apply * applies_total / t_apply / 1e12
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    fp64_peak = 1250.0  # GB300 nominal FP64 (non-tensor) GFLOP/s
+    traffic = _profile_traffic("sell_root_step_fp64_n1e6.txt")
+    roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm, 4) if hbm else None,
+                "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6800",
+                "kernel": "k_sell_step<double> (fused root step)",
+                "bytes_per_launch": round(bytes_apply / launches_apply),
+                "launches_timed": applies_total * launches_apply,
+                "avg_launch_us": round(t_apply / (applies_total * launches_apply) * 1e6, 3),
+                "fp64_achieved_tflops": round(achieved_tflops, 4),
+                "fp64_frac_of_nominal": round(achieved_tflops * 1e3 / fp64_peak, 4)}
+    if not hbm:
+        roofline["peak"] = 6800.0
+        roofline["frac"] = round(achieved_gbs / 6800.0, 4)
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+        "config": {"workload": cfg["name"], "n": n, "nnz": nnz, "d": cfg["d"], "m": cfg["m"], "k": cfg["k"],
+                   "nev": cfg["nev"], "rtol": cfg["rtol"], "format": "SELL-32", "parallelism": f"replicas x{ws}",
+                   "l2": "working set (basis 51 x 8 MB + matrix 60 MB) exceeds the 129 MB L2",
+                   "cycles_per_solve": cycles, "max_resid": maxres},
+        "e2e": {"value": round(e2e_pairs / te, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, seed, budget_s=args.cpu_budget, cycles=statistics.median(cycles))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def cpu_baseline(cfg, seed, budget_s=20.0, cycles=None):
+    """The oracle as it stands on the host cores, on a bounded sample of the workload.
+
+    Sample: the oracle's GMRES(d) build plus the first S Arnoldi steps on pi(A)
+    (S chosen to fit the budget), timed; extrapolated to a full solve of
+    m + (cycles - 1)(m - k) steps.  The cycle count is the oracle's own from
+    tests/golden/plain_large_oracle.txt (written by a script that runs only the
+    oracle) when present, else the GPU run's.
+    """
+    import oracle as O
+    from oracle.ppa import make_operator
+
+    A = O.to_scipy(cfg["A"])
+    n = A.shape[0]
+    c = O.Counters()
+    sigma = O.gershgorin_shift(A)
+    op = O.Operator(A, sigma, c)
+    b = inputs.start_vector(n, seed, 0)
+    v0 = inputs.start_vector(n, seed, 1)
+    t0 = time.perf_counter()
+    P = O.build_poly(op, b, cfg["d"], c)
+    t_build = time.perf_counter() - t0
+    opp = make_operator(op, P, c)
+    V = np.zeros((n, cfg["m"] + 1))
+    V[:, 0] = v0 / np.linalg.norm(v0)
+    steps = 0
+    t1 = time.perf_counter()
+    while steps < cfg["m"] and time.perf_counter() - t0 < budget_s:
+        w, _ = O.cgs2(V[:, : steps + 1], opp(V[:, steps]), c)
+        V[:, steps + 1] = w / np.linalg.norm(w)
+        steps += 1
+    t_step = (time.perf_counter() - t1) / max(steps, 1)
+    src = "gpu run"
+    try:
+        g = dict(line.split(None, 1) for line in open(os.path.join(ROOT, "tests", "golden", "plain_large_oracle.txt"))
+                 if line.strip() and not line.startswith("#"))
+        cycles = int(g["cycles"])
+        src = "oracle golden file"
+    except Exception:
+        pass
+    cycles = int(cycles or 1)
+    total_steps = cfg["m"] + (cycles - 1) * (cfg["m"] - cfg["k"])
+    t_solve = t_build + total_steps * t_step
+    return {"value": round(cfg["nev"] / t_solve, 5), "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle",
+            "sample": f"GMRES({cfg['d']}) build + {steps} of {total_steps} Arnoldi steps "
+                      f"({time.perf_counter() - t0:.1f} s); extrapolated with {cycles} cycles ({src}); "
+                      "scipy SpMV single-threaded, BLAS on all cores",
+            "seconds_per_solve_est": round(t_solve, 1)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    cfg = inputs.plain_large()
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(cfg, cfg["seed"], budget_s=args.cpu_budget)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            last = r
+    v = statistics.median(vals)
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(cfg["nev"] / v * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)", "impl": "reference",
+            "config": {"workload": cfg["name"], "n": cfg["A"].n, "nnz": cfg["A"].nnz},
+            "cpu_baseline": {**last, "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

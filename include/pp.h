@@ -1,0 +1,235 @@
+/*
+ * pp.h — C-ABI of the GB300 polynomial preconditioned Arnoldi library.
+ *
+ * Method: Embree, Loe & Morgan, "Polynomial Preconditioned Arnoldi".
+ * The library finds a few eigenvalues of a large sparse real matrix A nearest
+ * a target by running thick-restarted Arnoldi(m,k) on pi(A), where pi is the
+ * GMRES (minimum residual) polynomial of degree d (Section 2 box), applied in
+ * factored form pi(A) = prod_i (I - A/theta_i) with the roots theta_i in
+ * modified Leja order (Eq. (2.1)).
+ *
+ * Conventions for every entry point
+ *  - Plain C types only.  "_dev" pointers are CUDA device pointers; every other
+ *    pointer is host memory.  Matrices are CSR (row pointers int64, column
+ *    indices int32, values double), column indices within a row in any order.
+ *  - Ownership: the library copies every input it keeps; caller buffers stay
+ *    caller-owned and may be freed after the call returns.  Output arrays are
+ *    caller-allocated with the sizes stated.  Handles returned through an out
+ *    pointer are owned by the caller and released with the matching destroy.
+ *  - Errors: a negative pp_status means nothing valid was written to outputs
+ *    (the handle stays usable unless the status is PP_ECUDA); a positive status
+ *    is a usable result with a warning.  pp_last_error() returns a message for
+ *    the most recent failure on the calling thread.
+ *  - Threads: a context and its polynomials are used by one host thread at a
+ *    time.  All GPU work of a context runs on its stream, in order.
+ *  - Vectors on the device (pp_apply) use the context's storage precision:
+ *    double for PP_FP64, float for PP_FP32 and PP_FP32_BF16.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pp_ctx pp_ctx;
+typedef struct pp_poly pp_poly;
+
+typedef enum {
+    PP_OK = 0,
+    PP_ENOTCONV = 1,    /* not converged in max_cycles; best pairs and residuals written */
+    PP_EBREAKDOWN = 2,  /* GMRES ended early (invariant subspace); degree reduced, poly usable */
+    PP_EINVAL = -1,     /* bad argument */
+    PP_ENOMEM = -2,     /* device or host allocation failed */
+    PP_ECUDA = -3,      /* CUDA runtime error; the context must be destroyed */
+    PP_ETIMEOUT = -4,   /* a bounded device wait gave up */
+    PP_ENUMERIC = -5    /* NaN/Inf or a singular small dense problem */
+} pp_status;
+
+/* Storage / arithmetic precision of the hot path. */
+enum { PP_FP64 = 0, PP_FP32 = 1, PP_FP32_BF16 = 2 };
+/* Sparse format on the device: auto (chosen by the tuner), CSR, SELL-C-sigma. */
+enum { PP_FMT_AUTO = 0, PP_FMT_CSR = 1, PP_FMT_SELL = 2 };
+/* Which eigenvalues: smallest magnitude (Section 2) or smallest real part
+ * (run on A - sigma I with sigma the leftmost Gershgorin point, Section 2 footnote 1). */
+enum { PP_TARGET_SM = 0, PP_TARGET_SR = 1 };
+
+typedef struct {
+    int precision;      /* PP_FP64 (default), PP_FP32, PP_FP32_BF16 */
+    int format;         /* PP_FMT_AUTO (default) */
+    int target;         /* PP_TARGET_SR (default) or PP_TARGET_SM */
+    double sigma;       /* shift; NaN (default) = automatic from the target */
+    int add_roots;      /* 1 (default): Section 7 box, extra copies of roots with large pof */
+    int max_cycles;     /* Arnoldi cycles before PP_ENOTCONV; default 2000 */
+    int refine_steps;   /* FP64 refinement steps for the mixed-precision path; default 4 */
+    int sell_c;         /* SELL chunk height; 0 = tuner (32) */
+    int sell_sigma;     /* SELL sorting window; 0 or 1 = no sorting */
+    void *stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
+} pp_opts;
+
+/* Counters of Section 4 (mvps, dot products, vector operations) plus timings. */
+typedef struct {
+    int64_t cycles;       /* Arnoldi cycles run */
+    int64_t mvps;         /* products with A (polynomial build, applies, residual checks) */
+    int64_t dots;         /* length-n inner products */
+    int64_t vops;         /* length-n vector operations (dots, axpys, scalings) */
+    int64_t kernel_launches; /* library kernels launched by the call */
+    int32_t converged;    /* 1 when every wanted pair met the tolerance */
+    int32_t nconv;        /* number of wanted slots that met the tolerance */
+    double t_total;       /* seconds, wall clock of the call */
+    double t_apply;       /* seconds spent in pi(A) applies (device, event-timed) */
+    double t_orth;        /* seconds spent in CGS2 (device, event-timed) */
+    double t_restart;     /* seconds in restart + convergence test, host and device */
+    double max_resid;     /* largest ||A x - lambda x|| / ||A||_1 among returned slots */
+} pp_stats;
+
+/* Fill *o with the defaults listed above. */
+void pp_opts_default(pp_opts *o);
+
+/* Message for the last failure on this thread ("" if none).  Static storage. */
+const char *pp_last_error(void);
+
+/*
+ * pp_create — upload the sparse matrix A (n x n, CSR, host arrays) and prepare
+ * the device formats (Section 2: the method needs only products with A).
+ * rowptr: n+1 int64; colind: nnz int32 in [0, n); vals: nnz doubles.
+ * opts may be NULL (defaults).  On success *out receives a context.
+ * Errors: PP_EINVAL (n <= 0, bad indices), PP_ENOMEM, PP_ECUDA.
+ */
+pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                    const double *vals, const pp_opts *opts);
+void pp_destroy(pp_ctx *ctx);
+
+/* Number of library kernels launched on this context since pp_create. */
+int64_t pp_launch_count(const pp_ctx *ctx);
+
+/* ||A||_1 (maximum absolute column sum) and the shift sigma used for the target. */
+pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);
+
+/*
+ * pp_build_poly — GMRES polynomial of degree d (Section 2 box, step 1):
+ * one GMRES(d) cycle on A - sigma I from b (host, n doubles), harmonic Ritz
+ * values as roots (step 1(b)), modified Leja order (step 1(c)), then extra
+ * copies of roots with large pof when opts.add_roots (Section 7 box).
+ * The Arnoldi process runs on the GPU (SpMV + CGS2); the d x d dense steps run
+ * on the host in FP64.  Returns PP_EBREAKDOWN (poly usable, lower degree) when
+ * GMRES found an invariant subspace before step d.
+ */
+pp_status pp_build_poly(pp_ctx *ctx, int d, const double *b, pp_poly **out);
+
+/*
+ * pp_build_poly2 — double polynomial (Section 8): pi_1 of degree d1 from b,
+ * tau(z) = 1 - pi_1(z) applied as the running sum of pi_1's factors, pi_2 of
+ * degree d2 = GMRES polynomial of tau(A) from the same b.  Arnoldi then runs
+ * on pi_2(tau(A)), of composite degree d1*d2 (plus added roots).
+ */
+pp_status pp_build_poly2(pp_ctx *ctx, int d1, int d2, const double *b, pp_poly **out);
+
+/*
+ * pp_poly_from_roots — polynomial with the given roots, applied in the given
+ * order (no reordering, no added roots).  Conjugate pairs must be adjacent,
+ * the member with im > 0 first and exactly conjugate.  count >= 1.
+ */
+pp_status pp_poly_from_roots(pp_ctx *ctx, int count, const double *re, const double *im,
+                             pp_poly **out);
+
+/*
+ * pp_poly_roots — roots in application order (including added roots).
+ * re/im: capacity cap each; *count receives the number of roots (if > cap only
+ * cap are written).  For a double polynomial these are pi_2's roots;
+ * pp_poly_inner_roots gives pi_1's.
+ */
+pp_status pp_poly_roots(const pp_poly *p, double *re, double *im, int cap, int *count);
+pp_status pp_poly_inner_roots(const pp_poly *p, double *re, double *im, int cap, int *count);
+/* Degree reached by GMRES (before added roots) and the number of added roots. */
+pp_status pp_poly_info(const pp_poly *p, int *degree, int *added);
+/* Work of the GMRES build(s) that made p, counted as in Section 4 (both
+ * builds for a double polynomial; zero for pp_poly_from_roots). */
+pp_status pp_poly_counts(const pp_poly *p, int64_t *mvps, int64_t *dots, int64_t *vops);
+void pp_poly_destroy(pp_poly *p);
+
+/*
+ * pp_apply — y = pi(A - sigma I) x (Eq. (2.1)); for a double polynomial
+ * y = pi_2(tau(A - sigma I)) x (Section 8).  x_dev, y_dev: n elements of the
+ * context's storage type on the device; they may be the same buffer.
+ * Real roots take one fused SpMV pass each; a conjugate pair takes two passes
+ * in real arithmetic.  Asynchronous on the context's stream.
+ */
+pp_status pp_apply(const pp_poly *p, const void *x_dev, void *y_dev);
+
+/*
+ * pp_apply_host — as pp_apply with host x and y (n doubles each): copies in,
+ * applies, copies out, synchronises.
+ */
+pp_status pp_apply_host(const pp_poly *p, const double *x, double *y);
+
+/*
+ * pp_eigs — thick-restarted Arnoldi(m, k) on pi(A) (Section 2 box step 2;
+ * Section 4): nev eigenvalues of A nearest the target, m the largest subspace
+ * dimension, k Ritz vectors kept (k - 1 when a conjugate pair would split),
+ * one reorthogonalisation pass per step, convergence tested at the end of each
+ * cycle on A itself: ||A y_j - mu_j y_j|| <= rtol * ||A||_1 with mu_j the
+ * Rayleigh quotient of the unit Ritz vector y_j.
+ * p == NULL runs plain Arnoldi(m, k) on A - sigma I.
+ * v0: host start vector (n doubles), NULL = e_1 + ... (deterministic ones).
+ * Outputs (capacity nev + 1 slots; a conjugate pair takes two slots and the
+ * wanted set grows by one when nev would split a pair):
+ *   lam_re, lam_im: eigenvalue estimates, sorted by the target;
+ *   X: n x (nev+1) column-major (NULL to skip): a real eigenvector, or for a
+ *      pair (lam, conj(lam)) the columns (Re x, Im x) of the unit vector x;
+ *   resid: ||A x - lam x|| / ||A||_1 per slot;  *nout: slots written.
+ * Requires 1 <= nev < k < m, m < n.  Returns PP_ENOTCONV with the best pairs
+ * when max_cycles is reached.
+ */
+pp_status pp_eigs(pp_ctx *ctx, const pp_poly *p, int nev, int m, int k, double rtol,
+                  const double *v0, double *lam_re, double *lam_im, double *X, double *resid,
+                  int *nout, pp_stats *stats);
+
+/* ----- Host FP64 dense steps (no GPU needed; used by the calls above) ----- */
+
+/*
+ * pp_dense_eig — eigenvalues and right eigenvectors of a real n x n matrix
+ * (column-major, leading dimension lda), by Householder reduction to
+ * Hessenberg form and Francis double-shift QR.  wr/wi: n each; a conjugate
+ * pair is adjacent with wi > 0 first and exactly conjugate.  V (n x n, ldv,
+ * may be NULL): column j holds the real eigenvector, or for a pair (j, j+1)
+ * the real and imaginary parts of the unit eigenvector of wr[j] + i wi[j].
+ * Returns PP_ENUMERIC when QR does not converge.
+ */
+pp_status pp_dense_eig(int n, const double *A, int lda, double *wr, double *wi, double *V, int ldv);
+
+/*
+ * pp_harmonic_ritz — roots of the GMRES polynomial from H_{d+1,d}
+ * ((d+1) x d, column-major, ldh >= d+1): eigenvalues of H_d + h_{d+1,d}^2 f e_d^T
+ * with H_d^T f = e_d (Section 2 box, step 1(b)).  re/im: d each, pairs adjacent.
+ */
+pp_status pp_harmonic_ritz(int d, const double *H, int ldh, double *re, double *im);
+
+/*
+ * pp_leja_order — modified Leja order (Section 2 box, step 1(c); Bai, Hu &
+ * Reichel alg. 3.1) with logarithmic products: first the root of largest
+ * modulus, then repeatedly the root maximising the product of distances to the
+ * roots chosen so far; a complex choice (im > 0 member) is followed by its
+ * conjugate.  Ties: first in the order (-re, -im, input position).
+ */
+pp_status pp_leja_order(int count, const double *re, const double *im, double *out_re,
+                        double *out_im);
+
+/*
+ * pp_add_stability_roots — Section 7 box: for each root (a conjugate pair is
+ * one unit, Leja order) with pof = prod_{i != j} |1 - theta_j/theta_i|, add
+ * ceil((log10 pof - 4)/14) copies (none when pof <= 1e4): the first at the end
+ * of the list, the others at unit positions p + floor(t (L - p)/c), t = 1..c-1,
+ * between the root's position p and the end (L units, c copies).
+ * out_re/out_im: capacity cap; *out_count receives the new length.
+ */
+pp_status pp_add_stability_roots(int count, const double *re, const double *im, int cap,
+                                 double *out_re, double *out_im, int *out_count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H */

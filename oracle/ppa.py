@@ -426,7 +426,8 @@ def _target_sort(lam: np.ndarray, target: str) -> np.ndarray:
 
 def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: int, k: int,
          rtol: float, v0: np.ndarray, c: Counters, target_point: float = 1.0,
-         target: str = "SM", max_cycles: int = 2000, sigma: float = 0.0) -> EigResult:
+         target: str = "SM", max_cycles: int = 2000, sigma: float = 0.0,
+         log: Callable[[int, float], None] | None = None) -> EigResult:
     """Thick-restarted Arnoldi(m, k) on ``op`` (Section 2 box step 2; Section 4).
 
     * Build V_{m+1}, H_{m+1,m} with CGS2 (one reorthogonalisation pass).
@@ -442,6 +443,8 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
       restart), V_k = V_m Q_k, v_{k+1} = v_{m+1},
       H_k = [Q_k^T H_m Q_k ; h_{m+1,m} e_m^T Q_k].
     ``sigma`` is the shift of ``op``'s matrix; Rayleigh quotients use A itself.
+    ``log`` (optional) is called as log(cycle, max relative residual) after
+    each convergence test; it does not affect the arithmetic.
     """
     n = v0.size
     nA = norm1(A)
@@ -491,6 +494,8 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
                 X[:, slot], X[:, slot + 1] = y.real, y.imag
                 slot += 2
         hist.append(float(res.max()))
+        if log is not None:
+            log(cycle, float(res.max()))
         if np.all(res <= rtol):
             srt = _target_sort(lam, target)
             return EigResult(lam[srt], X[:, srt], res[srt], True, cycle, c, nu[want][srt], hist)

@@ -1,0 +1,76 @@
+"""Build the CUDA/C++ library in-tree (sm_103a only).
+
+Compiles csrc/*.cu with nvcc and csrc/*.cpp with g++ in parallel, then links
+``libpp.so`` next to this file.  No cmake; a minute or less on either machine.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "csrc")
+OUT = os.path.join(ROOT, "_build")
+LIB = os.path.join(HERE, "libpp.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def sources():
+    cu = sorted(f for f in os.listdir(SRC) if f.endswith(".cu"))
+    cpp = sorted(f for f in os.listdir(SRC) if f.endswith(".cpp"))
+    return cu, cpp
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    os.makedirs(OUT, exist_ok=True)
+    nvcc = _nvcc()
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", SRC]
+    cu, cpp = sources()
+    deps = [os.path.join(SRC, f) for f in cu + cpp + ["pp_internal.h"]] + [os.path.join(ROOT, "include", "pp.h")]
+    newest = max(os.path.getmtime(p) for p in deps)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+        return LIB
+    procs, objs = [], []
+    for f in cu:
+        obj = os.path.join(OUT, f + ".o")
+        cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *inc, "-c",
+               os.path.join(SRC, f), "-o", obj]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        objs.append(obj)
+    for f in cpp:
+        obj = os.path.join(OUT, f + ".o")
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-I", "/usr/local/cuda/include", "-c",
+               os.path.join(SRC, f), "-o", obj]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        objs.append(obj)
+    failed = []
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        text = out.decode(errors="replace")
+        if p.returncode != 0:
+            failed.append(" ".join(cmd) + "\n" + text)
+        elif verbose and text.strip():
+            print(text)
+    if failed:
+        raise RuntimeError("build failed:\n" + "\n".join(failed))
+    tmp = LIB + ".tmp"
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose=True, force="--force" in sys.argv))

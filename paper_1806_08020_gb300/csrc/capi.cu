@@ -1,0 +1,1206 @@
+// C-ABI entry points: contexts, polynomial construction (Section 2 box,
+// Section 7 box, Section 8), the factored apply (Eq. (2.1)) and
+// thick-restarted Arnoldi(m, k) on pi(A) (Section 2 box step 2, Section 4).
+//
+// The Arnoldi process runs entirely on the device: each step applies the
+// operator with fused root-step kernels, orthogonalises with three CGS2
+// passes that write the Hessenberg column on the device, and normalises.
+// The host synchronises once per polynomial build and once per cycle, where
+// the small dense FP64 steps run (harmonic Ritz roots, Leja order, Ritz
+// values, restart basis).
+#include "pp_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using ppd::cd;
+
+static thread_local std::string g_last_error;
+
+pp_status pp_fail(pp_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return pp_fail(e_ == cudaErrorMemoryAllocation ? PP_ENOMEM : PP_ECUDA, "%s: %s (%s:%d)", \
+                           #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+    } while (0)
+
+#define CKS(expr)                          \
+    do {                                   \
+        pp_status s_ = (expr);             \
+        if (s_ < 0) return s_;             \
+    } while (0)
+
+namespace {
+
+struct StepCoef {
+    int pair;      // 0: real root, 1: conjugate pair
+    double c;      // real: 1/theta
+    double c1, c2; // pair: 2 Re(theta)/|theta|^2, 1/|theta|^2
+};
+
+std::vector<StepCoef> steps_of(const std::vector<cd> &roots) {
+    std::vector<StepCoef> s;
+    for (size_t i = 0; i < roots.size();) {
+        cd t = roots[i];
+        if (t.imag() == 0.0) {
+            s.push_back({0, 1.0 / t.real(), 0, 0});
+            i += 1;
+        } else {
+            double m2 = t.real() * t.real() + t.imag() * t.imag();
+            s.push_back({1, 0, 2.0 * t.real() / m2, 1.0 / m2});
+            i += 2;
+        }
+    }
+    return s;
+}
+
+int mvps_of(const std::vector<StepCoef> &s) {
+    int m = 0;
+    for (auto &x : s) m += x.pair ? 2 : 1;
+    return m;
+}
+
+double now() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct pp_ctx {
+    int64_t n = 0, nnz = 0;
+    pp_opts opts{};
+    double norm1 = 0, sigma = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    ppk::Matrix A;     // storage precision (shifted operator uses sigma)
+    ppk::Matrix A64;   // FP64 copy for residuals on A (same as A in FP64 mode)
+    size_t esz = 8;    // bytes per stored vector element
+    std::vector<void *> allocs;
+    // scratch
+    void *vec[8] = {};
+    double *d_part = nullptr;
+    size_t part_cap = 0;
+    unsigned *d_ticket = nullptr;
+    double *d_small = nullptr;  // h1, h2, scal, misc (4 * 256 doubles)
+    int64_t launches = 0;
+    int64_t ldv() const { return (n + 31) / 32 * 32; }
+};
+
+struct pp_poly {
+    pp_ctx *ctx = nullptr;
+    std::vector<cd> roots;
+    std::vector<StepCoef> steps;
+    int degree = 0, added = 0;
+    bool breakdown = false;
+    pp_poly *inner = nullptr;  // pi_1 for a double polynomial (tau = 1 - pi_1)
+    int64_t mvps = 0, dots = 0, vops = 0;  // work of the GMRES build(s)
+    ~pp_poly() { delete inner; }
+};
+
+namespace {
+
+pp_status dmalloc(pp_ctx *c, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return pp_fail(PP_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    return PP_OK;
+}
+
+pp_status check_launch(pp_ctx *c) {
+    c->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pp_fail(PP_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return PP_OK;
+}
+
+// One pass: y/r/oy per StepArgs on matrix A.
+pp_status step(pp_ctx *c, const ppk::StepArgs &s) {
+    ppk::launch_step(c->A, s, c->stream);
+    return check_launch(c);
+}
+
+// y = pi(A - sigma I) x with the steps in order; scratch: vec[0], vec[1], vec[2].
+pp_status apply_single(pp_ctx *c, const std::vector<StepCoef> &st, const void *x, void *y) {
+    const void *cur = x;
+    void *P0 = c->vec[0], *P1 = c->vec[1], *T = c->vec[2];
+    for (size_t i = 0; i < st.size(); ++i) {
+        bool last = (i + 1 == st.size());
+        void *dst = (cur == P0) ? P1 : P0;
+        if (last && y != cur) dst = y;
+        ppk::StepArgs a;
+        a.sigma = c->sigma;
+        if (!st[i].pair) {
+            a.x = cur;
+            a.y = dst;
+            a.a2 = st[i].c;
+        } else {
+            ppk::StepArgs t;
+            t.sigma = c->sigma;
+            t.x = cur;
+            t.y = T;
+            t.plain = 1;
+            CKS(step(c, t));
+            a.x = T;
+            a.aux = cur;
+            a.y = dst;
+            a.a1 = st[i].c1;
+            a.a2 = -st[i].c2;
+        }
+        CKS(step(c, a));
+        cur = dst;
+    }
+    if (cur != y) CK(cudaMemcpyAsync(y, cur, c->n * c->esz, cudaMemcpyDeviceToDevice, c->stream));
+    return PP_OK;
+}
+
+// r = tau(A) u = u - pi_1(A) u as the running sum of pi_1's factors; the optional
+// outer epilogue writes oy = obase - (b1 ox + b2 r) in the last pass.
+// Scratch: vec[3], vec[4], vec[5].
+pp_status apply_tau(pp_ctx *c, const std::vector<StepCoef> &st, const void *u, void *r, bool r_write,
+                    const void *obase, const void *ox, void *oy, double b1, double b2) {
+    const void *cur = u;
+    void *P0 = c->vec[3], *P1 = c->vec[4], *T = c->vec[5];
+    for (size_t i = 0; i < st.size(); ++i) {
+        bool last = (i + 1 == st.size());
+        void *dst = (cur == P0) ? P1 : P0;
+        ppk::StepArgs a;
+        a.sigma = c->sigma;
+        a.r = r;
+        a.r_init = (i == 0);
+        a.r_write = (!last || r_write) ? 1 : 0;
+        a.y = last ? nullptr : dst;
+        if (last && oy) {
+            a.obase = obase;
+            a.ox = ox;
+            a.oy = oy;
+            a.b1 = b1;
+            a.b2 = b2;
+        }
+        if (!st[i].pair) {
+            a.x = cur;
+            a.a2 = st[i].c;
+        } else {
+            ppk::StepArgs t;
+            t.sigma = c->sigma;
+            t.x = cur;
+            t.y = T;
+            t.plain = 1;
+            CKS(step(c, t));
+            a.x = T;
+            a.aux = cur;
+            a.a1 = st[i].c1;
+            a.a2 = -st[i].c2;
+        }
+        CKS(step(c, a));
+        cur = dst;
+    }
+    return PP_OK;
+}
+
+// y = pi_2(tau(A)) x.  Outer scratch: vec[6], vec[7], vec[2] (t) and vec[1] (r).
+pp_status apply_double(pp_ctx *c, const pp_poly *p, const void *x, void *y) {
+    const auto &outer = p->steps;
+    const auto &inner = p->inner->steps;
+    const void *cur = x;
+    void *O0 = c->vec[6], *O1 = c->vec[7], *OT = c->vec[2], *R = c->vec[1];
+    for (size_t i = 0; i < outer.size(); ++i) {
+        bool last = (i + 1 == outer.size());
+        void *dst = (cur == O0) ? O1 : O0;
+        if (last && y != cur) dst = y;
+        if (!outer[i].pair) {
+            // dst = cur - tau(cur)/eta, fused into the last inner pass
+            CKS(apply_tau(c, inner, cur, R, false, cur, nullptr, dst, 0.0, outer[i].c));
+        } else {
+            // t = tau(cur); dst = cur - c1 t + c2 tau(t)
+            CKS(apply_tau(c, inner, cur, OT, true, nullptr, nullptr, nullptr, 0, 0));
+            CKS(apply_tau(c, inner, OT, R, false, cur, OT, dst, outer[i].c1, -outer[i].c2));
+        }
+        cur = dst;
+    }
+    if (cur != y) CK(cudaMemcpyAsync(y, cur, c->n * c->esz, cudaMemcpyDeviceToDevice, c->stream));
+    return PP_OK;
+}
+
+// y = Op(x): plain A - sigma I when p == nullptr, pi(A), or pi_2(tau(A)).
+pp_status op_apply(pp_ctx *c, const pp_poly *p, const void *x, void *y) {
+    if (!p) {
+        ppk::StepArgs a;
+        a.sigma = c->sigma;
+        a.x = x;
+        a.y = y;
+        a.plain = 1;
+        return step(c, a);
+    }
+    if (p->inner) return apply_double(c, p, x, y);
+    return apply_single(c, p->steps, x, y);
+}
+
+// tau(A) x into y (operator of the second GMRES in a double polynomial)
+pp_status op_tau(pp_ctx *c, const pp_poly *inner, const void *x, void *y) {
+    return apply_tau(c, inner->steps, x, y, true, nullptr, nullptr, nullptr, 0, 0);
+}
+
+int64_t op_mvps(const pp_poly *p) {
+    if (!p) return 1;
+    if (p->inner) {
+        int64_t in = mvps_of(p->inner->steps);
+        return in * mvps_of(p->steps);
+    }
+    return mvps_of(p->steps);
+}
+
+// vector operations per apply, counted as the oracle does: a real factor is
+// two length-n updates (polynomial and running sum), a pair four
+int64_t vops_of(const std::vector<StepCoef> &s) {
+    int64_t v = 0;
+    for (auto &x : s) v += x.pair ? 4 : 2;
+    return v;
+}
+
+int64_t op_vops(const pp_poly *p) {
+    if (!p) return 0;
+    if (p->inner) return vops_of(p->steps) + (int64_t)mvps_of(p->steps) * vops_of(p->inner->steps);
+    return vops_of(p->steps);
+}
+
+pp_status ensure_part(pp_ctx *c, size_t doubles) {
+    if (doubles <= c->part_cap) return PP_OK;
+    if (c->d_part) {
+        cudaFree(c->d_part);
+        c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), (void *)c->d_part), c->allocs.end());
+    }
+    c->d_part = nullptr;
+    CKS(dmalloc(c, (void **)&c->d_part, doubles * sizeof(double)));
+    c->part_cap = doubles;
+    return PP_OK;
+}
+
+// CGS2 of w against V[:, 0..j) -> V[:, j] normalised, H[0..j, col] on the device.
+pp_status cgs2_step(pp_ctx *c, void *V, int64_t ldv, int j, void *w, double *hcol) {
+    double *h1 = c->d_small, *h2 = c->d_small + 256, *scal = c->d_small + 512, *nrm = c->d_small + 513;
+    ppk::Prec pr = c->A.prec;
+    ppk::CgsArgs a;
+    a.n = (int)c->n;
+    a.V = V;
+    a.ldv = ldv;
+    a.j = j;
+    a.part = c->d_part;
+    a.ticket = c->d_ticket;
+    // pass 1: h1 = V^T w
+    a.mode = 0;
+    a.w = w;
+    a.out = h1;
+    ppk::launch_cgs(pr, a, c->stream);
+    CKS(check_launch(c));
+    // pass 2: w1 = w - V h1 (in place); h2 = V^T w1
+    a.mode = 1;
+    a.h = h1;
+    a.wout = w;
+    a.out = h2;
+    ppk::launch_cgs(pr, a, c->stream);
+    CKS(check_launch(c));
+    // pass 3: w2 = w1 - V h2 -> V[:, j]; H column; 1/||w2||
+    a.mode = 2;
+    a.h = h2;
+    a.h1 = h1;
+    a.wout = (char *)V + (size_t)j * ldv * c->esz;
+    a.out = nrm;
+    a.hcol = hcol;
+    a.scal = scal;
+    ppk::launch_cgs(pr, a, c->stream);
+    CKS(check_launch(c));
+    ppk::launch_scale(pr, (int)c->n, (char *)V + (size_t)j * ldv * c->esz, scal, c->stream);
+    return check_launch(c);
+}
+
+struct Timers {
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    cudaEvent_t get() {
+        if (used == ev.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ev.push_back(e);
+        }
+        return ev[used++];
+    }
+    ~Timers() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
+// Extend the Arnoldi decomposition from column j0 to m (Section 4): each step
+// w = Op(v_j), CGS2, v_{j+1}.  H is (m+1) x m column major on the device.
+pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, void *V, int64_t ldv, double *dH,
+                         int ldh, int j0, int m, void *W, Timers *tm, std::vector<std::pair<int, int>> *marks) {
+    for (int j = j0; j < m; ++j) {
+        const void *vj = (const char *)V + (size_t)j * ldv * c->esz;
+        cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+        if (tm) {
+            e0 = tm->get();
+            CK(cudaEventRecord(e0, c->stream));
+        }
+        if (tau_of)
+            CKS(op_tau(c, tau_of, vj, W));
+        else
+            CKS(op_apply(c, p, vj, W));
+        if (tm) {
+            e1 = tm->get();
+            CK(cudaEventRecord(e1, c->stream));
+        }
+        CKS(cgs2_step(c, V, ldv, j + 1, W, dH + (size_t)j * ldh));
+        if (tm) {
+            e2 = tm->get();
+            CK(cudaEventRecord(e2, c->stream));
+            marks->push_back({(int)tm->used - 3, (int)tm->used - 1});
+        }
+    }
+    return PP_OK;
+}
+
+void accumulate_times(Timers &tm, std::vector<std::pair<int, int>> &marks, double &t_apply, double &t_orth) {
+    for (auto &mk : marks) {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, tm.ev[mk.first], tm.ev[mk.first + 1]);
+        cudaEventElapsedTime(&b, tm.ev[mk.first + 1], tm.ev[mk.second]);
+        t_apply += a * 1e-3;
+        t_orth += b * 1e-3;
+    }
+    marks.clear();
+    tm.used = 0;
+}
+
+// Upload a host FP64 vector scaled by s into device storage.
+pp_status upload_vec(pp_ctx *c, const double *h, double s, void *d) {
+    std::vector<double> tmp(h, h + c->n);
+    for (auto &v : tmp) v *= s;
+    if (c->A.prec == ppk::F64) {
+        CK(cudaMemcpyAsync(d, tmp.data(), c->n * 8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> f(tmp.begin(), tmp.end());
+        CK(cudaMemcpyAsync(d, f.data(), c->n * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return PP_OK;
+}
+
+pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vector<double> &out) {
+    out.resize((size_t)c->n * cols);
+    if (c->A.prec == ppk::F64) {
+        CK(cudaMemcpy2DAsync(out.data(), c->n * 8, d, ld * 8, c->n * 8, cols, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> f((size_t)c->n * cols);
+        CK(cudaMemcpy2DAsync(f.data(), c->n * 4, d, ld * 4, c->n * 4, cols, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (size_t i = 0; i < f.size(); ++i) out[i] = f[i];
+    }
+    return PP_OK;
+}
+
+// GMRES(d) Arnoldi on Op from b (host), then harmonic Ritz roots, Leja, added roots.
+pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, pp_poly *out) {
+    if (d < 1 || d > 127) return pp_fail(PP_EINVAL, "degree must be in [1, 127] (got %d)", d);
+    if (d >= c->n) return pp_fail(PP_EINVAL, "degree %d must be below n = %lld", d, (long long)c->n);
+    int64_t ldv = c->ldv();
+    void *V = nullptr;
+    double *dH = nullptr;
+    pp_status st = PP_OK;
+    std::vector<void *> mine;
+    auto cleanup = [&]() {
+        for (void *q : mine) {
+            cudaFree(q);
+            c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), q), c->allocs.end());
+        }
+    };
+    if ((st = dmalloc(c, &V, (size_t)ldv * (d + 1) * c->esz)) < 0) return st;
+    mine.push_back(V);
+    if ((st = dmalloc(c, (void **)&dH, (size_t)(d + 1) * d * 8)) < 0) {
+        cleanup();
+        return st;
+    }
+    mine.push_back(dH);
+    double beta = 0;
+    for (int64_t i = 0; i < c->n; ++i) beta += b[i] * b[i];
+    beta = std::sqrt(beta);
+    if (!(beta > 0) || !std::isfinite(beta)) {
+        cleanup();
+        return pp_fail(PP_EINVAL, "start vector is zero or not finite");
+    }
+    std::vector<double> H((size_t)(d + 1) * d, 0.0);
+    if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)c->n) * 130)) < 0 || (st = upload_vec(c, b, 1.0 / beta, V)) < 0 ||
+        (st = arnoldi_extend(c, nullptr, tau_of, V, ldv, dH, d + 1, 0, d, c->vec[6], nullptr,
+                             nullptr)) < 0) {
+        cleanup();
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(H.data(), dH, H.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e != cudaSuccess) return pp_fail(PP_ECUDA, "build: %s", cudaGetErrorString(e));
+    for (double v : H)
+        if (!std::isfinite(v)) return pp_fail(PP_ENUMERIC, "build: non-finite Hessenberg entry");
+    // lucky breakdown: h_{j+1,j} <= 1e-14 ||H(0:j+2, 0:j+1)||_F
+    int steps = d;
+    bool brk = false;
+    double fro = 0;
+    for (int j = 0; j < d; ++j) {
+        for (int i = 0; i <= j + 1; ++i) fro += H[i + (size_t)j * (d + 1)] * H[i + (size_t)j * (d + 1)];
+        if (H[j + 1 + (size_t)j * (d + 1)] <= 1e-14 * std::sqrt(fro)) {
+            steps = j + 1;
+            brk = true;
+            break;
+        }
+    }
+    std::vector<double> re(steps), im(steps);
+    bool ok;
+    if (brk) {
+        std::vector<double> Hs((size_t)steps * steps);
+        for (int j = 0; j < steps; ++j)
+            for (int i = 0; i < steps; ++i) Hs[i + (size_t)j * steps] = H[i + (size_t)j * (d + 1)];
+        ok = ppd::dense_eig(steps, Hs.data(), steps, re.data(), im.data(), nullptr, 0);
+    } else {
+        ok = ppd::harmonic_ritz(d, H.data(), d + 1, re.data(), im.data());
+    }
+    if (!ok) return pp_fail(PP_ENUMERIC, "harmonic Ritz values: singular H_d or QR failure");
+    std::vector<cd> th(steps), ord;
+    for (int i = 0; i < steps; ++i) th[i] = cd(re[i], im[i]);
+    if (!ppd::leja_order(th, ord)) return pp_fail(PP_ENUMERIC, "roots not closed under conjugation");
+    int added = 0;
+    if (c->opts.add_roots) {
+        std::vector<cd> ext;
+        if (!ppd::add_stability_roots(ord, ext, added)) return pp_fail(PP_ENUMERIC, "added roots failed");
+        ord.swap(ext);
+    }
+    // work counted as the oracle does: start normalisation, then per step the
+    // operator, CGS2 against j+1 vectors and the norm
+    out->mvps = 0;
+    out->dots = 1;
+    out->vops = 2;
+    for (int j = 0; j < d; ++j) {
+        out->mvps += tau_of ? op_mvps(tau_of) : 1;
+        out->vops += tau_of ? vops_of(tau_of->steps) : 0;
+        out->dots += 2 * (j + 1) + 1;
+        out->vops += 4 * (j + 1) + 2;
+    }
+    out->roots = ord;
+    out->steps = steps_of(ord);
+    out->degree = steps;
+    out->added = added;
+    out->breakdown = brk;
+    return brk ? PP_EBREAKDOWN : PP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *pp_last_error(void) { return g_last_error.c_str(); }
+
+void pp_opts_default(pp_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = PP_FP64;
+    o->format = PP_FMT_AUTO;
+    o->target = PP_TARGET_SR;
+    o->sigma = NAN;
+    o->add_roots = 1;
+    o->max_cycles = 2000;
+    o->refine_steps = 4;
+    o->sell_c = 0;
+    o->sell_sigma = 0;
+    o->stream = nullptr;
+}
+
+void pp_destroy(pp_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals,
+                    const pp_opts *opts) {
+    if (!out || n <= 0 || !rowptr || !colind || !vals) return pp_fail(PP_EINVAL, "pp_create: bad arguments");
+    *out = nullptr;
+    int64_t nnz = rowptr[n];
+    if (rowptr[0] != 0 || nnz < 0 || nnz >= (int64_t)1 << 31 || n >= (int64_t)1 << 31)
+        return pp_fail(PP_EINVAL, "pp_create: rowptr must start at 0 and nnz, n < 2^31");
+    for (int64_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) return pp_fail(PP_EINVAL, "pp_create: rowptr not monotone at %lld", (long long)i);
+    for (int64_t k = 0; k < nnz; ++k)
+        if (colind[k] < 0 || colind[k] >= n || !std::isfinite(vals[k]))
+            return pp_fail(PP_EINVAL, "pp_create: bad entry %lld", (long long)k);
+    pp_ctx *c = new pp_ctx();
+    pp_opts_default(&c->opts);
+    if (opts) c->opts = *opts;
+    if (c->opts.precision != PP_FP64 && c->opts.precision != PP_FP32) {
+        delete c;
+        return pp_fail(PP_EINVAL, "pp_create: precision %d not supported", c->opts.precision);
+    }
+    c->n = n;
+    c->nnz = nnz;
+    // ||A||_1 and the Gershgorin shift on the host (exact, deterministic)
+    std::vector<double> colsum(n, 0.0);
+    double gl = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        double diag = 0, off = 0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            colsum[colind[k]] += std::fabs(vals[k]);
+            if (colind[k] == i)
+                diag += vals[k];
+            else
+                off += std::fabs(vals[k]);
+        }
+        gl = std::min(gl, diag - off);
+    }
+    c->norm1 = *std::max_element(colsum.begin(), colsum.end());
+    if (std::isnan(c->opts.sigma)) {
+        if (c->opts.target == PP_TARGET_SR)
+            c->sigma = (gl >= -1e-12 * c->norm1) ? 0.0 : std::min(0.0, gl);
+        else
+            c->sigma = 0.0;
+    } else {
+        c->sigma = c->opts.sigma;
+    }
+    if (c->opts.stream) {
+        c->stream = (cudaStream_t)c->opts.stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return pp_fail(PP_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+        }
+        c->own_stream = true;
+    }
+    ppk::Prec pr = c->opts.precision == PP_FP64 ? ppk::F64 : ppk::F32;
+    c->esz = pr == ppk::F64 ? 8 : 4;
+    pp_status st = PP_OK;
+    auto fail = [&](pp_status s) {
+        pp_destroy(c);
+        return s;
+    };
+    // device CSR (int32 row pointers, FP64 values)
+    int *d_rowptr = nullptr, *d_col = nullptr;
+    double *d_val = nullptr;
+    std::vector<int> rp32(n + 1);
+    for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rowptr[i];
+    if ((st = dmalloc(c, (void **)&d_rowptr, (n + 1) * 4)) < 0 || (st = dmalloc(c, (void **)&d_col, nnz * 4)) < 0 ||
+        (st = dmalloc(c, (void **)&d_val, nnz * 8)) < 0)
+        return fail(st);
+    if (cudaMemcpy(d_rowptr, rp32.data(), (n + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_col, colind, nnz * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_val, vals, nnz * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(pp_fail(PP_ECUDA, "pp_create: upload failed"));
+    // format choice: SELL-32 unless its padding exceeds 30 % (then CSR)
+    int nslices = (int)((n + 31) / 32);
+    std::vector<int> slen(nslices, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        int l = (int)(rowptr[i + 1] - rowptr[i]);
+        slen[i / 32] = std::max(slen[i / 32], l);
+    }
+    int64_t padded = 0;
+    for (int s = 0; s < nslices; ++s) padded += (int64_t)slen[s] * 32;
+    int fmt = c->opts.format;
+    if (fmt == PP_FMT_AUTO) fmt = (padded <= (int64_t)(1.3 * (double)nnz) + 32 * 8) ? PP_FMT_SELL : PP_FMT_CSR;
+    if (padded >= ((int64_t)1 << 31)) fmt = PP_FMT_CSR;
+    ppk::Matrix M;
+    M.n = (int)n;
+    M.prec = pr;
+    M.csr = {(int)n, d_rowptr, d_col, d_val};
+    if (pr == ppk::F32) {
+        void *v32 = nullptr;
+        if ((st = dmalloc(c, &v32, nnz * 4)) < 0) return fail(st);
+        ppk::launch_csr_convert(pr, nnz, d_val, v32, c->stream);
+        M.csr.val = v32;
+    }
+    if (fmt == PP_FMT_SELL) {
+        std::vector<int> sptr(nslices + 1, 0);
+        for (int s = 0; s < nslices; ++s) sptr[s + 1] = sptr[s] + slen[s] * 32;
+        int *d_sptr = nullptr, *d_scol = nullptr;
+        void *d_sval = nullptr;
+        if ((st = dmalloc(c, (void **)&d_sptr, (nslices + 1) * 4)) < 0 ||
+            (st = dmalloc(c, (void **)&d_scol, padded * 4)) < 0 || (st = dmalloc(c, &d_sval, padded * c->esz)) < 0)
+            return fail(st);
+        if (cudaMemcpy(d_sptr, sptr.data(), (nslices + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(pp_fail(PP_ECUDA, "pp_create: upload failed"));
+        ppk::launch_sell_fill(pr, (int)n, d_rowptr, d_col, d_val, d_sptr, d_scol, d_sval, c->stream);
+        if (cudaGetLastError() != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: SELL fill failed"));
+        M.fmt = 2;
+        M.sell = {(int)n, nslices, d_sptr, d_scol, d_sval};
+    } else {
+        M.fmt = 1;
+    }
+    c->A = M;
+    // FP64 operator for residuals on A (Section 4 tests convergence on A itself)
+    c->A64 = M;
+    c->A64.prec = ppk::F64;
+    c->A64.fmt = 1;
+    c->A64.csr = {(int)n, d_rowptr, d_col, d_val};
+    if (pr == ppk::F64) c->A64 = M;
+    // scratch vectors
+    for (int i = 0; i < 8; ++i)
+        if ((st = dmalloc(c, &c->vec[i], (size_t)c->ldv() * c->esz)) < 0) return fail(st);
+    if ((st = dmalloc(c, (void **)&c->d_ticket, 64)) < 0 || (st = dmalloc(c, (void **)&c->d_small, 4096 * 8)) < 0)
+        return fail(st);
+    if (cudaMemset(c->d_ticket, 0, 64) != cudaSuccess || cudaMemset(c->d_small, 0, 4096 * 8) != cudaSuccess)
+        return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
+    if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)n) * 130)) < 0) return fail(st);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: setup kernels failed"));
+    *out = c;
+    return PP_OK;
+}
+
+int64_t pp_launch_count(const pp_ctx *c) { return c ? c->launches : 0; }
+
+pp_status pp_matrix_info(const pp_ctx *c, double *norm1, double *sigma) {
+    if (!c) return pp_fail(PP_EINVAL, "pp_matrix_info: null context");
+    if (norm1) *norm1 = c->norm1;
+    if (sigma) *sigma = c->sigma;
+    return PP_OK;
+}
+
+pp_status pp_build_poly(pp_ctx *c, int d, const double *b, pp_poly **out) {
+    if (!c || !b || !out) return pp_fail(PP_EINVAL, "pp_build_poly: bad arguments");
+    pp_poly *p = new pp_poly();
+    p->ctx = c;
+    pp_status st = build_roots(c, d, b, nullptr, p);
+    if (st < 0) {
+        delete p;
+        return st;
+    }
+    *out = p;
+    return st;
+}
+
+pp_status pp_build_poly2(pp_ctx *c, int d1, int d2, const double *b, pp_poly **out) {
+    if (!c || !b || !out) return pp_fail(PP_EINVAL, "pp_build_poly2: bad arguments");
+    pp_poly *p1 = new pp_poly();
+    p1->ctx = c;
+    pp_status s1 = build_roots(c, d1, b, nullptr, p1);
+    if (s1 < 0) {
+        delete p1;
+        return s1;
+    }
+    pp_poly *p = new pp_poly();
+    p->ctx = c;
+    p->inner = p1;
+    pp_status s2 = build_roots(c, d2, b, p1, p);
+    if (s2 < 0) {
+        delete p;
+        return s2;
+    }
+    *out = p;
+    return (s1 == PP_EBREAKDOWN || s2 == PP_EBREAKDOWN) ? PP_EBREAKDOWN : PP_OK;
+}
+
+pp_status pp_poly_from_roots(pp_ctx *c, int count, const double *re, const double *im, pp_poly **out) {
+    if (!c || count < 1 || !re || !im || !out) return pp_fail(PP_EINVAL, "pp_poly_from_roots: bad arguments");
+    std::vector<cd> r(count);
+    for (int i = 0; i < count; ++i) {
+        r[i] = cd(re[i], im[i]);
+        if (!std::isfinite(re[i]) || !std::isfinite(im[i]) || (re[i] == 0 && im[i] == 0))
+            return pp_fail(PP_EINVAL, "pp_poly_from_roots: root %d is zero or not finite", i);
+    }
+    for (int i = 0; i < count;) {
+        if (r[i].imag() == 0) {
+            ++i;
+            continue;
+        }
+        if (r[i].imag() < 0 || i + 1 >= count || r[i + 1] != std::conj(r[i]))
+            return pp_fail(PP_EINVAL, "pp_poly_from_roots: pair at %d not adjacent (im > 0 first)", i);
+        i += 2;
+    }
+    pp_poly *p = new pp_poly();
+    p->ctx = c;
+    p->roots = r;
+    p->steps = steps_of(r);
+    p->degree = count;
+    *out = p;
+    return PP_OK;
+}
+
+static pp_status copy_roots(const std::vector<cd> &r, double *re, double *im, int cap, int *count) {
+    if (count) *count = (int)r.size();
+    for (int i = 0; i < (int)r.size() && i < cap; ++i) {
+        if (re) re[i] = r[i].real();
+        if (im) im[i] = r[i].imag();
+    }
+    return PP_OK;
+}
+
+pp_status pp_poly_roots(const pp_poly *p, double *re, double *im, int cap, int *count) {
+    if (!p) return pp_fail(PP_EINVAL, "pp_poly_roots: null poly");
+    return copy_roots(p->roots, re, im, cap, count);
+}
+
+pp_status pp_poly_inner_roots(const pp_poly *p, double *re, double *im, int cap, int *count) {
+    if (!p) return pp_fail(PP_EINVAL, "pp_poly_inner_roots: null poly");
+    if (!p->inner) {
+        if (count) *count = 0;
+        return PP_OK;
+    }
+    return copy_roots(p->inner->roots, re, im, cap, count);
+}
+
+pp_status pp_poly_info(const pp_poly *p, int *degree, int *added) {
+    if (!p) return pp_fail(PP_EINVAL, "pp_poly_info: null poly");
+    if (degree) *degree = p->degree;
+    if (added) *added = p->added;
+    return PP_OK;
+}
+
+pp_status pp_poly_counts(const pp_poly *p, int64_t *mvps, int64_t *dots, int64_t *vops) {
+    if (!p) return pp_fail(PP_EINVAL, "pp_poly_counts: null poly");
+    int64_t a = p->mvps, b = p->dots, v = p->vops;
+    if (p->inner) {
+        a += p->inner->mvps;
+        b += p->inner->dots;
+        v += p->inner->vops;
+    }
+    if (mvps) *mvps = a;
+    if (dots) *dots = b;
+    if (vops) *vops = v;
+    return PP_OK;
+}
+
+void pp_poly_destroy(pp_poly *p) { delete p; }
+
+pp_status pp_apply(const pp_poly *p, const void *x_dev, void *y_dev) {
+    if (!p || !x_dev || !y_dev) return pp_fail(PP_EINVAL, "pp_apply: bad arguments");
+    return op_apply(p->ctx, p, x_dev, y_dev);
+}
+
+pp_status pp_apply_host(const pp_poly *p, const double *x, double *y) {
+    if (!p || !x || !y) return pp_fail(PP_EINVAL, "pp_apply_host: bad arguments");
+    pp_ctx *c = p->ctx;
+    void *dx = nullptr;
+    CK(cudaMalloc(&dx, c->ldv() * c->esz));
+    pp_status st = upload_vec(c, x, 1.0, dx);
+    if (st >= 0) st = op_apply(c, p, dx, dx);
+    std::vector<double> out;
+    if (st >= 0) st = download_vecs(c, dx, c->ldv(), 1, out);
+    cudaFree(dx);
+    if (st < 0) return st;
+    std::memcpy(y, out.data(), c->n * 8);
+    return PP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Thick-restarted Arnoldi(m, k) on Op (Section 2 box step 2; Section 4)
+// ---------------------------------------------------------------------------
+pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k, double rtol, const double *v0, double *lam_re,
+                  double *lam_im, double *X, double *resid, int *nout, pp_stats *stats) {
+    double t_start = now();
+    if (!c || nev < 1 || k <= nev || m <= k || m >= c->n || m > 127 || !lam_re || !lam_im || !resid || !nout)
+        return pp_fail(PP_EINVAL, "pp_eigs: need 1 <= nev < k < m < n, m <= 127 and output arrays");
+    if (!(rtol > 0)) return pp_fail(PP_EINVAL, "pp_eigs: rtol must be positive");
+    const int64_t n = c->n, ldv = c->ldv();
+    const size_t esz = c->esz;
+    const double target = p ? 1.0 : 0.0;
+    pp_stats S{};
+    int64_t launches0 = c->launches;
+    std::vector<void *> mine;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(c->stream);
+        for (void *q : mine) {
+            cudaFree(q);
+            c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), q), c->allocs.end());
+        }
+    };
+    pp_status st;
+    void *V = nullptr, *V2 = nullptr, *Y = nullptr, *AY = nullptr, *W = c->vec[6];
+    double *dH = nullptr, *dQ = nullptr, *dq = nullptr, *dmu = nullptr;
+    int *dpartner = nullptr;
+    const int ldh = m + 1;
+    const int wcap = nev + 1;
+#define ALLOC(ptr, bytes)                                             \
+    do {                                                              \
+        if ((st = dmalloc(c, (void **)&(ptr), (bytes))) < 0) {        \
+            cleanup();                                                \
+            return st;                                                \
+        }                                                             \
+        mine.push_back((void *)(ptr));                                \
+    } while (0)
+    ALLOC(V, (size_t)ldv * (m + 1) * esz);
+    ALLOC(V2, (size_t)ldv * (m + 1) * esz);
+    ALLOC(Y, (size_t)ldv * (wcap + 1) * esz);
+    ALLOC(AY, (size_t)ldv * (wcap + 1) * esz);
+    ALLOC(dH, (size_t)ldh * m * 8);
+    ALLOC(dQ, (size_t)m * m * 8);
+    ALLOC(dq, (size_t)4 * (wcap + 1) * 8);
+    ALLOC(dmu, (size_t)3 * (wcap + 1) * 8);
+    ALLOC(dpartner, (size_t)(wcap + 1) * 4);
+#undef ALLOC
+    if (p && p->inner) W = c->vec[0];  // the double apply uses vec[1..7]; W must not alias them
+    if ((st = ensure_part(c, std::max((size_t)ppk::cgs_grid((int)n) * 130, (size_t)(wcap + 1) * 3 * 1024))) < 0) {
+        cleanup();
+        return st;
+    }
+    // start vector
+    std::vector<double> v0h(n, 1.0);
+    if (v0) std::copy(v0, v0 + n, v0h.begin());
+    double nv = 0;
+    for (double x : v0h) nv += x * x;
+    nv = std::sqrt(nv);
+    if (!(nv > 0) || !std::isfinite(nv)) {
+        cleanup();
+        return pp_fail(PP_EINVAL, "pp_eigs: start vector is zero or not finite");
+    }
+    if ((st = upload_vec(c, v0h.data(), 1.0 / nv, V)) < 0) {
+        cleanup();
+        return st;
+    }
+    cudaMemsetAsync(dH, 0, (size_t)ldh * m * 8, c->stream);
+    S.dots += 1;
+    S.vops += 2;
+    const int64_t opm = op_mvps(p);
+    const int64_t opv = op_vops(p);
+    Timers tm;
+    std::vector<std::pair<int, int>> marks;
+    std::vector<double> H((size_t)ldh * m), Hm((size_t)m * m), wr(m), wi(m), Sv((size_t)m * m);
+    std::vector<double> best_lam_re, best_lam_im, best_res, best_X;
+    int best_nw = 0;
+    bool converged = false;
+    int j0 = 0;
+    int nw = nev;
+    std::vector<int> order;
+    std::vector<cd> nu(m);
+    std::vector<double> lre, lim, res;
+    std::vector<int> slot_col;  // Y column of each slot
+    std::vector<int> partner_out;
+    for (int64_t cycle = 1; cycle <= c->opts.max_cycles; ++cycle) {
+        S.cycles = cycle;
+        if ((st = arnoldi_extend(c, p, nullptr, V, ldv, dH, ldh, j0, m, W, &tm, &marks)) < 0) {
+            cleanup();
+            return st;
+        }
+        S.mvps += opm * (m - j0);
+        for (int j = j0; j < m; ++j) {
+            S.dots += 2 * (j + 1) + 1;
+            S.vops += 4 * (j + 1) + 2 + opv;
+        }
+        double th0 = now();
+        cudaError_t e = cudaMemcpyAsync(H.data(), dH, H.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
+        }
+        accumulate_times(tm, marks, S.t_apply, S.t_orth);
+        for (double v : H)
+            if (!std::isfinite(v)) {
+                cleanup();
+                return pp_fail(PP_ENUMERIC, "pp_eigs: non-finite Hessenberg entry in cycle %lld", (long long)cycle);
+            }
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < m; ++i) Hm[i + (size_t)j * m] = H[i + (size_t)j * ldh];
+        if (!ppd::dense_eig(m, Hm.data(), m, wr.data(), wi.data(), Sv.data(), m)) {
+            cleanup();
+            return pp_fail(PP_ENUMERIC, "pp_eigs: Ritz values: QR failed");
+        }
+        for (int i = 0; i < m; ++i) nu[i] = cd(wr[i], wi[i]);
+        order = ppd::ritz_order(nu, target);
+        nw = nev + (nu[order[nev - 1]].imag() > 0 ? 1 : 0);
+        // Ritz vectors of the wanted set: columns (Re, Im) of each pair once
+        std::vector<double> Sw((size_t)m * nw);
+        std::vector<int> partner(nw), kind(nw);
+        std::vector<double> sg(nw, 0.0);
+        slot_col.assign(nw, 0);
+        for (int s = 0; s < nw;) {
+            int i = order[s];
+            if (wi[i] == 0.0) {
+                std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &Sw[(size_t)s * m]);
+                partner[s] = s;
+                slot_col[s] = s;
+                s += 1;
+            } else {
+                // eigenvector of the im > 0 member: columns (Re, Im) at i (im > 0) or i-1
+                int base = wi[i] > 0 ? i : i - 1;
+                std::copy(&Sv[(size_t)base * m], &Sv[(size_t)base * m] + m, &Sw[(size_t)s * m]);
+                std::copy(&Sv[(size_t)(base + 1) * m], &Sv[(size_t)(base + 1) * m] + m, &Sw[(size_t)(s + 1) * m]);
+                partner[s] = s + 1;
+                partner[s + 1] = s;
+                sg[s] = 1.0;
+                sg[s + 1] = -1.0;
+                slot_col[s] = s;
+                slot_col[s + 1] = s + 1;
+                s += 2;
+            }
+        }
+        // Y = V_m Sw; AY = A Y (FP64 operator, unshifted); Rayleigh quotients and residuals
+        e = cudaMemcpyAsync(dQ, Sw.data(), Sw.size() * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpartner, partner.data(), nw * 4, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
+        }
+        ppk::launch_rotate(c->A.prec, (int)n, V, ldv, m, dQ, nw, Y, ldv, c->stream);
+        if ((st = check_launch(c)) < 0) {
+            cleanup();
+            return st;
+        }
+        for (int s = 0; s < nw; ++s) {
+            ppk::StepArgs a;
+            a.x = (char *)Y + (size_t)s * ldv * esz;
+            a.y = (char *)AY + (size_t)s * ldv * esz;
+            a.plain = 1;
+            ppk::launch_step(c->A, a, c->stream);
+            if ((st = check_launch(c)) < 0) {
+                cleanup();
+                return st;
+            }
+        }
+        S.mvps += nw;
+        ppk::ColDotArgs cda;
+        cda.n = (int)n;
+        cda.nw = nw;
+        cda.Y = Y;
+        cda.AY = AY;
+        cda.ld = ldv;
+        cda.partner = dpartner;
+        cda.q = dq;
+        cda.part = c->d_part;
+        cda.ticket = c->d_ticket;
+        cda.mode = 0;
+        ppk::launch_coldots(c->A.prec, cda, c->stream);
+        if ((st = check_launch(c)) < 0) {
+            cleanup();
+            return st;
+        }
+        std::vector<double> q((size_t)4 * nw);
+        e = cudaMemcpyAsync(q.data(), dq, q.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
+        }
+        // mu = y^H A y / y^H y per slot
+        std::vector<double> mu((size_t)3 * nw, 0.0), ynrm(nw);
+        lre.assign(nw, 0);
+        lim.assign(nw, 0);
+        for (int s = 0; s < nw;) {
+            if (partner[s] == s) {
+                double yy = q[4 * s], yay = q[4 * s + 1];
+                lre[s] = yay / yy;
+                lim[s] = 0;
+                ynrm[s] = yy;
+                s += 1;
+            } else {
+                int r = s, i = s + 1;
+                double yy = q[4 * r] + q[4 * i];
+                double mr = (q[4 * r + 1] + q[4 * i + 1]) / yy;
+                double mi = (q[4 * r + 2] - q[4 * i + 2]) / yy;
+                lre[r] = lre[i] = mr;
+                lim[r] = mi;
+                lim[i] = -mi;
+                ynrm[r] = ynrm[i] = yy;
+                s += 2;
+            }
+        }
+        // residual columns: Re part AYr - mr Yr + mi Yi, Im part AYi - mr Yi - mi Yr
+        for (int s = 0; s < nw; ++s) {
+            mu[s] = lre[s];
+            mu[nw + s] = (partner[s] == s) ? 0.0 : (sg[s] > 0 ? lim[s] : lim[partner[s]]);
+            mu[2 * nw + s] = sg[s];
+        }
+        e = cudaMemcpyAsync(dmu, mu.data(), mu.size() * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
+        }
+        cda.mode = 1;
+        cda.mur = dmu;
+        cda.mui = dmu + nw;
+        cda.sg = dmu + 2 * nw;
+        ppk::launch_coldots(c->A.prec, cda, c->stream);
+        if ((st = check_launch(c)) < 0) {
+            cleanup();
+            return st;
+        }
+        e = cudaMemcpyAsync(q.data(), dq, q.size() * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
+        }
+        res.assign(nw, 0);
+        bool all = true;
+        int nconv = 0;
+        for (int s = 0; s < nw;) {
+            if (partner[s] == s) {
+                res[s] = std::sqrt(std::max(q[4 * s + 3], 0.0) / ynrm[s]) / c->norm1;
+                nconv += res[s] <= rtol;
+                all = all && (res[s] <= rtol);
+                s += 1;
+            } else {
+                double r2 = (q[4 * s + 3] + q[4 * (s + 1) + 3]) / ynrm[s];
+                res[s] = res[s + 1] = std::sqrt(std::max(r2, 0.0)) / c->norm1;
+                nconv += 2 * (res[s] <= rtol);
+                all = all && (res[s] <= rtol);
+                s += 2;
+            }
+        }
+        for (double x : res)
+            if (!std::isfinite(x)) all = false;
+        S.nconv = nconv;
+        S.vops += (int64_t)4 * m * nw;
+        best_nw = nw;
+        partner_out = partner;
+        if (all || cycle == c->opts.max_cycles) {
+            converged = all;
+            S.t_restart += now() - th0;
+            break;
+        }
+        // thick restart: keep k (k-1 if a pair would split), Q_k = qr([Re, Im] of kept Ritz vectors)
+        int kk = (nu[order[k - 1]].imag() > 0) ? k - 1 : k;
+        std::vector<double> B((size_t)m * kk);
+        int col = 0;
+        for (int s = 0; s < kk; ++s) {
+            int i = order[s];
+            if (wi[i] == 0.0) {
+                std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &B[(size_t)col * m]);
+                col++;
+            } else if (wi[i] > 0) {
+                std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &B[(size_t)col * m]);
+                std::copy(&Sv[(size_t)(i + 1) * m], &Sv[(size_t)(i + 1) * m] + m, &B[(size_t)(col + 1) * m]);
+                col += 2;
+            }
+        }
+        std::vector<double> Q((size_t)m * kk);
+        ppd::thin_qr(m, kk, B.data(), Q.data());
+        e = cudaMemcpyAsync(dQ, Q.data(), Q.size() * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
+        }
+        ppk::launch_rotate(c->A.prec, (int)n, V, ldv, m, dQ, kk, V2, ldv, c->stream);
+        if ((st = check_launch(c)) < 0) {
+            cleanup();
+            return st;
+        }
+        e = cudaMemcpyAsync((char *)V2 + (size_t)kk * ldv * esz, (char *)V + (size_t)m * ldv * esz, n * esz,
+                            cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
+        }
+        std::swap(V, V2);
+        S.vops += (int64_t)m * kk;
+        // H_k = [Q^T H_m Q ; h_{m+1,m} e_m^T Q]
+        std::vector<double> HQ((size_t)m * kk, 0.0), Hn((size_t)ldh * m, 0.0);
+        for (int cc = 0; cc < kk; ++cc)
+            for (int r = 0; r < m; ++r) {
+                double s = 0;
+                for (int t = 0; t < m; ++t) s += Hm[r + (size_t)t * m] * Q[t + (size_t)cc * m];
+                HQ[r + (size_t)cc * m] = s;
+            }
+        for (int cc = 0; cc < kk; ++cc) {
+            for (int r = 0; r < kk; ++r) {
+                double s = 0;
+                for (int t = 0; t < m; ++t) s += Q[t + (size_t)r * m] * HQ[t + (size_t)cc * m];
+                Hn[r + (size_t)cc * ldh] = s;
+            }
+            Hn[kk + (size_t)cc * ldh] = H[m + (size_t)(m - 1) * ldh] * Q[(m - 1) + (size_t)cc * m];
+        }
+        e = cudaMemcpyAsync(dH, Hn.data(), Hn.size() * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
+        }
+        j0 = kk;
+        S.t_restart += now() - th0;
+    }
+    // outputs sorted by the target: SR -> (Re, |Im|, Im > 0 first); SM -> (|lam|, Re, Im > 0 first)
+    std::vector<int> srt(best_nw);
+    for (int s = 0; s < best_nw; ++s) srt[s] = s;
+    bool sr = c->opts.target == PP_TARGET_SR;
+    std::stable_sort(srt.begin(), srt.end(), [&](int a, int b) {
+        double ka = sr ? lre[a] : std::hypot(lre[a], lim[a]), kb = sr ? lre[b] : std::hypot(lre[b], lim[b]);
+        if (ka != kb) return ka < kb;
+        if (sr) {
+            if (std::fabs(lim[a]) != std::fabs(lim[b])) return std::fabs(lim[a]) < std::fabs(lim[b]);
+        } else if (lre[a] != lre[b]) {
+            return lre[a] < lre[b];
+        }
+        return lim[a] > lim[b];
+    });
+    std::vector<double> Yh;
+    if (X) {
+        if ((st = download_vecs(c, Y, ldv, best_nw, Yh)) < 0) {
+            cleanup();
+            return st;
+        }
+    }
+    double maxres = 0;
+    for (int s = 0; s < best_nw; ++s) {
+        int o = srt[s];
+        lam_re[s] = lre[o];
+        lam_im[s] = lim[o];
+        resid[s] = res[o];
+        maxres = std::max(maxres, res[o]);
+        if (X) {
+            // unit vector: a real slot, or the pair's (Re x, Im x) for the member with
+            // Im(lambda) > 0 (x = yr + i yi when Im(mu) > 0 for the Re column's quotient,
+            // its conjugate otherwise), both scaled by the complex norm
+            bool pair = partner_out[o] != o;
+            int cr = pair ? std::min(o, partner_out[o]) : o, ci = pair ? cr + 1 : o;
+            double nrm2 = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                double a = Yh[(size_t)cr * n + i];
+                nrm2 += a * a;
+                if (pair) {
+                    double b = Yh[(size_t)ci * n + i];
+                    nrm2 += b * b;
+                }
+            }
+            double sc = 1.0 / std::sqrt(nrm2);
+            if (!pair) {
+                for (int64_t i = 0; i < n; ++i) X[(size_t)s * n + i] = Yh[(size_t)o * n + i] * sc;
+            } else {
+                bool first = lim[o] > 0 || (lim[o] == 0 && o == cr);
+                double sgn = (lim[cr] >= 0) ? 1.0 : -1.0;  // conj when the Re column's quotient has Im < 0
+                const double *src = first ? &Yh[(size_t)cr * n] : &Yh[(size_t)ci * n];
+                double f = first ? sc : sgn * sc;
+                for (int64_t i = 0; i < n; ++i) X[(size_t)s * n + i] = src[i] * f;
+            }
+        }
+    }
+    *nout = best_nw;
+    cleanup();
+    S.converged = converged ? 1 : 0;
+    S.max_resid = maxres;
+    S.kernel_launches = c->launches - launches0;
+    S.t_total = now() - t_start;
+    if (stats) *stats = S;
+    if (!converged) return pp_fail(PP_ENOTCONV, "pp_eigs: not converged in %d cycles", c->opts.max_cycles);
+    return PP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,510 @@
+// CUDA kernels of the hot path (sm_103a).
+//
+//  * k_sell_step / k_csr_step: one fused pass of the factored GMRES polynomial
+//    (Eq. (2.1)): SpMV with A - sigma I plus the root-step axpy and the running
+//    sum (Section 2 footnote 2) in the same pass; conjugate pairs use two passes
+//    in real arithmetic; the double polynomial's outer step (Section 8) is
+//    fused into the last inner pass.
+//  * k_cgs: the three passes of classical Gram-Schmidt with one
+//    reorthogonalisation (Section 4), each a single sweep over the basis with
+//    a deterministic two-level reduction finished by the last block.
+//  * k_rotate: V_m Q_k for the thick restart and Ritz vectors (Section 4).
+//  * k_coldots: Rayleigh quotients and residual norms on A (Section 4).
+#include "pp_internal.h"
+
+#include <cuda_runtime.h>
+
+namespace ppk {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+template <typename T>
+__device__ __forceinline__ double ld_acc(const T *p, size_t i) {
+    return (double)__ldg(p + i);
+}
+
+// ---------------------------------------------------------------------------
+// Fused root step
+// ---------------------------------------------------------------------------
+template <typename T, typename Acc>
+__device__ __forceinline__ void step_epilogue(int row, Acc u, const StepArgs &s) {
+    const T *x = (const T *)s.x;
+    Acc xi = (Acc)x[row];
+    if (s.sigma != 0.0) u = u - (Acc)s.sigma * xi;
+    if (s.plain) {
+        ((T *)s.y)[row] = (T)u;
+        return;
+    }
+    Acc delta = (Acc)s.a1 * xi + (Acc)s.a2 * u;
+    if (s.y) {
+        Acc base = s.aux ? (Acc)((const T *)s.aux)[row] : xi;
+        ((T *)s.y)[row] = (T)(base - delta);
+    }
+    if (s.r) {
+        T *r = (T *)s.r;
+        Acc rv = s.r_init ? delta : (Acc)r[row] + delta;
+        if (s.r_write) r[row] = (T)rv;
+        if (s.oy) {
+            Acc od = (Acc)s.b2 * rv;
+            if (s.ox) od += (Acc)s.b1 * (Acc)((const T *)s.ox)[row];
+            ((T *)s.oy)[row] = (T)((Acc)((const T *)s.obase)[row] - od);
+        }
+    }
+}
+
+template <typename T, typename V, typename Acc>
+__global__ void __launch_bounds__(kThreads) k_sell_step(SellView A, StepArgs s) {
+    int row = blockIdx.x * kThreads + threadIdx.x;
+    if (row >= A.n) return;
+    int sl = row >> 5, lane = row & 31;
+    int beg = __ldg(A.slice_ptr + sl), end = __ldg(A.slice_ptr + sl + 1);
+    int len = (end - beg) >> 5;
+    const int *col = A.col + beg + lane;
+    const V *val = (const V *)A.val + beg + lane;
+    const T *x = (const T *)s.x;
+    Acc acc = 0;
+#pragma unroll 4
+    for (int k = 0; k < len; ++k) {
+        Acc a = (Acc)__ldg(val + 32 * k);
+        int c = __ldg(col + 32 * k);
+        acc = fma(a, (Acc)__ldg(x + c), acc);
+    }
+    step_epilogue<T, Acc>(row, acc, s);
+}
+
+template <typename T, typename V, typename Acc>
+__global__ void __launch_bounds__(kThreads) k_csr_step(CsrView A, StepArgs s) {
+    int row = blockIdx.x * kThreads + threadIdx.x;
+    if (row >= A.n) return;
+    int beg = __ldg(A.rowptr + row), end = __ldg(A.rowptr + row + 1);
+    const V *val = (const V *)A.val;
+    const T *x = (const T *)s.x;
+    Acc acc = 0;
+    for (int k = beg; k < end; ++k) acc = fma((Acc)__ldg(val + k), (Acc)__ldg(x + __ldg(A.col + k)), acc);
+    step_epilogue<T, Acc>(row, acc, s);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic grid reduction: every block writes `nout` partials to
+// part[block * nout + o]; the last block to arrive sums them in block order.
+// ---------------------------------------------------------------------------
+__device__ bool last_block(unsigned *ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1);
+    __syncthreads();
+    return is_last;
+}
+
+__device__ void reduce_partials(const double *part, int nblocks, int nout, double *out) {
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int o = warp; o < nout; o += kWarps) {
+        double s = 0;
+        for (int b = lane; b < nblocks; b += 32) s += __ldcg(part + (size_t)b * nout + o);
+#pragma unroll
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) out[o] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CGS2 passes. A tile is kRows consecutive rows; warp w owns basis columns
+// c = w + 8 cc (cc < CPW).  Each lane holds kRows/32 rows of the tile.
+// ---------------------------------------------------------------------------
+constexpr int kRows = 64;
+constexpr int kQ = kRows / 32;
+
+template <typename T, int CPW>
+__global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const T *V = (const T *)a.V;
+    const T *w = (const T *)a.w;
+    T *wout = (T *)a.wout;
+    const int j = a.j, n = a.n;
+    __shared__ double red[kWarps][kRows];
+    __shared__ double wsh[kRows];
+    __shared__ double hs[8 * CPW];
+    __shared__ double nrm_sh[kWarps];
+    if (a.mode != 0)
+        for (int c = tid; c < j; c += kThreads) hs[c] = a.h[c];
+    __syncthreads();
+    double acc[CPW];
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) acc[cc] = 0;
+    double nrm = 0;
+    const int ntiles = (n + kRows - 1) / kRows;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * kRows;
+        double vv[CPW][kQ];
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+            int c = warp + kWarps * cc;
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                int row = r0 + lane + 32 * q;
+                vv[cc][q] = (c < j && row < n) ? ld_acc(V, (size_t)c * a.ldv + row) : 0.0;
+            }
+        }
+        if (a.mode == 0) {
+            double wv[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                int row = r0 + lane + 32 * q;
+                wv[q] = row < n ? ld_acc(w, row) : 0.0;
+            }
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc)
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wv[q], acc[cc]);
+            continue;
+        }
+        // w - V h for the tile rows: per-warp partial sums, then across warps
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            double s = 0;
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) {
+                int c = warp + kWarps * cc;
+                if (c < j) s = fma(vv[cc][q], hs[c], s);
+            }
+            red[warp][lane + 32 * q] = s;
+        }
+        __syncthreads();
+        if (tid < kRows) {
+            int row = r0 + tid;
+            double v = 0;
+            if (row < n) {
+                double s = 0;
+#pragma unroll
+                for (int ww = 0; ww < kWarps; ++ww) s += red[ww][tid];
+                v = ld_acc(w, row) - s;
+                T vt = (T)v;
+                wout[row] = vt;
+                v = (double)vt;
+                nrm = fma(v, v, nrm);
+            }
+            wsh[tid] = v;
+        }
+        __syncthreads();
+        if (a.mode == 1) {
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc)
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wsh[lane + 32 * q], acc[cc]);
+        }
+    }
+    // per-block partials
+    const int nout = (a.mode == 0) ? j : (a.mode == 1 ? j + 1 : 1);
+    double *part = a.part + (size_t)blockIdx.x * nout;
+    if (a.mode != 2) {
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+            double s = acc[cc];
+#pragma unroll
+            for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            int c = warp + kWarps * cc;
+            if (lane == 0 && c < j) part[c] = s;
+        }
+    }
+    if (a.mode != 0) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+        if (lane == 0) nrm_sh[warp] = nrm;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0;
+            for (int ww = 0; ww < kWarps; ++ww) s += nrm_sh[ww];
+            part[a.mode == 1 ? j : 0] = s;
+        }
+    }
+    if (!last_block(a.ticket)) return;
+    reduce_partials(a.part, gridDim.x, nout, a.out);
+    __syncthreads();
+    if (tid == 0) *a.ticket = 0;
+    if (a.mode == 2) {
+        __threadfence_block();
+        __syncthreads();
+        double nn = sqrt(a.out[0]);
+        for (int c = tid; c < j; c += kThreads) a.hcol[c] = a.h1[c] + a.h[c];
+        if (tid == 0) {
+            a.hcol[j] = nn;
+            a.scal[0] = nn > 0 ? 1.0 / nn : 0.0;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_scale(int n, T *x, const double *scal) {
+    double s = *scal;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] = (T)((double)x[i] * s);
+}
+
+// ---------------------------------------------------------------------------
+// Out = V[:, 0:m] Q  (tile of 32 rows per block iteration; Q and the V tile in
+// shared memory; warp w computes output columns w, w+8, ...)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_rotate(int n, const T *V, int64_t ldv, int m, const double *Q,
+                                                     int kk, T *out, int64_t ldo) {
+    extern __shared__ double sm[];
+    double *Qs = sm;               // m * kk
+    double *Vs = sm + (size_t)m * kk;  // m * 32
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < m * kk; i += kThreads) Qs[i] = Q[i];
+    const int ntiles = (n + 31) / 32;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int row = tile * 32 + lane;
+        __syncthreads();
+        for (int r = warp; r < m; r += kWarps) Vs[r * 32 + lane] = row < n ? ld_acc(V, (size_t)r * ldv + row) : 0.0;
+        __syncthreads();
+        for (int c = warp; c < kk; c += kWarps) {
+            double acc = 0;
+            const double *qc = Qs + (size_t)c * m;
+            for (int r = 0; r < m; ++r) acc = fma(Vs[r * 32 + lane], qc[r], acc);
+            if (row < n) out[(size_t)c * ldo + row] = (T)acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column dots for the convergence test.  grid.y = column, grid.x = row chunks.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_coldots(ColDotArgs a) {
+    const int c = blockIdx.y;
+    const int p = a.partner[c];
+    const T *Y = (const T *)a.Y, *AY = (const T *)a.AY;
+    const T *yc = Y + (size_t)c * a.ld, *ayc = AY + (size_t)c * a.ld;
+    const T *yp = Y + (size_t)p * a.ld, *ayp = AY + (size_t)p * a.ld;
+    double s0 = 0, s1 = 0, s2 = 0;
+    double mr = 0, mi = 0;
+    if (a.mode == 1) {
+        mr = a.mur[c];
+        mi = a.sg[c] * a.mui[c];
+    }
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < a.n; i += gridDim.x * kThreads) {
+        double y = ld_acc(yc, i), ay = ld_acc(ayc, i);
+        if (a.mode == 0) {
+            s0 = fma(y, y, s0);
+            s1 = fma(y, ay, s1);
+            s2 = fma(y, ld_acc(ayp, i), s2);
+        } else {
+            double r = ay - mr * y + mi * ld_acc(yp, i);
+            s0 = fma(r, r, s0);
+        }
+    }
+    __shared__ double sh[3][kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    }
+    if (lane == 0) {
+        sh[0][warp] = s0;
+        sh[1][warp] = s1;
+        sh[2][warp] = s2;
+    }
+    __syncthreads();
+    const int nout = 3;
+    double *part = a.part + ((size_t)c * gridDim.x + blockIdx.x) * nout;
+    if (threadIdx.x < 3) {
+        double s = 0;
+        for (int ww = 0; ww < kWarps; ++ww) s += sh[threadIdx.x][ww];
+        part[threadIdx.x] = s;
+    }
+    if (!last_block(a.ticket)) return;
+    // reduce: for column cc, entries part[(cc*gx + b)*3 + t]
+    const int gx = gridDim.x;
+    for (int idx = threadIdx.x >> 5; idx < a.nw * 3; idx += kWarps) {
+        int cc = idx / 3, t = idx % 3;
+        double s = 0;
+        for (int b = lane; b < gx; b += 32) s += __ldcg(a.part + ((size_t)cc * gx + b) * 3 + t);
+#pragma unroll
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) {
+            if (a.mode == 0)
+                a.q[4 * cc + t] = s;
+            else if (t == 0)
+                a.q[4 * cc + 3] = s;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *a.ticket = 0;
+}
+
+// ---------------------------------------------------------------------------
+// SELL-32 construction
+// ---------------------------------------------------------------------------
+__global__ void k_sell_slice_len(int n, const int *rowptr, int *slice_len) {
+    int row = blockIdx.x * kThreads + threadIdx.x;
+    int len = row < n ? rowptr[row + 1] - rowptr[row] : 0;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
+    if ((threadIdx.x & 31) == 0 && row - (int)(threadIdx.x & 31) < n) slice_len[row >> 5] = len;
+}
+
+template <typename V>
+__global__ void k_sell_fill(int n, const int *rowptr, const int *col, const double *val, const int *slice_ptr,
+                            int *scol, V *sval) {
+    int row = blockIdx.x * kThreads + threadIdx.x;
+    int sl = row >> 5, lane = row & 31;
+    if ((row & ~31) >= n) return;
+    int beg = slice_ptr[sl], width = (slice_ptr[sl + 1] - beg) >> 5;
+    int rb = row < n ? rowptr[row] : 0, re = row < n ? rowptr[row + 1] : 0;
+    int last = row < n ? (re > rb ? col[re - 1] : row) : 0;
+    for (int k = 0; k < width; ++k) {
+        int src = rb + k;
+        size_t dst = (size_t)beg + 32 * k + lane;
+        if (src < re) {
+            scol[dst] = col[src];
+            sval[dst] = (V)val[src];
+        } else {
+            scol[dst] = last;  // padding: repeat a valid column, value 0
+            sval[dst] = (V)0;
+        }
+    }
+}
+
+template <typename V>
+__global__ void k_convert_vals(int64_t nnz, const double *val, V *out) {
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * kThreads)
+        out[i] = (V)val[i];
+}
+
+template <typename A, typename B>
+__global__ void k_convert(int n, const A *x, B *y) {
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) y[i] = (B)x[i];
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 132;
+    }
+    return sms;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    int blocks = (A.n + kThreads - 1) / kThreads;
+    if (A.fmt == 2) {
+        if (A.prec == F64)
+            k_sell_step<double, double, double><<<blocks, kThreads, 0, st>>>(A.sell, s);
+        else
+            k_sell_step<float, float, float><<<blocks, kThreads, 0, st>>>(A.sell, s);
+    } else {
+        if (A.prec == F64)
+            k_csr_step<double, double, double><<<blocks, kThreads, 0, st>>>(A.csr, s);
+        else
+            k_csr_step<float, float, float><<<blocks, kThreads, 0, st>>>(A.csr, s);
+    }
+}
+
+int cgs_grid(int n) {
+    int tiles = (n + kRows - 1) / kRows;
+    int g = num_sms() * 4;
+    return tiles < g ? tiles : g;
+}
+
+template <typename T>
+static void cgs_dispatch(const CgsArgs &a, cudaStream_t st) {
+    int g = cgs_grid(a.n);
+    int cpw = (a.j + kWarps - 1) / kWarps;
+    if (cpw <= 2)
+        k_cgs<T, 2><<<g, kThreads, 0, st>>>(a);
+    else if (cpw <= 4)
+        k_cgs<T, 4><<<g, kThreads, 0, st>>>(a);
+    else if (cpw <= 8)
+        k_cgs<T, 8><<<g, kThreads, 0, st>>>(a);
+    else
+        k_cgs<T, 16><<<g, kThreads, 0, st>>>(a);
+}
+
+void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st) {
+    if (p == F64)
+        cgs_dispatch<double>(a, st);
+    else
+        cgs_dispatch<float>(a, st);
+}
+
+void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st) {
+    int g = num_sms() * 4;
+    if (p == F64)
+        k_scale<double><<<g, kThreads, 0, st>>>(n, (double *)x, scal);
+    else
+        k_scale<float><<<g, kThreads, 0, st>>>(n, (float *)x, scal);
+}
+
+void launch_rotate(Prec p, int n, const void *V, int64_t ldv, int m, const double *Q, int kk, void *out,
+                   int64_t ldo, cudaStream_t st) {
+    size_t smem = ((size_t)m * kk + (size_t)m * 32) * sizeof(double);
+    int tiles = (n + 31) / 32;
+    int g = num_sms() * 2;
+    if (tiles < g) g = tiles;
+    if (p == F64) {
+        cudaFuncSetAttribute(k_rotate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rotate<double><<<g, kThreads, smem, st>>>(n, (const double *)V, ldv, m, Q, kk, (double *)out, ldo);
+    } else {
+        cudaFuncSetAttribute(k_rotate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rotate<float><<<g, kThreads, smem, st>>>(n, (const float *)V, ldv, m, Q, kk, (float *)out, ldo);
+    }
+}
+
+void launch_coldots(Prec p, const ColDotArgs &a, cudaStream_t st) {
+    int gx = (a.n + kThreads * 8 - 1) / (kThreads * 8);
+    int cap = num_sms() * 2;
+    if (gx > cap) gx = cap;
+    if (gx < 1) gx = 1;
+    dim3 grid(gx, a.nw);
+    if (p == F64)
+        k_coldots<double><<<grid, kThreads, 0, st>>>(a);
+    else
+        k_coldots<float><<<grid, kThreads, 0, st>>>(a);
+}
+
+void launch_sell_slice_len(int n, const int *rowptr, int *slice_len, cudaStream_t st) {
+    int blocks = (n + kThreads - 1) / kThreads;
+    k_sell_slice_len<<<blocks, kThreads, 0, st>>>(n, rowptr, slice_len);
+}
+
+void launch_sell_fill(Prec p, int n, const int *rowptr, const int *col, const double *val, const int *slice_ptr,
+                      int *scol, void *sval, cudaStream_t st) {
+    int blocks = (n + kThreads - 1) / kThreads;
+    if (p == F64)
+        k_sell_fill<double><<<blocks, kThreads, 0, st>>>(n, rowptr, col, val, slice_ptr, scol, (double *)sval);
+    else
+        k_sell_fill<float><<<blocks, kThreads, 0, st>>>(n, rowptr, col, val, slice_ptr, scol, (float *)sval);
+}
+
+void launch_csr_convert(Prec p, int64_t nnz, const double *val, void *out, cudaStream_t st) {
+    int g = num_sms() * 4;
+    if (p == F32) k_convert_vals<float><<<g, kThreads, 0, st>>>(nnz, val, (float *)out);
+}
+
+void launch_convert(Prec from, Prec to, int n, const void *x, void *y, cudaStream_t st) {
+    int g = num_sms() * 4;
+    if (from == F64 && to == F32)
+        k_convert<double, float><<<g, kThreads, 0, st>>>(n, (const double *)x, (float *)y);
+    else if (from == F32 && to == F64)
+        k_convert<float, double><<<g, kThreads, 0, st>>>(n, (const float *)x, (double *)y);
+    else if (from == F64)
+        k_convert<double, double><<<g, kThreads, 0, st>>>(n, (const double *)x, (double *)y);
+    else
+        k_convert<float, float><<<g, kThreads, 0, st>>>(n, (const float *)x, (float *)y);
+}
+
+}  // namespace ppk

@@ -1,0 +1,144 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include "pp.h"
+
+#include <complex>
+#include <cstdint>
+#include <vector>
+
+// Record a failure message for pp_last_error() and return the status.
+pp_status pp_fail(pp_status s, const char *fmt, ...);
+
+namespace ppd {
+using cd = std::complex<double>;
+bool dense_eig(int n, const double *A, int lda, double *wr, double *wi, double *V, int ldv);
+bool lu_solve(int n, std::vector<double> M, double *b);
+bool harmonic_ritz(int d, const double *H, int ldh, double *re, double *im);
+void thin_qr(int m, int k, const double *B, double *Q);
+bool leja_order(const std::vector<cd> &roots, std::vector<cd> &out);
+double pof_log10(const std::vector<cd> &roots, size_t j);
+int extra_copies(double lp);
+bool add_stability_roots(const std::vector<cd> &ordered, std::vector<cd> &out, int &added);
+std::vector<int> ritz_order(const std::vector<cd> &nu, double target);
+}  // namespace ppd
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#else
+typedef struct CUstream_st *cudaStream_t;
+#endif
+
+namespace ppk {
+
+// Storage precisions of device vectors / matrix values.
+enum Prec { F64 = 0, F32 = 1 };
+
+// SELL-C-sigma matrix with C = 32: slice s holds rows [32 s, 32 s + 32);
+// entries of slice s occupy [slice_ptr[s], slice_ptr[s+1]) laid out column
+// major within the slice (entry k of lane l at slice_ptr[s] + 32 k + l).
+// perm (optional) maps sorted row r -> original row perm[r].
+struct SellView {
+    int n;
+    int nslices;
+    const int *slice_ptr;
+    const int *col;
+    const void *val;
+};
+
+struct CsrView {
+    int n;
+    const int *rowptr;
+    const int *col;
+    const void *val;
+};
+
+// One fused pass of the factored polynomial (Eq. (2.1)):
+//   u = (A - sigma I) x
+//   plain:  y = u
+//   else:   delta = a1 x + a2 u;  y = base - delta (base = aux or x);
+//           r = (r_init ? 0 : r) + delta (the running sum of Section 2 footnote 2)
+//   outer (double polynomial, Section 8): oy = obase - (b1 ox + b2 r)
+struct StepArgs {
+    const void *x = nullptr;
+    const void *aux = nullptr;
+    void *y = nullptr;
+    void *r = nullptr;
+    int plain = 0;
+    int r_init = 0;
+    int r_write = 1;
+    double a1 = 0, a2 = 0, sigma = 0;
+    const void *obase = nullptr;
+    const void *ox = nullptr;
+    void *oy = nullptr;
+    double b1 = 0, b2 = 0;
+};
+
+struct Matrix {
+    int n = 0;
+    int fmt = 2;  // 1 CSR, 2 SELL
+    Prec prec = F64;
+    SellView sell{};
+    CsrView csr{};
+};
+
+void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st);
+
+// CGS2 passes over the basis V (column major, leading dimension ldv, j columns).
+//  mode 0: out[0..j) = V^T w
+//  mode 1: wout = w - V h;  out[0..j) = V^T wout;  out[j] = ||wout||^2
+//  mode 2: wout = w - V h;  out[0] = ||wout||^2; then H column: hcol[c] = h1[c] + h[c]
+//          (c < j), hcol[j] = ||wout||, scal[0] = 1/||wout||
+struct CgsArgs {
+    int mode = 0;
+    int n = 0;
+    const void *V = nullptr;
+    int64_t ldv = 0;
+    int j = 0;
+    const void *w = nullptr;
+    void *wout = nullptr;
+    const double *h = nullptr;
+    const double *h1 = nullptr;
+    double *hcol = nullptr;
+    double *scal = nullptr;
+    double *out = nullptr;
+    double *part = nullptr;
+    unsigned *ticket = nullptr;
+};
+int cgs_grid(int n);
+void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st);
+void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st);
+
+// Out[:, c] = sum_r V[:, r] Q[r, c] (c < kk), Q column major m x kk on the device.
+void launch_rotate(Prec p, int n, const void *V, int64_t ldv, int m, const double *Q, int kk, void *out,
+                   int64_t ldo, cudaStream_t st);
+
+// Column dots for the convergence test (Section 4).
+//  mode 0: q[4c+0] = Y_c.Y_c, q[4c+1] = Y_c.AY_c, q[4c+2] = Y_c.AY_{pc}
+//  mode 1: q[4c+3] = || AY_c - mur_c Y_c + sg_c mui_c Y_{pc} ||^2
+struct ColDotArgs {
+    int mode = 0;
+    int n = 0;
+    int nw = 0;
+    const void *Y = nullptr;
+    const void *AY = nullptr;
+    int64_t ld = 0;
+    const int *partner = nullptr;
+    const double *mur = nullptr;
+    const double *mui = nullptr;
+    const double *sg = nullptr;
+    double *q = nullptr;
+    double *part = nullptr;
+    unsigned *ticket = nullptr;
+};
+void launch_coldots(Prec p, const ColDotArgs &a, cudaStream_t st);
+
+// SELL construction from a device CSR (row lengths -> slice widths -> fill).
+void launch_sell_slice_len(int n, const int *rowptr, int *slice_len, cudaStream_t st);
+void launch_sell_fill(Prec p, int n, const int *rowptr, const int *col, const double *val,
+                      const int *slice_ptr, int *scol, void *sval, cudaStream_t st);
+void launch_csr_convert(Prec p, int64_t nnz, const double *val, void *out, cudaStream_t st);
+// y = x converted between storage precisions
+void launch_convert(Prec from, Prec to, int n, const void *x, void *y, cudaStream_t st);
+
+}  // namespace ppk

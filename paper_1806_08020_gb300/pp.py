@@ -1,0 +1,312 @@
+"""ctypes binding of the C-ABI in ``include/pp.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: the polynomial build, apply and Arnoldi iteration
+all run in ``libpp.so``.  Importing this module loads the library and raises
+if it has not been built (``__graft_entry__.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpp.so")
+
+PP_OK, PP_ENOTCONV, PP_EBREAKDOWN = 0, 1, 2
+PP_EINVAL, PP_ENOMEM, PP_ECUDA, PP_ETIMEOUT, PP_ENUMERIC = -1, -2, -3, -4, -5
+PP_FP64, PP_FP32, PP_FP32_BF16 = 0, 1, 2
+PP_FMT_AUTO, PP_FMT_CSR, PP_FMT_SELL = 0, 1, 2
+PP_TARGET_SM, PP_TARGET_SR = 0, 1
+
+
+class pp_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("format", C.c_int), ("target", C.c_int), ("sigma", C.c_double),
+                ("add_roots", C.c_int), ("max_cycles", C.c_int), ("refine_steps", C.c_int),
+                ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("stream", C.c_void_p)]
+
+
+class pp_stats(C.Structure):
+    _fields_ = [("cycles", C.c_int64), ("mvps", C.c_int64), ("dots", C.c_int64), ("vops", C.c_int64),
+                ("kernel_launches", C.c_int64), ("converged", C.c_int32), ("nconv", C.c_int32),
+                ("t_total", C.c_double), ("t_apply", C.c_double), ("t_orth", C.c_double),
+                ("t_restart", C.c_double), ("max_resid", C.c_double)]
+
+    def to_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pp status {status}: {msg}")
+        self.status = status
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_I64 = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "pp_opts_default": (None, [C.POINTER(pp_opts)]),
+    "pp_last_error": (C.c_char_p, []),
+    "pp_create": (C.c_int, [C.POINTER(_P), C.c_int64, _I64, C.POINTER(C.c_int32), _D, C.POINTER(pp_opts)]),
+    "pp_destroy": (None, [_P]),
+    "pp_matrix_info": (C.c_int, [_P, _D, _D]),
+    "pp_launch_count": (C.c_int64, [_P]),
+    "pp_build_poly": (C.c_int, [_P, C.c_int, _D, C.POINTER(_P)]),
+    "pp_build_poly2": (C.c_int, [_P, C.c_int, C.c_int, _D, C.POINTER(_P)]),
+    "pp_poly_from_roots": (C.c_int, [_P, C.c_int, _D, _D, C.POINTER(_P)]),
+    "pp_poly_roots": (C.c_int, [_P, _D, _D, C.c_int, _I]),
+    "pp_poly_inner_roots": (C.c_int, [_P, _D, _D, C.c_int, _I]),
+    "pp_poly_info": (C.c_int, [_P, _I, _I]),
+    "pp_poly_counts": (C.c_int, [_P, _I64, _I64, _I64]),
+    "pp_poly_destroy": (None, [_P]),
+    "pp_apply": (C.c_int, [_P, _P, _P]),
+    "pp_apply_host": (C.c_int, [_P, _D, _D]),
+    "pp_eigs": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D, _D, _I,
+                          C.POINTER(pp_stats)]),
+    "pp_dense_eig": (C.c_int, [C.c_int, _D, C.c_int, _D, _D, _D, C.c_int]),
+    "pp_harmonic_ritz": (C.c_int, [C.c_int, _D, C.c_int, _D, _D]),
+    "pp_leja_order": (C.c_int, [C.c_int, _D, _D, _D, _D]),
+    "pp_add_stability_roots": (C.c_int, [C.c_int, _D, _D, C.c_int, _D, _D, _I]),
+}
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points this binding declares (all exported by libpp.so)."""
+    return list(_SIGS)
+
+
+def _check(status: int, allow=(PP_OK,)) -> int:
+    if status in allow:
+        return status
+    raise PPError(status, LIB.pp_last_error().decode(errors="replace"))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Handles
+# ---------------------------------------------------------------------------
+class Context:
+    """Owner of a pp_ctx handle (the uploaded matrix and its device scratch)."""
+
+    def __init__(self, handle: int, n: int, precision: int):
+        self.handle = C.c_void_p(handle)
+        self.n = n
+        self.precision = precision
+
+    def close(self):
+        if self.handle:
+            LIB.pp_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Poly:
+    """Owner of a pp_poly handle; keeps its context alive."""
+
+    def __init__(self, handle: int, ctx: Context, status: int):
+        self.handle = C.c_void_p(handle)
+        self.ctx = ctx
+        self.status = status
+
+    def close(self):
+        if self.handle:
+            LIB.pp_poly_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_opts(**kw) -> pp_opts:
+    o = pp_opts()
+    LIB.pp_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def pp_create(A, **opts) -> Context:
+    """A: object with n, rowptr (int64), colind (int32), vals (float64)."""
+    o = default_opts(**opts)
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+    va = _f64(A.vals)
+    h = C.c_void_p()
+    _check(LIB.pp_create(C.byref(h), int(A.n), rp.ctypes.data_as(_I64), ci.ctypes.data_as(C.POINTER(C.c_int32)),
+                         _dp(va), C.byref(o)))
+    return Context(h.value, int(A.n), o.precision)
+
+
+def pp_matrix_info(ctx: Context) -> tuple[float, float]:
+    a, s = C.c_double(), C.c_double()
+    _check(LIB.pp_matrix_info(ctx.handle, C.byref(a), C.byref(s)))
+    return a.value, s.value
+
+
+def pp_launch_count(ctx: Context) -> int:
+    return int(LIB.pp_launch_count(ctx.handle))
+
+
+def pp_build_poly(ctx: Context, d: int, b) -> Poly:
+    b = _f64(b)
+    h = C.c_void_p()
+    st = _check(LIB.pp_build_poly(ctx.handle, int(d), _dp(b), C.byref(h)), allow=(PP_OK, PP_EBREAKDOWN))
+    return Poly(h.value, ctx, st)
+
+
+def pp_build_poly2(ctx: Context, d1: int, d2: int, b) -> Poly:
+    b = _f64(b)
+    h = C.c_void_p()
+    st = _check(LIB.pp_build_poly2(ctx.handle, int(d1), int(d2), _dp(b), C.byref(h)), allow=(PP_OK, PP_EBREAKDOWN))
+    return Poly(h.value, ctx, st)
+
+
+def pp_poly_from_roots(ctx: Context, roots) -> Poly:
+    r = np.asarray(roots, dtype=complex)
+    re, im = _f64(r.real), _f64(r.imag)
+    h = C.c_void_p()
+    _check(LIB.pp_poly_from_roots(ctx.handle, int(r.size), _dp(re), _dp(im), C.byref(h)))
+    return Poly(h.value, ctx, PP_OK)
+
+
+def _roots(fn, p: Poly) -> np.ndarray:
+    cnt = C.c_int()
+    _check(fn(p.handle, None, None, 0, C.byref(cnt)))
+    re = np.zeros(max(cnt.value, 1))
+    im = np.zeros(max(cnt.value, 1))
+    _check(fn(p.handle, _dp(re), _dp(im), cnt.value, C.byref(cnt)))
+    return (re + 1j * im)[: cnt.value]
+
+
+def pp_poly_roots(p: Poly) -> np.ndarray:
+    return _roots(LIB.pp_poly_roots, p)
+
+
+def pp_poly_inner_roots(p: Poly) -> np.ndarray:
+    return _roots(LIB.pp_poly_inner_roots, p)
+
+
+def pp_poly_info(p: Poly) -> tuple[int, int]:
+    d, a = C.c_int(), C.c_int()
+    _check(LIB.pp_poly_info(p.handle, C.byref(d), C.byref(a)))
+    return d.value, a.value
+
+
+def pp_poly_counts(p: Poly) -> dict:
+    m, d, v = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(LIB.pp_poly_counts(p.handle, C.byref(m), C.byref(d), C.byref(v)))
+    return dict(mvps=m.value, dots=d.value, vops=v.value)
+
+
+def pp_apply(p: Poly, x_dev: int, y_dev: int) -> None:
+    """y = pi(A) x on device pointers (context storage type, asynchronous on its stream)."""
+    _check(LIB.pp_apply(p.handle, C.c_void_p(int(x_dev)), C.c_void_p(int(y_dev))))
+
+
+def pp_apply_host(p: Poly, x) -> np.ndarray:
+    x = _f64(x)
+    y = np.empty_like(x)
+    _check(LIB.pp_apply_host(p.handle, _dp(x), _dp(y)))
+    return y
+
+
+@dataclass
+class EigsResult:
+    lam: np.ndarray
+    X: np.ndarray | None
+    resid: np.ndarray
+    status: int
+    stats: dict
+
+
+def pp_eigs(ctx: Context, p: Poly | None, nev: int, m: int, k: int, rtol: float, v0=None,
+            want_vectors: bool = True) -> EigsResult:
+    n = ctx.n
+    cap = nev + 1
+    lre, lim, res = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+    X = np.zeros((cap, n)) if want_vectors else None
+    v0a = _f64(v0) if v0 is not None else None
+    nout = C.c_int()
+    st = pp_stats()
+    status = _check(LIB.pp_eigs(ctx.handle, p.handle if p is not None else None, int(nev), int(m), int(k),
+                                float(rtol), _dp(v0a) if v0a is not None else None, _dp(lre), _dp(lim),
+                                _dp(X) if X is not None else None, _dp(res), C.byref(nout), C.byref(st)),
+                    allow=(PP_OK, PP_ENOTCONV))
+    k_ = nout.value
+    return EigsResult(lre[:k_] + 1j * lim[:k_], X[:k_].T.copy() if X is not None else None, res[:k_], status,
+                      st.to_dict())
+
+
+# ---------------------------------------------------------------------------
+# Host FP64 dense steps (no GPU needed)
+# ---------------------------------------------------------------------------
+def pp_dense_eig(A: np.ndarray, vectors: bool = True):
+    A = np.asfortranarray(A, dtype=np.float64)
+    n = A.shape[0]
+    wr, wi = np.zeros(n), np.zeros(n)
+    V = np.zeros((n, n), order="F") if vectors else None
+    _check(LIB.pp_dense_eig(n, A.ctypes.data_as(_D), n, _dp(wr), _dp(wi),
+                            V.ctypes.data_as(_D) if V is not None else None, n))
+    return wr + 1j * wi, V
+
+
+def pp_harmonic_ritz(H: np.ndarray) -> np.ndarray:
+    H = np.asfortranarray(H, dtype=np.float64)
+    d = H.shape[1]
+    re, im = np.zeros(d), np.zeros(d)
+    _check(LIB.pp_harmonic_ritz(d, H.ctypes.data_as(_D), H.shape[0], _dp(re), _dp(im)))
+    return re + 1j * im
+
+
+def pp_leja_order(roots) -> np.ndarray:
+    r = np.asarray(roots, dtype=complex)
+    re, im = _f64(r.real), _f64(r.imag)
+    ore, oim = np.zeros(r.size), np.zeros(r.size)
+    _check(LIB.pp_leja_order(r.size, _dp(re), _dp(im), _dp(ore), _dp(oim)))
+    return ore + 1j * oim
+
+
+def pp_add_stability_roots(roots) -> np.ndarray:
+    r = np.asarray(roots, dtype=complex)
+    re, im = _f64(r.real), _f64(r.imag)
+    cap = 8 * r.size + 8
+    ore, oim = np.zeros(cap), np.zeros(cap)
+    cnt = C.c_int()
+    _check(LIB.pp_add_stability_roots(r.size, _dp(re), _dp(im), cap, _dp(ore), _dp(oim), C.byref(cnt)))
+    return (ore + 1j * oim)[: cnt.value]

@@ -1,0 +1,129 @@
+"""GPU parity of the factored polynomial apply (Eq. (2.1)) and the double
+polynomial (Section 8) against the oracle, through the C-ABI.
+
+Both sides apply the same root list to the same seeded vector, so the results
+agree up to FP64 rounding order.  Tolerance: the forward error of the product
+form is bounded by u times the sum over factors of |1/theta_i| ||A - sigma I||_inf
+||p_{i-1}||_inf (each factor's SpMV and axpy), times a small constant for the
+per-row accumulation; the bound is computed from the oracle's own intermediates.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_08020_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+U = np.finfo(np.float64).eps / 2
+
+
+def _bound(A, sigma, roots, x):
+    """u * 64 * sum_i (1 + |c_i| ||A||_inf) ||p_{i-1}||_inf over the factors (pairs: two passes)."""
+    Ainf = float(abs(A).sum(axis=1).max()) + abs(sigma)
+    op = O.Operator(A, sigma, O.Counters())
+    p = x.copy()
+    tot = 0.0
+    i = 0
+    while i < roots.size:
+        th = roots[i]
+        if th.imag == 0:
+            tot += (1 + Ainf / abs(th)) * np.abs(p).max()
+            p = p - op(p) / th.real
+            i += 1
+        else:
+            m2 = abs(th) ** 2
+            t = op(p)
+            tot += (1 + 2 * abs(th.real) * Ainf / m2 + Ainf**2 / m2) * np.abs(p).max() + np.abs(t).max()
+            p = p - (2 * th.real / m2) * t + op(t) / m2
+            i += 2
+    return 64 * U * tot
+
+
+CASES = {
+    "cd_n2500": lambda: inputs.plain_small()["A"],
+    "cd_complex": lambda: inputs.convection_diffusion_2d(30, 200.0),
+    "banded": lambda: inputs.banded_random(3001, 7, 1),
+    "ex7": lambda: inputs.diagonal(inputs.example7_diag()),
+    "ragged_n37": lambda: inputs.banded_random(37, 2, 3),
+}
+
+
+@pytest.mark.parametrize("fmt", ["auto", "csr"])
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("d", [1, 7, 20])
+def test_apply_matches_oracle(case, d, fmt):
+    from paper_1806_08020_gb300 import pp
+    Acsr = CASES[case]()
+    A = O.to_scipy(Acsr)
+    n = Acsr.n
+    sigma = O.gershgorin_shift(A)
+    P = O.build_poly(O.Operator(A, sigma, O.Counters()), inputs.start_vector(n, 5, 0), min(d, n - 1),
+                     O.Counters())
+    ctx = pp.pp_create(Acsr, target=pp.PP_TARGET_SR,
+                       format=pp.PP_FMT_CSR if fmt == "csr" else pp.PP_FMT_AUTO)
+    assert pp.pp_matrix_info(ctx)[1] == sigma
+    poly = pp.pp_poly_from_roots(ctx, P.roots)
+    x = inputs.start_vector(n, 6, 0)
+    y = pp.pp_apply_host(poly, x)
+    ref, _ = O.apply_poly(O.Operator(A, sigma, O.Counters()), P.roots, x)
+    err = np.abs(y - ref).max()
+    assert err <= _bound(A, sigma, P.roots, x), (err, _bound(A, sigma, P.roots, x))
+
+
+def test_apply_device_pointers_and_inplace():
+    import torch
+    from paper_1806_08020_gb300 import pp
+    Acsr = inputs.plain_small()["A"]
+    A = O.to_scipy(Acsr)
+    P = O.build_poly(O.Operator(A, 0.0, O.Counters()), inputs.start_vector(2500, 1, 0), 10, O.Counters())
+    ctx = pp.pp_create(Acsr, stream=torch.cuda.current_stream().cuda_stream)
+    poly = pp.pp_poly_from_roots(ctx, P.roots)
+    x = inputs.start_vector(2500, 2, 0)
+    ref, _ = O.apply_poly(O.Operator(A, 0.0, O.Counters()), P.roots, x)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(xd)
+    pp.pp_apply(poly, xd.data_ptr(), yd.data_ptr())
+    torch.cuda.synchronize()
+    tol = _bound(A, 0.0, P.roots, x)
+    assert np.abs(yd.cpu().numpy() - ref).max() <= tol
+    assert np.array_equal(xd.cpu().numpy(), x)  # input untouched
+    pp.pp_apply(poly, xd.data_ptr(), xd.data_ptr())  # in place
+    torch.cuda.synchronize()
+    assert np.abs(xd.cpu().numpy() - ref).max() <= tol
+
+
+def test_apply_pairs_on_diagonal_exact():
+    """Conjugate pairs in real arithmetic: pi(D) x = pi(lambda_i) x_i."""
+    from paper_1806_08020_gb300 import pp
+    lam = np.linspace(0.5, 3.0, 1000)
+    roots = O.modified_leja(np.array([2.5, 1.0 + 0.5j, 1.0 - 0.5j, 0.7, 2.0 + 1.5j, 2.0 - 1.5j]))
+    ctx = pp.pp_create(inputs.diagonal(lam), target=pp.PP_TARGET_SM)
+    poly = pp.pp_poly_from_roots(ctx, roots)
+    x = inputs.start_vector(1000, 4, 0)
+    y = pp.pp_apply_host(poly, x)
+    assert np.allclose(y, O.poly_eval(roots, lam).real * x, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("d1,d2", [(3, 4), (5, 6)])
+def test_double_poly_apply_matches_oracle(d1, d2):
+    """GPU double polynomial: roots as sets vs the oracle's build, and the apply of
+    the GPU's own roots vs the oracle's apply of the same roots."""
+    from paper_1806_08020_gb300 import pp
+    lam = np.concatenate([np.linspace(0.05, 1.0, 300), np.linspace(2.0, 50.0, 1700)])
+    Acsr = inputs.diagonal(lam)
+    A = O.to_scipy(Acsr)
+    b = inputs.start_vector(lam.size, 9, 0)
+    ctx = pp.pp_create(Acsr, target=pp.PP_TARGET_SM)
+    poly = pp.pp_build_poly2(ctx, d1, d2, b)
+    outer, inner = pp.pp_poly_roots(poly), pp.pp_poly_inner_roots(poly)
+    ref = O.build_double_poly(O.Operator(A, 0.0, O.Counters()), b, d1, d2, O.Counters())
+    for got, want in ((inner, ref.inner.roots), (outer, ref.roots)):
+        assert got.size == want.size
+        for z in want:
+            assert np.min(np.abs(got - z)) <= 1e-8 * abs(z)
+    x = inputs.start_vector(lam.size, 9, 1)
+    y = pp.pp_apply_host(poly, x)
+    tau = 1 - O.poly_eval(inner, lam)
+    want = (O.poly_eval(outer, tau) * x).real
+    assert np.abs(y - want).max() <= 1e-10 * np.abs(x).max()
