@@ -87,7 +87,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = []
         for i, nm in enumerate(names):
-            if any("Active" in r[5 + i] for r in rows if len(r) > 5 + i):
+            if any(r[5 + i].strip() == "Active" for r in rows if len(r) > 5 + i):
                 reasons.append(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
@@ -231,7 +231,6 @@ def run_ours(args, ws, rank, local):
     row_len = np.diff(A.rowptr)
     nnz_padded = int(np.sum(np.maximum.reduceat(row_len, np.arange(0, n, 32))) * 32)
     bytes_apply, launches_apply = _step_bytes(n, nnz_padded, nslices, roots)
-    applies_total = sum(c for c in [0])  # placeholder replaced below
     # number of applies per solve: m + (cycles - 1) (m - k); t_apply covers all of them
     applies_total = sum(cfg["m"] + (c - 1) * (cfg["m"] - cfg["k"]) for c in cycles)
     achieved_gbs = bytes_apply * applies_total / t_apply / 1e9

@@ -187,6 +187,19 @@ pp_status pp_eigs(pp_ctx *ctx, const pp_poly *p, int nev, int m, int k, double r
                   const double *v0, double *lam_re, double *lam_im, double *X, double *resid,
                   int *nout, pp_stats *stats);
 
+/*
+ * pp_orthogonalize — one Arnoldi orthogonalisation step (Section 4: classical
+ * Gram-Schmidt followed by one reorthogonalisation pass, CGS2): with the j
+ * orthonormal columns of V (device, column major, leading dimension ldv >= n,
+ * context storage type) and w (device, n), computes h1 = V^T w, w1 = w - V h1,
+ * h2 = V^T w1, w2 = w1 - V h2, and writes v = w2 / ||w2|| to v_dev (device, n;
+ * may not alias V or w).  w is overwritten by w1.  h_host (host, j + 1
+ * doubles) receives h1 + h2 followed by ||w2||.  Synchronises the stream.
+ * Requires 1 <= j <= 128.
+ */
+pp_status pp_orthogonalize(pp_ctx *ctx, const void *V_dev, int64_t ldv, int j, void *w_dev, void *v_dev,
+                           double *h_host);
+
 /* ----- Host FP64 dense steps (no GPU needed; used by the calls above) ----- */
 
 /*

@@ -8,7 +8,7 @@
 // The host synchronises once per polynomial build and once per cycle, where
 // the small dense FP64 steps run (harmonic Ritz roots, Leja order, Ritz
 // values, restart basis).
-#include "pp_internal.h"
+#include "ctx.h"
 
 #include <cuda_runtime.h>
 
@@ -21,7 +21,6 @@
 #include <string>
 #include <vector>
 
-using ppd::cd;
 
 static thread_local std::string g_last_error;
 
@@ -35,88 +34,7 @@ pp_status pp_fail(pp_status s, const char *fmt, ...) {
     return s;
 }
 
-#define CK(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess)                                                                     \
-            return pp_fail(e_ == cudaErrorMemoryAllocation ? PP_ENOMEM : PP_ECUDA, "%s: %s (%s:%d)", \
-                           #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
-    } while (0)
-
-#define CKS(expr)                          \
-    do {                                   \
-        pp_status s_ = (expr);             \
-        if (s_ < 0) return s_;             \
-    } while (0)
-
-namespace {
-
-struct StepCoef {
-    int pair;      // 0: real root, 1: conjugate pair
-    double c;      // real: 1/theta
-    double c1, c2; // pair: 2 Re(theta)/|theta|^2, 1/|theta|^2
-};
-
-std::vector<StepCoef> steps_of(const std::vector<cd> &roots) {
-    std::vector<StepCoef> s;
-    for (size_t i = 0; i < roots.size();) {
-        cd t = roots[i];
-        if (t.imag() == 0.0) {
-            s.push_back({0, 1.0 / t.real(), 0, 0});
-            i += 1;
-        } else {
-            double m2 = t.real() * t.real() + t.imag() * t.imag();
-            s.push_back({1, 0, 2.0 * t.real() / m2, 1.0 / m2});
-            i += 2;
-        }
-    }
-    return s;
-}
-
-int mvps_of(const std::vector<StepCoef> &s) {
-    int m = 0;
-    for (auto &x : s) m += x.pair ? 2 : 1;
-    return m;
-}
-
-double now() {
-    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
-
-}  // namespace
-
-struct pp_ctx {
-    int64_t n = 0, nnz = 0;
-    pp_opts opts{};
-    double norm1 = 0, sigma = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    ppk::Matrix A;     // storage precision (shifted operator uses sigma)
-    ppk::Matrix A64;   // FP64 copy for residuals on A (same as A in FP64 mode)
-    size_t esz = 8;    // bytes per stored vector element
-    std::vector<void *> allocs;
-    // scratch
-    void *vec[8] = {};
-    double *d_part = nullptr;
-    size_t part_cap = 0;
-    unsigned *d_ticket = nullptr;
-    double *d_small = nullptr;  // h1, h2, scal, misc (4 * 256 doubles)
-    int64_t launches = 0;
-    int64_t ldv() const { return (n + 31) / 32 * 32; }
-};
-
-struct pp_poly {
-    pp_ctx *ctx = nullptr;
-    std::vector<cd> roots;
-    std::vector<StepCoef> steps;
-    int degree = 0, added = 0;
-    bool breakdown = false;
-    pp_poly *inner = nullptr;  // pi_1 for a double polynomial (tau = 1 - pi_1)
-    int64_t mvps = 0, dots = 0, vops = 0;  // work of the GMRES build(s)
-    ~pp_poly() { delete inner; }
-};
-
-namespace {
+namespace ppi {
 
 pp_status dmalloc(pp_ctx *c, void **p, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -127,6 +45,12 @@ pp_status dmalloc(pp_ctx *c, void **p, size_t bytes) {
     }
     c->allocs.push_back(*p);
     return PP_OK;
+}
+
+void dfree(pp_ctx *c, void *p) {
+    if (!p) return;
+    cudaFree(p);
+    c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), p), c->allocs.end());
 }
 
 pp_status check_launch(pp_ctx *c) {
@@ -299,9 +223,9 @@ pp_status ensure_part(pp_ctx *c, size_t doubles) {
 }
 
 // CGS2 of w against V[:, 0..j) -> V[:, j] normalised, H[0..j, col] on the device.
-pp_status cgs2_step(pp_ctx *c, void *V, int64_t ldv, int j, void *w, double *hcol) {
+pp_status cgs2_step(pp_ctx *c, ppk::Prec pr, void *V, int64_t ldv, int j, void *w, double *hcol) {
     double *h1 = c->d_small, *h2 = c->d_small + 256, *scal = c->d_small + 512, *nrm = c->d_small + 513;
-    ppk::Prec pr = c->A.prec;
+    const size_t esz = pr == ppk::F64 ? 8 : 4;
     ppk::CgsArgs a;
     a.n = (int)c->n;
     a.V = V;
@@ -326,31 +250,28 @@ pp_status cgs2_step(pp_ctx *c, void *V, int64_t ldv, int j, void *w, double *hco
     a.mode = 2;
     a.h = h2;
     a.h1 = h1;
-    a.wout = (char *)V + (size_t)j * ldv * c->esz;
+    a.wout = (char *)V + (size_t)j * ldv * esz;
     a.out = nrm;
     a.hcol = hcol;
     a.scal = scal;
     ppk::launch_cgs(pr, a, c->stream);
     CKS(check_launch(c));
-    ppk::launch_scale(pr, (int)c->n, (char *)V + (size_t)j * ldv * c->esz, scal, c->stream);
+    ppk::launch_scale(pr, (int)c->n, (char *)V + (size_t)j * ldv * esz, scal, c->stream);
     return check_launch(c);
 }
 
-struct Timers {
-    std::vector<cudaEvent_t> ev;
-    size_t used = 0;
-    cudaEvent_t get() {
-        if (used == ev.size()) {
-            cudaEvent_t e;
-            cudaEventCreate(&e);
-            ev.push_back(e);
-        }
-        return ev[used++];
+cudaEvent_t Timers::get() {
+    if (used == ev.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ev.push_back(e);
     }
-    ~Timers() {
-        for (auto e : ev) cudaEventDestroy(e);
-    }
-};
+    return ev[used++];
+}
+
+Timers::~Timers() {
+    for (auto e : ev) cudaEventDestroy(e);
+}
 
 // Extend the Arnoldi decomposition from column j0 to m (Section 4): each step
 // w = Op(v_j), CGS2, v_{j+1}.  H is (m+1) x m column major on the device.
@@ -371,7 +292,7 @@ pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, voi
             e1 = tm->get();
             CK(cudaEventRecord(e1, c->stream));
         }
-        CKS(cgs2_step(c, V, ldv, j + 1, W, dH + (size_t)j * ldh));
+        CKS(cgs2_step(c, c->A.prec, V, ldv, j + 1, W, dH + (size_t)j * ldh));
         if (tm) {
             e2 = tm->get();
             CK(cudaEventRecord(e2, c->stream));
@@ -408,9 +329,9 @@ pp_status upload_vec(pp_ctx *c, const double *h, double s, void *d) {
     return PP_OK;
 }
 
-pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vector<double> &out) {
+pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vector<double> &out, ppk::Prec pr) {
     out.resize((size_t)c->n * cols);
-    if (c->A.prec == ppk::F64) {
+    if (pr == ppk::F64) {
         CK(cudaMemcpy2DAsync(out.data(), c->n * 8, d, ld * 8, c->n * 8, cols, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     } else {
@@ -515,7 +436,9 @@ pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, 
     return brk ? PP_EBREAKDOWN : PP_OK;
 }
 
-}  // namespace
+}  // namespace ppi
+
+using namespace ppi;
 
 // ===========================================================================
 extern "C" {
@@ -679,6 +602,48 @@ pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_
 
 int64_t pp_launch_count(const pp_ctx *c) { return c ? c->launches : 0; }
 
+pp_status pp_orthogonalize(pp_ctx *c, const void *V, int64_t ldv, int j, void *w, void *v, double *h_host) {
+    if (!c || !V || !w || !v || !h_host || j < 1 || j > 128 || ldv < c->n)
+        return pp_fail(PP_EINVAL, "pp_orthogonalize: bad arguments");
+    // the CGS2 passes read V[:, 0..j) and write the result as column j of a
+    // basis; here the result goes to v: run the passes with a one-column shim
+    double *dh = c->d_small + 1024;  // j+1 doubles of H column
+    ppk::Prec pr = c->A.prec;
+    double *h1 = c->d_small, *h2 = c->d_small + 256, *scal = c->d_small + 512, *nrm = c->d_small + 513;
+    ppk::CgsArgs a;
+    a.n = (int)c->n;
+    a.V = V;
+    a.ldv = ldv;
+    a.j = j;
+    a.part = c->d_part;
+    a.ticket = c->d_ticket;
+    a.mode = 0;
+    a.w = w;
+    a.out = h1;
+    ppk::launch_cgs(pr, a, c->stream);
+    CKS(check_launch(c));
+    a.mode = 1;
+    a.h = h1;
+    a.wout = w;
+    a.out = h2;
+    ppk::launch_cgs(pr, a, c->stream);
+    CKS(check_launch(c));
+    a.mode = 2;
+    a.h = h2;
+    a.h1 = h1;
+    a.wout = v;
+    a.out = nrm;
+    a.hcol = dh;
+    a.scal = scal;
+    ppk::launch_cgs(pr, a, c->stream);
+    CKS(check_launch(c));
+    ppk::launch_scale(pr, (int)c->n, v, scal, c->stream);
+    CKS(check_launch(c));
+    CK(cudaMemcpyAsync(h_host, dh, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PP_OK;
+}
+
 pp_status pp_matrix_info(const pp_ctx *c, double *norm1, double *sigma) {
     if (!c) return pp_fail(PP_EINVAL, "pp_matrix_info: null context");
     if (norm1) *norm1 = c->norm1;
@@ -805,401 +770,10 @@ pp_status pp_apply_host(const pp_poly *p, const double *x, double *y) {
     pp_status st = upload_vec(c, x, 1.0, dx);
     if (st >= 0) st = op_apply(c, p, dx, dx);
     std::vector<double> out;
-    if (st >= 0) st = download_vecs(c, dx, c->ldv(), 1, out);
+    if (st >= 0) st = download_vecs(c, dx, c->ldv(), 1, out, c->A.prec);
     cudaFree(dx);
     if (st < 0) return st;
     std::memcpy(y, out.data(), c->n * 8);
-    return PP_OK;
-}
-
-// ---------------------------------------------------------------------------
-// Thick-restarted Arnoldi(m, k) on Op (Section 2 box step 2; Section 4)
-// ---------------------------------------------------------------------------
-pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k, double rtol, const double *v0, double *lam_re,
-                  double *lam_im, double *X, double *resid, int *nout, pp_stats *stats) {
-    double t_start = now();
-    if (!c || nev < 1 || k <= nev || m <= k || m >= c->n || m > 127 || !lam_re || !lam_im || !resid || !nout)
-        return pp_fail(PP_EINVAL, "pp_eigs: need 1 <= nev < k < m < n, m <= 127 and output arrays");
-    if (!(rtol > 0)) return pp_fail(PP_EINVAL, "pp_eigs: rtol must be positive");
-    const int64_t n = c->n, ldv = c->ldv();
-    const size_t esz = c->esz;
-    const double target = p ? 1.0 : 0.0;
-    pp_stats S{};
-    int64_t launches0 = c->launches;
-    std::vector<void *> mine;
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(c->stream);
-        for (void *q : mine) {
-            cudaFree(q);
-            c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), q), c->allocs.end());
-        }
-    };
-    pp_status st;
-    void *V = nullptr, *V2 = nullptr, *Y = nullptr, *AY = nullptr, *W = c->vec[6];
-    double *dH = nullptr, *dQ = nullptr, *dq = nullptr, *dmu = nullptr;
-    int *dpartner = nullptr;
-    const int ldh = m + 1;
-    const int wcap = nev + 1;
-#define ALLOC(ptr, bytes)                                             \
-    do {                                                              \
-        if ((st = dmalloc(c, (void **)&(ptr), (bytes))) < 0) {        \
-            cleanup();                                                \
-            return st;                                                \
-        }                                                             \
-        mine.push_back((void *)(ptr));                                \
-    } while (0)
-    ALLOC(V, (size_t)ldv * (m + 1) * esz);
-    ALLOC(V2, (size_t)ldv * (m + 1) * esz);
-    ALLOC(Y, (size_t)ldv * (wcap + 1) * esz);
-    ALLOC(AY, (size_t)ldv * (wcap + 1) * esz);
-    ALLOC(dH, (size_t)ldh * m * 8);
-    ALLOC(dQ, (size_t)m * m * 8);
-    ALLOC(dq, (size_t)4 * (wcap + 1) * 8);
-    ALLOC(dmu, (size_t)3 * (wcap + 1) * 8);
-    ALLOC(dpartner, (size_t)(wcap + 1) * 4);
-#undef ALLOC
-    if (p && p->inner) W = c->vec[0];  // the double apply uses vec[1..7]; W must not alias them
-    if ((st = ensure_part(c, std::max((size_t)ppk::cgs_grid((int)n) * 130, (size_t)(wcap + 1) * 3 * 1024))) < 0) {
-        cleanup();
-        return st;
-    }
-    // start vector
-    std::vector<double> v0h(n, 1.0);
-    if (v0) std::copy(v0, v0 + n, v0h.begin());
-    double nv = 0;
-    for (double x : v0h) nv += x * x;
-    nv = std::sqrt(nv);
-    if (!(nv > 0) || !std::isfinite(nv)) {
-        cleanup();
-        return pp_fail(PP_EINVAL, "pp_eigs: start vector is zero or not finite");
-    }
-    if ((st = upload_vec(c, v0h.data(), 1.0 / nv, V)) < 0) {
-        cleanup();
-        return st;
-    }
-    cudaMemsetAsync(dH, 0, (size_t)ldh * m * 8, c->stream);
-    S.dots += 1;
-    S.vops += 2;
-    const int64_t opm = op_mvps(p);
-    const int64_t opv = op_vops(p);
-    Timers tm;
-    std::vector<std::pair<int, int>> marks;
-    std::vector<double> H((size_t)ldh * m), Hm((size_t)m * m), wr(m), wi(m), Sv((size_t)m * m);
-    std::vector<double> best_lam_re, best_lam_im, best_res, best_X;
-    int best_nw = 0;
-    bool converged = false;
-    int j0 = 0;
-    int nw = nev;
-    std::vector<int> order;
-    std::vector<cd> nu(m);
-    std::vector<double> lre, lim, res;
-    std::vector<int> slot_col;  // Y column of each slot
-    std::vector<int> partner_out;
-    for (int64_t cycle = 1; cycle <= c->opts.max_cycles; ++cycle) {
-        S.cycles = cycle;
-        if ((st = arnoldi_extend(c, p, nullptr, V, ldv, dH, ldh, j0, m, W, &tm, &marks)) < 0) {
-            cleanup();
-            return st;
-        }
-        S.mvps += opm * (m - j0);
-        for (int j = j0; j < m; ++j) {
-            S.dots += 2 * (j + 1) + 1;
-            S.vops += 4 * (j + 1) + 2 + opv;
-        }
-        double th0 = now();
-        cudaError_t e = cudaMemcpyAsync(H.data(), dH, H.size() * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) {
-            cleanup();
-            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
-        }
-        accumulate_times(tm, marks, S.t_apply, S.t_orth);
-        for (double v : H)
-            if (!std::isfinite(v)) {
-                cleanup();
-                return pp_fail(PP_ENUMERIC, "pp_eigs: non-finite Hessenberg entry in cycle %lld", (long long)cycle);
-            }
-        for (int j = 0; j < m; ++j)
-            for (int i = 0; i < m; ++i) Hm[i + (size_t)j * m] = H[i + (size_t)j * ldh];
-        if (!ppd::dense_eig(m, Hm.data(), m, wr.data(), wi.data(), Sv.data(), m)) {
-            cleanup();
-            return pp_fail(PP_ENUMERIC, "pp_eigs: Ritz values: QR failed");
-        }
-        for (int i = 0; i < m; ++i) nu[i] = cd(wr[i], wi[i]);
-        order = ppd::ritz_order(nu, target);
-        nw = nev + (nu[order[nev - 1]].imag() > 0 ? 1 : 0);
-        // Ritz vectors of the wanted set: columns (Re, Im) of each pair once
-        std::vector<double> Sw((size_t)m * nw);
-        std::vector<int> partner(nw), kind(nw);
-        std::vector<double> sg(nw, 0.0);
-        slot_col.assign(nw, 0);
-        for (int s = 0; s < nw;) {
-            int i = order[s];
-            if (wi[i] == 0.0) {
-                std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &Sw[(size_t)s * m]);
-                partner[s] = s;
-                slot_col[s] = s;
-                s += 1;
-            } else {
-                // eigenvector of the im > 0 member: columns (Re, Im) at i (im > 0) or i-1
-                int base = wi[i] > 0 ? i : i - 1;
-                std::copy(&Sv[(size_t)base * m], &Sv[(size_t)base * m] + m, &Sw[(size_t)s * m]);
-                std::copy(&Sv[(size_t)(base + 1) * m], &Sv[(size_t)(base + 1) * m] + m, &Sw[(size_t)(s + 1) * m]);
-                partner[s] = s + 1;
-                partner[s + 1] = s;
-                sg[s] = 1.0;
-                sg[s + 1] = -1.0;
-                slot_col[s] = s;
-                slot_col[s + 1] = s + 1;
-                s += 2;
-            }
-        }
-        // Y = V_m Sw; AY = A Y (FP64 operator, unshifted); Rayleigh quotients and residuals
-        e = cudaMemcpyAsync(dQ, Sw.data(), Sw.size() * 8, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dpartner, partner.data(), nw * 4, cudaMemcpyHostToDevice, c->stream);
-        if (e != cudaSuccess) {
-            cleanup();
-            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
-        }
-        ppk::launch_rotate(c->A.prec, (int)n, V, ldv, m, dQ, nw, Y, ldv, c->stream);
-        if ((st = check_launch(c)) < 0) {
-            cleanup();
-            return st;
-        }
-        for (int s = 0; s < nw; ++s) {
-            ppk::StepArgs a;
-            a.x = (char *)Y + (size_t)s * ldv * esz;
-            a.y = (char *)AY + (size_t)s * ldv * esz;
-            a.plain = 1;
-            ppk::launch_step(c->A, a, c->stream);
-            if ((st = check_launch(c)) < 0) {
-                cleanup();
-                return st;
-            }
-        }
-        S.mvps += nw;
-        ppk::ColDotArgs cda;
-        cda.n = (int)n;
-        cda.nw = nw;
-        cda.Y = Y;
-        cda.AY = AY;
-        cda.ld = ldv;
-        cda.partner = dpartner;
-        cda.q = dq;
-        cda.part = c->d_part;
-        cda.ticket = c->d_ticket;
-        cda.mode = 0;
-        ppk::launch_coldots(c->A.prec, cda, c->stream);
-        if ((st = check_launch(c)) < 0) {
-            cleanup();
-            return st;
-        }
-        std::vector<double> q((size_t)4 * nw);
-        e = cudaMemcpyAsync(q.data(), dq, q.size() * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) {
-            cleanup();
-            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
-        }
-        // mu = y^H A y / y^H y per slot
-        std::vector<double> mu((size_t)3 * nw, 0.0), ynrm(nw);
-        lre.assign(nw, 0);
-        lim.assign(nw, 0);
-        for (int s = 0; s < nw;) {
-            if (partner[s] == s) {
-                double yy = q[4 * s], yay = q[4 * s + 1];
-                lre[s] = yay / yy;
-                lim[s] = 0;
-                ynrm[s] = yy;
-                s += 1;
-            } else {
-                int r = s, i = s + 1;
-                double yy = q[4 * r] + q[4 * i];
-                double mr = (q[4 * r + 1] + q[4 * i + 1]) / yy;
-                double mi = (q[4 * r + 2] - q[4 * i + 2]) / yy;
-                lre[r] = lre[i] = mr;
-                lim[r] = mi;
-                lim[i] = -mi;
-                ynrm[r] = ynrm[i] = yy;
-                s += 2;
-            }
-        }
-        // residual columns: Re part AYr - mr Yr + mi Yi, Im part AYi - mr Yi - mi Yr
-        for (int s = 0; s < nw; ++s) {
-            mu[s] = lre[s];
-            mu[nw + s] = (partner[s] == s) ? 0.0 : (sg[s] > 0 ? lim[s] : lim[partner[s]]);
-            mu[2 * nw + s] = sg[s];
-        }
-        e = cudaMemcpyAsync(dmu, mu.data(), mu.size() * 8, cudaMemcpyHostToDevice, c->stream);
-        if (e != cudaSuccess) {
-            cleanup();
-            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
-        }
-        cda.mode = 1;
-        cda.mur = dmu;
-        cda.mui = dmu + nw;
-        cda.sg = dmu + 2 * nw;
-        ppk::launch_coldots(c->A.prec, cda, c->stream);
-        if ((st = check_launch(c)) < 0) {
-            cleanup();
-            return st;
-        }
-        e = cudaMemcpyAsync(q.data(), dq, q.size() * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) {
-            cleanup();
-            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
-        }
-        res.assign(nw, 0);
-        bool all = true;
-        int nconv = 0;
-        for (int s = 0; s < nw;) {
-            if (partner[s] == s) {
-                res[s] = std::sqrt(std::max(q[4 * s + 3], 0.0) / ynrm[s]) / c->norm1;
-                nconv += res[s] <= rtol;
-                all = all && (res[s] <= rtol);
-                s += 1;
-            } else {
-                double r2 = (q[4 * s + 3] + q[4 * (s + 1) + 3]) / ynrm[s];
-                res[s] = res[s + 1] = std::sqrt(std::max(r2, 0.0)) / c->norm1;
-                nconv += 2 * (res[s] <= rtol);
-                all = all && (res[s] <= rtol);
-                s += 2;
-            }
-        }
-        for (double x : res)
-            if (!std::isfinite(x)) all = false;
-        S.nconv = nconv;
-        S.vops += (int64_t)4 * m * nw;
-        best_nw = nw;
-        partner_out = partner;
-        if (all || cycle == c->opts.max_cycles) {
-            converged = all;
-            S.t_restart += now() - th0;
-            break;
-        }
-        // thick restart: keep k (k-1 if a pair would split), Q_k = qr([Re, Im] of kept Ritz vectors)
-        int kk = (nu[order[k - 1]].imag() > 0) ? k - 1 : k;
-        std::vector<double> B((size_t)m * kk);
-        int col = 0;
-        for (int s = 0; s < kk; ++s) {
-            int i = order[s];
-            if (wi[i] == 0.0) {
-                std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &B[(size_t)col * m]);
-                col++;
-            } else if (wi[i] > 0) {
-                std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &B[(size_t)col * m]);
-                std::copy(&Sv[(size_t)(i + 1) * m], &Sv[(size_t)(i + 1) * m] + m, &B[(size_t)(col + 1) * m]);
-                col += 2;
-            }
-        }
-        std::vector<double> Q((size_t)m * kk);
-        ppd::thin_qr(m, kk, B.data(), Q.data());
-        e = cudaMemcpyAsync(dQ, Q.data(), Q.size() * 8, cudaMemcpyHostToDevice, c->stream);
-        if (e != cudaSuccess) {
-            cleanup();
-            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
-        }
-        ppk::launch_rotate(c->A.prec, (int)n, V, ldv, m, dQ, kk, V2, ldv, c->stream);
-        if ((st = check_launch(c)) < 0) {
-            cleanup();
-            return st;
-        }
-        e = cudaMemcpyAsync((char *)V2 + (size_t)kk * ldv * esz, (char *)V + (size_t)m * ldv * esz, n * esz,
-                            cudaMemcpyDeviceToDevice, c->stream);
-        if (e != cudaSuccess) {
-            cleanup();
-            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
-        }
-        std::swap(V, V2);
-        S.vops += (int64_t)m * kk;
-        // H_k = [Q^T H_m Q ; h_{m+1,m} e_m^T Q]
-        std::vector<double> HQ((size_t)m * kk, 0.0), Hn((size_t)ldh * m, 0.0);
-        for (int cc = 0; cc < kk; ++cc)
-            for (int r = 0; r < m; ++r) {
-                double s = 0;
-                for (int t = 0; t < m; ++t) s += Hm[r + (size_t)t * m] * Q[t + (size_t)cc * m];
-                HQ[r + (size_t)cc * m] = s;
-            }
-        for (int cc = 0; cc < kk; ++cc) {
-            for (int r = 0; r < kk; ++r) {
-                double s = 0;
-                for (int t = 0; t < m; ++t) s += Q[t + (size_t)r * m] * HQ[t + (size_t)cc * m];
-                Hn[r + (size_t)cc * ldh] = s;
-            }
-            Hn[kk + (size_t)cc * ldh] = H[m + (size_t)(m - 1) * ldh] * Q[(m - 1) + (size_t)cc * m];
-        }
-        e = cudaMemcpyAsync(dH, Hn.data(), Hn.size() * 8, cudaMemcpyHostToDevice, c->stream);
-        if (e != cudaSuccess) {
-            cleanup();
-            return pp_fail(PP_ECUDA, "pp_eigs: %s", cudaGetErrorString(e));
-        }
-        j0 = kk;
-        S.t_restart += now() - th0;
-    }
-    // outputs sorted by the target: SR -> (Re, |Im|, Im > 0 first); SM -> (|lam|, Re, Im > 0 first)
-    std::vector<int> srt(best_nw);
-    for (int s = 0; s < best_nw; ++s) srt[s] = s;
-    bool sr = c->opts.target == PP_TARGET_SR;
-    std::stable_sort(srt.begin(), srt.end(), [&](int a, int b) {
-        double ka = sr ? lre[a] : std::hypot(lre[a], lim[a]), kb = sr ? lre[b] : std::hypot(lre[b], lim[b]);
-        if (ka != kb) return ka < kb;
-        if (sr) {
-            if (std::fabs(lim[a]) != std::fabs(lim[b])) return std::fabs(lim[a]) < std::fabs(lim[b]);
-        } else if (lre[a] != lre[b]) {
-            return lre[a] < lre[b];
-        }
-        return lim[a] > lim[b];
-    });
-    std::vector<double> Yh;
-    if (X) {
-        if ((st = download_vecs(c, Y, ldv, best_nw, Yh)) < 0) {
-            cleanup();
-            return st;
-        }
-    }
-    double maxres = 0;
-    for (int s = 0; s < best_nw; ++s) {
-        int o = srt[s];
-        lam_re[s] = lre[o];
-        lam_im[s] = lim[o];
-        resid[s] = res[o];
-        maxres = std::max(maxres, res[o]);
-        if (X) {
-            // unit vector: a real slot, or the pair's (Re x, Im x) for the member with
-            // Im(lambda) > 0 (x = yr + i yi when Im(mu) > 0 for the Re column's quotient,
-            // its conjugate otherwise), both scaled by the complex norm
-            bool pair = partner_out[o] != o;
-            int cr = pair ? std::min(o, partner_out[o]) : o, ci = pair ? cr + 1 : o;
-            double nrm2 = 0;
-            for (int64_t i = 0; i < n; ++i) {
-                double a = Yh[(size_t)cr * n + i];
-                nrm2 += a * a;
-                if (pair) {
-                    double b = Yh[(size_t)ci * n + i];
-                    nrm2 += b * b;
-                }
-            }
-            double sc = 1.0 / std::sqrt(nrm2);
-            if (!pair) {
-                for (int64_t i = 0; i < n; ++i) X[(size_t)s * n + i] = Yh[(size_t)o * n + i] * sc;
-            } else {
-                bool first = lim[o] > 0 || (lim[o] == 0 && o == cr);
-                double sgn = (lim[cr] >= 0) ? 1.0 : -1.0;  // conj when the Re column's quotient has Im < 0
-                const double *src = first ? &Yh[(size_t)cr * n] : &Yh[(size_t)ci * n];
-                double f = first ? sc : sgn * sc;
-                for (int64_t i = 0; i < n; ++i) X[(size_t)s * n + i] = src[i] * f;
-            }
-        }
-    }
-    *nout = best_nw;
-    cleanup();
-    S.converged = converged ? 1 : 0;
-    S.max_resid = maxres;
-    S.kernel_launches = c->launches - launches0;
-    S.t_total = now() - t_start;
-    if (stats) *stats = S;
-    if (!converged) return pp_fail(PP_ENOTCONV, "pp_eigs: not converged in %d cycles", c->opts.max_cycles);
     return PP_OK;
 }
 

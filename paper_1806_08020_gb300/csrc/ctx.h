@@ -1,0 +1,126 @@
+// Private declarations shared by capi.cu (contexts, polynomials, applies)
+// and eigs.cu (the Arnoldi driver): the context and polynomial handles and
+// the device-side helpers both use.
+#pragma once
+
+#include "pp_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <complex>
+#include <utility>
+#include <vector>
+
+using ppd::cd;
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return pp_fail(e_ == cudaErrorMemoryAllocation ? PP_ENOMEM : PP_ECUDA, "%s: %s (%s:%d)", \
+                           #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+    } while (0)
+
+#define CKS(expr)                          \
+    do {                                   \
+        pp_status s_ = (expr);             \
+        if (s_ < 0) return s_;             \
+    } while (0)
+
+
+namespace ppi {
+
+struct StepCoef {
+    int pair;      // 0: real root, 1: conjugate pair
+    double c;      // real: 1/theta
+    double c1, c2; // pair: 2 Re(theta)/|theta|^2, 1/|theta|^2
+};
+
+inline std::vector<StepCoef> steps_of(const std::vector<cd> &roots) {
+    std::vector<StepCoef> s;
+    for (size_t i = 0; i < roots.size();) {
+        cd t = roots[i];
+        if (t.imag() == 0.0) {
+            s.push_back({0, 1.0 / t.real(), 0, 0});
+            i += 1;
+        } else {
+            double m2 = t.real() * t.real() + t.imag() * t.imag();
+            s.push_back({1, 0, 2.0 * t.real() / m2, 1.0 / m2});
+            i += 2;
+        }
+    }
+    return s;
+}
+
+inline int mvps_of(const std::vector<StepCoef> &s) {
+    int m = 0;
+    for (auto &x : s) m += x.pair ? 2 : 1;
+    return m;
+}
+
+inline double now() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace ppi
+
+struct pp_ctx {
+    int64_t n = 0, nnz = 0;
+    pp_opts opts{};
+    double norm1 = 0, sigma = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    ppk::Matrix A;     // storage precision (shifted operator uses sigma)
+    ppk::Matrix A64;   // FP64 copy for residuals on A (same as A in FP64 mode)
+    size_t esz = 8;    // bytes per stored vector element
+    std::vector<void *> allocs;
+    // scratch
+    void *vec[8] = {};
+    double *d_part = nullptr;
+    size_t part_cap = 0;
+    unsigned *d_ticket = nullptr;
+    double *d_small = nullptr;  // h1, h2, scal, misc (4 * 256 doubles)
+    int64_t launches = 0;
+    int64_t ldv() const { return (n + 31) / 32 * 32; }
+};
+
+struct pp_poly {
+    pp_ctx *ctx = nullptr;
+    std::vector<cd> roots;
+    std::vector<ppi::StepCoef> steps;
+    int degree = 0, added = 0;
+    bool breakdown = false;
+    pp_poly *inner = nullptr;  // pi_1 for a double polynomial (tau = 1 - pi_1)
+    int64_t mvps = 0, dots = 0, vops = 0;  // work of the GMRES build(s)
+    ~pp_poly() { delete inner; }
+};
+
+
+namespace ppi {
+
+struct Timers {
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
+    cudaEvent_t get();
+    ~Timers();
+};
+
+pp_status dmalloc(pp_ctx *c, void **p, size_t bytes);
+void dfree(pp_ctx *c, void *p);
+pp_status check_launch(pp_ctx *c);
+pp_status step(pp_ctx *c, const ppk::StepArgs &s);
+pp_status op_apply(pp_ctx *c, const pp_poly *p, const void *x, void *y);
+pp_status op_tau(pp_ctx *c, const pp_poly *inner, const void *x, void *y);
+int64_t op_mvps(const pp_poly *p);
+int64_t op_vops(const pp_poly *p);
+int64_t vops_of(const std::vector<StepCoef> &s);
+pp_status ensure_part(pp_ctx *c, size_t doubles);
+pp_status cgs2_step(pp_ctx *c, ppk::Prec pr, void *V, int64_t ldv, int j, void *w, double *hcol);
+pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, void *V, int64_t ldv, double *dH,
+                         int ldh, int j0, int m, void *W, Timers *tm, std::vector<std::pair<int, int>> *marks);
+void accumulate_times(Timers &tm, std::vector<std::pair<int, int>> &marks, double &t_apply, double &t_orth);
+pp_status upload_vec(pp_ctx *c, const double *h, double s, void *d);
+pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vector<double> &out, ppk::Prec pr);
+
+}  // namespace ppi

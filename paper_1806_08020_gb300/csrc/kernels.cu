@@ -55,23 +55,52 @@ __device__ __forceinline__ void step_epilogue(int row, Acc u, const StepArgs &s)
     }
 }
 
+// Row sum u = sum_k A(row, col_k) x(col_k) over a SELL-32 slice row (the
+// slice width is warp-uniform).  Kept to ~30 registers so that 8 blocks of
+// 256 threads stay resident per SM: the gathers are latency-bound and need the
+// warps more than a wider unroll.
+template <typename T, typename V, typename Acc>
+__device__ __forceinline__ Acc sell_row(const SellView &A, const T *__restrict__ x, int row) {
+    const int sl = row >> 5, lane = row & 31;
+    const int beg = __ldg(A.slice_ptr + sl);
+    const int len = (__ldg(A.slice_ptr + sl + 1) - beg) >> 5;
+    const int *col = A.col + beg + lane;
+    const V *val = (const V *)A.val + beg + lane;
+    Acc acc = 0;
+#pragma unroll 4
+    for (int k = 0; k < len; ++k) acc = fma((Acc)__ldg(val + 32 * k), (Acc)__ldg(x + __ldg(col + 32 * k)), acc);
+    return acc;
+}
+
+// Specialised passes of the factored polynomial (the hot cases):
+//   KIND 0 plain:  y = u
+//   KIND 1 real:   y = x - a2 u                (a2 = 1/theta)
+//   KIND 2 pair 2: y = aux - a1 x - a2 u        (x = t, aux = p, a1 = c1, a2 = -c2)
+// with u = A x - sigma x when SIGMA.
+template <typename T, typename V, typename Acc, int KIND, bool SIGMA>
+__global__ void __launch_bounds__(kThreads) k_sell_pass(SellView A, StepArgs s) {
+    const int row = blockIdx.x * kThreads + threadIdx.x;
+    if (row >= A.n) return;
+    const T *x = (const T *)s.x;
+    Acc u = sell_row<T, V, Acc>(A, x, row);
+    if (SIGMA) u = fma(-(Acc)s.sigma, (Acc)x[row], u);
+    T *y = (T *)s.y;
+    if (KIND == 0) {
+        y[row] = (T)u;
+    } else if (KIND == 1) {
+        y[row] = (T)fma(-(Acc)s.a2, u, (Acc)x[row]);
+    } else {
+        Acc v = fma(-(Acc)s.a1, (Acc)x[row], (Acc)((const T *)s.aux)[row]);
+        y[row] = (T)fma(-(Acc)s.a2, u, v);
+    }
+}
+
+// General pass (running sum, optional output, outer epilogue): see StepArgs.
 template <typename T, typename V, typename Acc>
 __global__ void __launch_bounds__(kThreads) k_sell_step(SellView A, StepArgs s) {
     int row = blockIdx.x * kThreads + threadIdx.x;
     if (row >= A.n) return;
-    int sl = row >> 5, lane = row & 31;
-    int beg = __ldg(A.slice_ptr + sl), end = __ldg(A.slice_ptr + sl + 1);
-    int len = (end - beg) >> 5;
-    const int *col = A.col + beg + lane;
-    const V *val = (const V *)A.val + beg + lane;
-    const T *x = (const T *)s.x;
-    Acc acc = 0;
-#pragma unroll 4
-    for (int k = 0; k < len; ++k) {
-        Acc a = (Acc)__ldg(val + 32 * k);
-        int c = __ldg(col + 32 * k);
-        acc = fma(a, (Acc)__ldg(x + c), acc);
-    }
+    Acc acc = sell_row<T, V, Acc>(A, (const T *)s.x, row);
     step_epilogue<T, Acc>(row, acc, s);
 }
 
@@ -399,13 +428,38 @@ int num_sms() {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+template <typename T>
+static void sell_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    int blocks = (A.n + kThreads - 1) / kThreads;
+    const bool general = s.r || s.oy || !s.y;
+    const bool sig = s.sigma != 0.0;
+    if (general) {
+        k_sell_step<T, T, T><<<blocks, kThreads, 0, st>>>(A.sell, s);
+        return;
+    }
+    int kind = s.plain ? 0 : (s.aux ? 2 : 1);
+    if (!s.plain && !s.aux && s.a1 != 0.0) {  // not one of the specialised forms
+        k_sell_step<T, T, T><<<blocks, kThreads, 0, st>>>(A.sell, s);
+        return;
+    }
+#define PP_PASS(K, S) k_sell_pass<T, T, T, K, S><<<blocks, kThreads, 0, st>>>(A.sell, s)
+    if (kind == 0) {
+        if (sig) PP_PASS(0, true); else PP_PASS(0, false);
+    } else if (kind == 1) {
+        if (sig) PP_PASS(1, true); else PP_PASS(1, false);
+    } else {
+        if (sig) PP_PASS(2, true); else PP_PASS(2, false);
+    }
+#undef PP_PASS
+}
+
 void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st) {
     int blocks = (A.n + kThreads - 1) / kThreads;
     if (A.fmt == 2) {
         if (A.prec == F64)
-            k_sell_step<double, double, double><<<blocks, kThreads, 0, st>>>(A.sell, s);
+            sell_dispatch<double>(A, s, st);
         else
-            k_sell_step<float, float, float><<<blocks, kThreads, 0, st>>>(A.sell, s);
+            sell_dispatch<float>(A, s, st);
     } else {
         if (A.prec == F64)
             k_csr_step<double, double, double><<<blocks, kThreads, 0, st>>>(A.csr, s);
@@ -420,25 +474,40 @@ int cgs_grid(int n) {
     return tiles < g ? tiles : g;
 }
 
+// Blocks of a CGS pass: one wave of resident blocks (at most 4 per SM, which
+// bounds the partial-sum buffer), never more than there are tiles.
+template <typename T, int CPW>
+static int resident_grid(int n, int cap) {
+    static int per_sm = 0;  // one per instantiation
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs<T, CPW>, kThreads, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (per_sm > 4) per_sm = 4;
+    }
+    int tiles = (n + kRows - 1) / kRows;
+    int g = per_sm * num_sms();
+    if (cap > 0 && g > cap) g = cap;
+    return tiles < g ? tiles : g;
+}
+
 template <typename T>
-static void cgs_dispatch(const CgsArgs &a, cudaStream_t st) {
-    int g = cgs_grid(a.n);
+static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
     int cpw = (a.j + kWarps - 1) / kWarps;
     if (cpw <= 2)
-        k_cgs<T, 2><<<g, kThreads, 0, st>>>(a);
+        k_cgs<T, 2><<<resident_grid<T, 2>(a.n, cap), kThreads, 0, st>>>(a);
     else if (cpw <= 4)
-        k_cgs<T, 4><<<g, kThreads, 0, st>>>(a);
+        k_cgs<T, 4><<<resident_grid<T, 4>(a.n, cap), kThreads, 0, st>>>(a);
     else if (cpw <= 8)
-        k_cgs<T, 8><<<g, kThreads, 0, st>>>(a);
+        k_cgs<T, 8><<<resident_grid<T, 8>(a.n, cap), kThreads, 0, st>>>(a);
     else
-        k_cgs<T, 16><<<g, kThreads, 0, st>>>(a);
+        k_cgs<T, 16><<<resident_grid<T, 16>(a.n, cap), kThreads, 0, st>>>(a);
 }
 
 void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st) {
     if (p == F64)
-        cgs_dispatch<double>(a, st);
+        cgs_dispatch<double>(a, 0, st);
     else
-        cgs_dispatch<float>(a, st);
+        cgs_dispatch<float>(a, 0, st);
 }
 
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st) {

@@ -69,6 +69,7 @@ _SIGS = {
     "pp_apply_host": (C.c_int, [_P, _D, _D]),
     "pp_eigs": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D, _D, _I,
                           C.POINTER(pp_stats)]),
+    "pp_orthogonalize": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, _D]),
     "pp_dense_eig": (C.c_int, [C.c_int, _D, C.c_int, _D, _D, _D, C.c_int]),
     "pp_harmonic_ritz": (C.c_int, [C.c_int, _D, C.c_int, _D, _D]),
     "pp_leja_order": (C.c_int, [C.c_int, _D, _D, _D, _D]),
@@ -244,6 +245,14 @@ def pp_apply_host(p: Poly, x) -> np.ndarray:
     y = np.empty_like(x)
     _check(LIB.pp_apply_host(p.handle, _dp(x), _dp(y)))
     return y
+
+
+def pp_orthogonalize(ctx: Context, V_dev: int, ldv: int, j: int, w_dev: int, v_dev: int) -> np.ndarray:
+    """CGS2 of w against V[:, :j] on the device; returns h (j coefficients, then the norm)."""
+    h = np.zeros(j + 1)
+    _check(LIB.pp_orthogonalize(ctx.handle, C.c_void_p(int(V_dev)), int(ldv), int(j), C.c_void_p(int(w_dev)),
+                                C.c_void_p(int(v_dev)), _dp(h)))
+    return h
 
 
 @dataclass

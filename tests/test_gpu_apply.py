@@ -127,3 +127,29 @@ def test_double_poly_apply_matches_oracle(d1, d2):
     tau = 1 - O.poly_eval(inner, lam)
     want = (O.poly_eval(outer, tau) * x).real
     assert np.abs(y - want).max() <= 1e-10 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("n,j", [(37, 1), (1000, 7), (4099, 33), (100003, 51), (20000, 128)])
+def test_orthogonalize_matches_oracle_cgs2(n, j):
+    """CGS2 (Section 4) on the device vs the oracle's cgs2 on the same V and w."""
+    import torch
+    from paper_1806_08020_gb300 import pp
+    rng = np.random.default_rng(n + j)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, j)))
+    w = rng.standard_normal(n) + Q @ rng.standard_normal(j) * 10
+    ctx = pp.pp_create(inputs.diagonal(np.ones(n)), stream=torch.cuda.current_stream().cuda_stream)
+    ldv = (n + 31) // 32 * 32
+    Vd = torch.zeros((j, ldv), dtype=torch.float64, device="cuda")
+    Vd[:, :n] = torch.tensor(Q.T)
+    wd = torch.tensor(w, device="cuda")
+    vd = torch.empty(n, dtype=torch.float64, device="cuda")
+    h = pp.pp_orthogonalize(ctx, Vd.data_ptr(), ldv, j, wd.data_ptr(), vd.data_ptr())
+    w2, href = O.cgs2(Q, w, O.Counters())
+    nw = np.linalg.norm(w)
+    # each pass is a sum of n products: error <= n u ||V|| ||w|| per coefficient
+    tol = 4 * n * U * nw
+    assert np.abs(h[:j] - href).max() <= tol
+    assert abs(h[j] - np.linalg.norm(w2)) <= tol
+    v = vd.cpu().numpy()
+    assert np.abs(v - w2 / np.linalg.norm(w2)).max() <= tol / np.linalg.norm(w2) * 4
+    assert np.abs(Q.T @ v).max() <= 1e-12 * np.sqrt(n)
