@@ -200,6 +200,40 @@ pp_status pp_eigs(pp_ctx *ctx, const pp_poly *p, int nev, int m, int k, double r
 pp_status pp_orthogonalize(pp_ctx *ctx, const void *V_dev, int64_t ldv, int j, void *w_dev, void *v_dev,
                            double *h_host);
 
+/*
+ * pp_orthogonalize_noalloc — the CGS2 step of pp_orthogonalize for callers
+ * that cannot allocate device memory.  The paper has no counterpart: this is
+ * a deployment variant of the same computation.
+ *
+ * Who needs it: a caller whose device memory is owned by someone else (a
+ * host framework that reserves the whole GPU for its own caching allocator,
+ * so a cudaMalloc here would fail or fragment it), a latency-critical loop
+ * that cannot pay for cudaMalloc/cudaFree (they may synchronise the device),
+ * or a plugin that is not allowed to own device allocations.  Such a caller
+ * passes its inputs and outputs and creates no pp_ctx; this call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Computes, in FP64 and on the given stream (NULL = legacy default stream):
+ * with the j orthonormal columns of V_dev (n x j, column major, leading
+ * dimension ldv >= n) and w_dev (n), h1 = V^T w, w1 = w - V h1 (written back
+ * to w_dev), h2 = V^T w1, w2 = w1 - V h2; v_dev (n, not aliasing V or w)
+ * receives w2 / ||w2||; h_dev (device, j + 1 doubles) receives h1 + h2 and
+ * then ||w2||.  Asynchronous: nothing is copied to the host.
+ *
+ * Scratch: a file-scope __device__ array of about 636 KB (partial sums for at
+ * most 608 blocks x 130 values, the two coefficient vectors, the norm and the
+ * reduction ticket), held by every GPU that loads the library until the
+ * process exits.  Limits: 1 <= j <= 128 (beyond that PP_EINVAL with a
+ * message); n < 2^31.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call uses the same array and
+ * leaves the last call's contents in it (the ticket is cleared at the start
+ * of each call); calls that overlap on the GPU, e.g. on two streams, race on
+ * it, so issue them on one stream or otherwise serialise them.
+ */
+pp_status pp_orthogonalize_noalloc(int64_t n, const double *V_dev, int64_t ldv, int j, double *w_dev,
+                                   double *v_dev, double *h_dev, void *stream);
+
 /* ----- Host FP64 dense steps (no GPU needed; used by the calls above) ----- */
 
 /*

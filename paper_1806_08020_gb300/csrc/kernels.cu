@@ -510,6 +510,13 @@ void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st) {
         cgs_dispatch<float>(a, 0, st);
 }
 
+void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st) {
+    if (p == F64)
+        cgs_dispatch<double>(a, grid_cap, st);
+    else
+        cgs_dispatch<float>(a, grid_cap, st);
+}
+
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st) {
     int g = num_sms() * 4;
     if (p == F64)

@@ -107,6 +107,8 @@ struct CgsArgs {
 };
 int cgs_grid(int n);
 void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st);
+// as launch_cgs with at most grid_cap blocks (the partial sums need grid_cap * (j+1) doubles)
+void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st);
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st);
 
 // Out[:, c] = sum_r V[:, r] Q[r, c] (c < kk), Q column major m x kk on the device.

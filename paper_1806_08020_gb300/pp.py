@@ -70,6 +70,7 @@ _SIGS = {
     "pp_eigs": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _D, _D, _D, _D, _D, _I,
                           C.POINTER(pp_stats)]),
     "pp_orthogonalize": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, _D]),
+    "pp_orthogonalize_noalloc": (C.c_int, [C.c_int64, _P, C.c_int64, C.c_int, _P, _P, _P, _P]),
     "pp_dense_eig": (C.c_int, [C.c_int, _D, C.c_int, _D, _D, _D, C.c_int]),
     "pp_harmonic_ritz": (C.c_int, [C.c_int, _D, C.c_int, _D, _D]),
     "pp_leja_order": (C.c_int, [C.c_int, _D, _D, _D, _D]),
@@ -253,6 +254,13 @@ def pp_orthogonalize(ctx: Context, V_dev: int, ldv: int, j: int, w_dev: int, v_d
     _check(LIB.pp_orthogonalize(ctx.handle, C.c_void_p(int(V_dev)), int(ldv), int(j), C.c_void_p(int(w_dev)),
                                 C.c_void_p(int(v_dev)), _dp(h)))
     return h
+
+
+def pp_orthogonalize_noalloc(n: int, V_dev: int, ldv: int, j: int, w_dev: int, v_dev: int, h_dev: int,
+                             stream: int = 0) -> None:
+    """The CGS2 step without any allocation: every pointer is the caller's device memory."""
+    _check(LIB.pp_orthogonalize_noalloc(int(n), C.c_void_p(int(V_dev)), int(ldv), int(j), C.c_void_p(int(w_dev)),
+                                        C.c_void_p(int(v_dev)), C.c_void_p(int(h_dev)), C.c_void_p(int(stream))))
 
 
 @dataclass
