@@ -93,6 +93,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def merge_over_ranks(t: float, count: int, device) -> tuple[float, int]:
+    """Whole-job figures over replicas: the slowest rank's time and the sum of counts.
+
+    Each rank solves its own seeded instance (weak scaling); this reduction of
+    two scalars after the timed region is the only collective.
+    """
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return t, count
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    cc = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(cc, op=dist.ReduceOp.SUM)
+    return float(tt.item()), int(cc.item())
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Seed of rank r's instance: independent problems per replica."""
+    return base + 7919 * rank
+
+
 def _peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -157,7 +179,7 @@ def run_ours(args, ws, rank, local):
     cfg = inputs.plain_large()
     A = cfg["A"]
     n, nnz = A.n, A.nnz
-    seed = cfg["seed"] + 7919 * rank  # each rank its own instance
+    seed = rank_seed(cfg["seed"], rank)  # each rank its own instance
     b = inputs.start_vector(n, seed, 0)
     v0 = inputs.start_vector(n, seed, 1)
     stream = torch.cuda.Stream(device=dev)
@@ -194,12 +216,7 @@ def run_ours(args, ws, rank, local):
         barrier()
     launches = pp.pp_launch_count(ctx) - launches0
     t = ev0.elapsed_time(ev1) * 1e-3
-    if ws > 1:
-        tt = torch.tensor([t, pairs], dtype=torch.float64, device=dev)
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t, pairs = float(tmax[0]), int(tt[1])
+    t, pairs = merge_over_ranks(t, pairs, dev)
     value = pairs / t
 
     # end to end through the C-ABI from host buffers: upload, solve, vectors back
@@ -218,12 +235,7 @@ def run_ours(args, ws, rank, local):
         c2.close()
     barrier()
     te = time.perf_counter() - te0
-    if ws > 1:
-        tt = torch.tensor([te, e2e_pairs], dtype=torch.float64, device=dev)
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        te, e2e_pairs = float(tmax[0]), int(tt[1])
+    te, e2e_pairs = merge_over_ranks(te, e2e_pairs, dev)
 
     # roofline of the dominant kernel (fused SELL root step), event-timed over the region
     roots = pp.pp_poly_roots(poly)
@@ -253,6 +265,30 @@ def run_ours(args, ws, rank, local):
         roofline["peak"] = 6800.0
         roofline["frac"] = round(achieved_gbs / 6800.0, 4)
 
+    # the same workload with FP32 apply and basis and FP64 refinement on A
+    ctx32 = pp.pp_create(A, stream=stream.cuda_stream, precision=pp.PP_FP32)
+    def solve32():
+        p32 = pp.pp_build_poly(ctx32, cfg["d"], b)
+        return pp.pp_eigs(ctx32, p32, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=False)
+    for _ in range(max(1, args.warmup)):
+        solve32()
+    barrier()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mixed_pairs, mixed_res, mixed_cycles = 0, 0.0, []
+    m0.record(stream)
+    for _ in range(args.steps):
+        r32 = solve32()
+        mixed_pairs += int(np.sum(r32.resid <= cfg["rtol"])) if r32.status == 0 else 0
+        mixed_res = max(mixed_res, float(np.max(r32.resid)))
+        mixed_cycles.append(r32.stats["cycles"])
+    m1.record(stream)
+    barrier()
+    tm = m0.elapsed_time(m1) * 1e-3
+    out_mixed = {"value": round(mixed_pairs / tm, 3), "unit": UNIT, "ms_per_step": round(tm / args.steps * 1e3, 3),
+                 "precision": "FP32 apply/basis, FP64 residuals and refinement on A",
+                 "cycles_per_solve": mixed_cycles, "max_resid": mixed_res}
+    ctx32.close()
+
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
@@ -266,6 +302,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "clocks": clk.summary(),
+        "mixed_fp32": out_mixed,
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, seed, budget_s=args.cpu_budget, cycles=statistics.median(cycles))
@@ -325,6 +362,110 @@ def cpu_baseline(cfg, seed, budget_s=20.0, cycles=None):
             "seconds_per_solve_est": round(t_solve, 1)}
 
 
+def run_batch(args, ws, rank, local):
+    """64 uneven 2-D CD instances: batched mixed precision vs the plain FP64 method per instance."""
+    import torch
+
+    from paper_1806_08020_gb300 import pp
+
+    torch.cuda.set_device(local)
+    specs = inputs.batch_instances(count=args.instances)
+    mats = [inputs.convection_diffusion_2d(sp["N"], sp["beta"]) for sp in specs]
+    bs = [inputs.start_vector(A.n, sp["seed"] + 7919 * rank, 0) for A, sp in zip(mats, specs)]
+    vs = [inputs.start_vector(A.n, sp["seed"] + 7919 * rank, 1) for A, sp in zip(mats, specs)]
+    ds = [sp["d"] for sp in specs]
+    stream = torch.cuda.Stream()
+    B = pp.pp_batch_create(mats, precision=pp.PP_FP32, stream=stream.cuda_stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0 = pp.pp_batch_launch_count(B)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        status, res = pp.pp_batch_solve(B, ds, bs, vs, 8, 30, 13, 1e-8, want_vectors=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) * 1e-3
+    pairs = sum(int(np.sum(r.resid <= 1e-8)) for r in res if r.status == 0)
+    conv = sum(r.status == 0 for r in res)
+    launches = pp.pp_batch_launch_count(B) - l0
+    # the plain FP64 GPU method, one instance after the other
+    t64, pairs64, conv64 = 0.0, 0, 0
+    for A, d, b, v in zip(mats, ds, bs, vs):
+        ctx = pp.pp_create(A, stream=stream.cuda_stream, max_cycles=300)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = pp.pp_eigs(ctx, pp.pp_build_poly(ctx, d, b), 8, 30, 13, 1e-8, v, want_vectors=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 += e0.elapsed_time(e1) * 1e-3
+        pairs64 += int(np.sum(r.resid <= 1e-8)) if r.status == 0 else 0
+        conv64 += r.status == 0
+        ctx.close()
+    return {"metric": "eigenpairs/s at residual 1e-8, batched mixed precision (64 uneven 2-D CD instances)",
+            "value": round(pairs / t, 3), "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
+            "ms_per_step": round(t * 1e3, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 apply / f64 refine", "data": "synthetic (seeded generator)",
+            "config": {"workload": f"batch of {len(mats)} CD instances, N U{{64..512}}, beta U[1,200], d U{{20..80}}, "
+                                   "Arnoldi(30,13), nev 8", "sum_n": int(sum(A.n for A in mats)),
+                       "converged": conv, "fp64_continuations": sum(1 for r in res if r.stats["fp64_cycles"] > 0),
+                       "cycles": [r.stats["cycles"] for r in res]},
+            "plain_fp64_sequential": {"value": round(pairs64 / t64, 3), "unit": UNIT, "seconds": round(t64, 2),
+                                      "converged": conv64},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+
+
+def run_serve(args, ws, rank, local):
+    """The Poisson request stream (first --requests requests) through the continuous-batching server."""
+    import torch
+
+    from paper_1806_08020_gb300 import pp
+
+    torch.cuda.set_device(local)
+    stream_spec = inputs.request_stream(count=args.requests)
+    reqs = []
+    for q in stream_spec:  # inputs are generated before the timed region
+        A = inputs.banded_random(q["n"], q["w"], q["seed"] + 7919 * rank)
+        reqs.append((q, A, inputs.start_vector(A.n, q["seed"], 0), inputs.start_vector(A.n, q["seed"], 1)))
+    S = pp.pp_server_create(precision=pp.PP_FP32, max_cycles=args.serve_max_cycles)
+    pending, done = {}, {}
+    i = 0
+    t0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i][0]["arrival"] <= now:
+                q, A, b, v = reqs[i]
+                rid = pp.pp_server_submit(S, A, q["d"], q["nev"], q["m"], q["k"], 1e-8, b, v)
+                pending[rid] = q
+                i += 1
+            if pending:
+                pp.pp_server_step(S)
+            else:
+                time.sleep(0.0005)
+            for rid in list(pending):
+                r = pp.pp_server_result(S, rid)
+                if r is not None:
+                    done[rid] = r
+                    del pending[rid]
+        wall = time.perf_counter() - t0
+    lat = np.array([l for _, l in done.values()])
+    pairs = sum(int(np.sum(r.resid <= 1e-8)) for r, _ in done.values() if r.status == 0)
+    conv = sum(r.status == 0 for r, _ in done.values())
+    offered = len(reqs) / max(stream_spec[-1]["arrival"], 1e-9)
+    return {"metric": "eigenpairs/s at residual 1e-8 and p50/p99 latency, served request stream",
+            "value": round(pairs / wall, 3), "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
+            "ms_per_step": round(wall * 1e3, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 apply / f64 refine", "data": "synthetic (seeded generator)",
+            "config": {"workload": f"first {len(reqs)} requests of the Poisson(50/s) stream: banded n logU[1e4,2e6], "
+                                   "half-band U{5..25}, nev U{4..32}, d U{10..100}",
+                       "max_cycles_per_request": args.serve_max_cycles},
+            "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4),
+                          "p99": round(float(np.percentile(lat, 99)), 4)},
+            "load": {"offered_req_per_s": round(offered, 2), "achieved_req_per_s": round(len(done) / wall, 2),
+                     "converged": conv, "requests": len(done)},
+            "gpu_launches": int(pp.pp_server_launch_count(S)), "clocks": clk.summary()}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return None
@@ -353,10 +494,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "batch", "serve"])
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--serve-max-cycles", type=int, default=300)
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
+    elif args.workload == "batch":
+        out = run_batch(args, ws, rank, local)
+    elif args.workload == "serve":
+        out = run_serve(args, ws, rank, local)
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0 and out is not None:

@@ -41,6 +41,7 @@ typedef enum {
     PP_OK = 0,
     PP_ENOTCONV = 1,    /* not converged in max_cycles; best pairs and residuals written */
     PP_EBREAKDOWN = 2,  /* GMRES ended early (invariant subspace); degree reduced, poly usable */
+    PP_EAGAIN = 3,      /* a served request has not finished yet */
     PP_EINVAL = -1,     /* bad argument */
     PP_ENOMEM = -2,     /* device or host allocation failed */
     PP_ECUDA = -3,      /* CUDA runtime error; the context must be destroyed */
@@ -83,6 +84,8 @@ typedef struct {
     double t_orth;        /* seconds spent in CGS2 (device, event-timed) */
     double t_restart;     /* seconds in restart + convergence test, host and device */
     double max_resid;     /* largest ||A x - lambda x|| / ||A||_1 among returned slots */
+    int64_t fp64_cycles;  /* cycles run in FP64 (all of them for PP_FP64; for PP_FP32 the
+                             cycles of the FP64 continuation, 0 when FP32 + refinement sufficed) */
 } pp_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -180,6 +183,10 @@ pp_status pp_apply_host(const pp_poly *p, const double *x, double *y);
  *   X: n x (nev+1) column-major (NULL to skip): a real eigenvector, or for a
  *      pair (lam, conj(lam)) the columns (Re x, Im x) of the unit vector x;
  *   resid: ||A x - lam x|| / ||A||_1 per slot;  *nout: slots written.
+ * PP_FP32 contexts (mixed precision): the cycles run in FP32 storage; the
+ * convergence test is always FP64 on A; at the FP32 floor the Ritz vectors are
+ * refined in FP64 (block Krylov space of A, Rayleigh-Ritz); if that does not
+ * reach rtol the solve continues in FP64 from the refined vectors.
  * Requires 1 <= nev < k < m, m < n.  Returns PP_ENOTCONV with the best pairs
  * when max_cycles is reached.
  */
@@ -233,6 +240,86 @@ pp_status pp_orthogonalize(pp_ctx *ctx, const void *V_dev, int64_t ldv, int j, v
  */
 pp_status pp_orthogonalize_noalloc(int64_t n, const double *V_dev, int64_t ldv, int j, double *w_dev,
                                    double *v_dev, double *h_dev, void *stream);
+
+/* ----- Batching: many independent instances advanced together ----- */
+typedef struct pp_batch pp_batch;
+
+/*
+ * pp_batch_create — upload `count` independent sparse matrices (host CSR each,
+ * as pp_create) for solving together.  opts applies to all (PP_FP32 for the
+ * mixed-precision path); the device format is SELL-32.
+ */
+pp_status pp_batch_create(pp_batch **out, int count, const int64_t *n, const int64_t *const *rowptr,
+                          const int32_t *const *colind, const double *const *vals, const pp_opts *opts);
+
+/*
+ * pp_batch_solve — for every instance i: the GMRES polynomial of degree d[i]
+ * from bvec[i] (Section 2 box), then thick-restarted Arnoldi(m, k) on
+ * pi_i(A_i) from v0[i] (NULL or v0[i] NULL: ones) for nev eigenvalues
+ * (Section 4), all instances in lockstep: each Arnoldi step is one CUDA graph
+ * of one launch per polynomial pass for all active instances plus batched
+ * CGS2 sweeps.  Instances stop individually when converged.  Outputs per
+ * instance as in pp_eigs: lam_re[i], lam_im[i], resid[i] (capacity nev + 1),
+ * X[i] (n[i] x (nev + 1), column major; X or X[i] may be NULL), nout[i],
+ * stats[i] (may be NULL).  Returns PP_ENOTCONV if any instance did not
+ * converge (its best pairs are written), a negative status on failure.
+ */
+pp_status pp_batch_solve(pp_batch *b, const int *d, const double *const *bvec, const double *const *v0, int nev,
+                         int m, int k, double rtol, double *const *lam_re, double *const *lam_im,
+                         double *const *X, double *const *resid, int *nout, pp_stats *stats);
+/* Kernels launched by pp_batch_solve calls on this batch so far. */
+int64_t pp_batch_launch_count(const pp_batch *b);
+void pp_batch_destroy(pp_batch *b);
+
+/* ----- Serving: continuous batching of a request stream ----- */
+typedef struct pp_server pp_server;
+
+/*
+ * pp_server_create — a request server on the current GPU.  Requests wait in a
+ * FIFO queue and are admitted, oldest first, while their estimated device
+ * memory fits in mem_budget bytes (0 = 80 % of the free memory) and fewer
+ * than max_active (0 = 256) are on the GPU.  Admitted requests share the
+ * batched engine of pp_batch_solve: each Arnoldi cycle advances all of them,
+ * a request that converges is retired at once (its device memory is freed)
+ * and the queue head is admitted in its place, so requests that arrive while
+ * others run join them on the device.  opts: precision (PP_FP32 = FP32 apply,
+ * FP64 test and refinement), target, max_cycles, refine_steps, stream.
+ * keep_vectors: return eigenvectors in pp_server_result (host memory n x
+ * (nev + 1) per request).
+ */
+pp_status pp_server_create(pp_server **out, const pp_opts *opts, int64_t mem_budget, int max_active,
+                           int keep_vectors);
+/*
+ * pp_server_submit — queue one eigen-solve (inputs are copied; thread safe):
+ * matrix (host CSR, as pp_create), polynomial degree d from b (host, n), and
+ * Arnoldi(m, k) for nev eigenvalues from v0 (host or NULL) to rtol.  *id
+ * receives the request id.  PP_ENOMEM when the request alone exceeds the
+ * memory budget.
+ */
+pp_status pp_server_submit(pp_server *s, int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals,
+                           int d, int nev, int m, int k, double rtol, const double *b, const double *v0, int64_t *id);
+/*
+ * pp_server_step — admit what fits, run one Arnoldi cycle of every admitted
+ * request, retire the finished ones.  *active / *queued (may be NULL) receive
+ * the requests on the GPU and waiting.  Call it in a loop (one host thread).
+ */
+pp_status pp_server_step(pp_server *s, int *active, int *queued);
+/*
+ * pp_server_result — PP_EAGAIN while request id is queued or running;
+ * otherwise its final status with the outputs of pp_eigs (capacity nev + 1;
+ * X n x (nev + 1) or NULL) and *latency (seconds from submit to result, may
+ * be NULL).  Each result can be fetched once (thread safe).
+ */
+pp_status pp_server_result(pp_server *s, int64_t id, double *lam_re, double *lam_im, double *X, double *resid,
+                           int *nout, pp_stats *stats, double *latency);
+/* Kernels launched by the server's batched engine so far (batched passes and sweeps). */
+int64_t pp_server_launch_count(const pp_server *s);
+/* Device bytes the server reserves for one request of this shape (the
+ * admission estimate: matrix with padding headroom, FP64 residual operator,
+ * scratch, two basis slabs, test buffers and, for PP_FP32, the FP64 copy used
+ * when FP32 cannot reach rtol). */
+int64_t pp_server_request_bytes(const pp_server *s, int64_t n, int64_t nnz, int m, int nev);
+void pp_server_destroy(pp_server *s);
 
 /* ----- Host FP64 dense steps (no GPU needed; used by the calls above) ----- */
 

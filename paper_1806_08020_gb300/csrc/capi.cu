@@ -373,6 +373,11 @@ pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, 
         return pp_fail(PP_EINVAL, "start vector is zero or not finite");
     }
     std::vector<double> H((size_t)(d + 1) * d, 0.0);
+    // CGS2 writes rows 0..j+1 of column j only; the rest of H must read as zero
+    if (cudaMemsetAsync(dH, 0, (size_t)(d + 1) * d * 8, c->stream) != cudaSuccess) {
+        cleanup();
+        return pp_fail(PP_ECUDA, "build: memset failed");
+    }
     if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)c->n) * 130)) < 0 || (st = upload_vec(c, b, 1.0 / beta, V)) < 0 ||
         (st = arnoldi_extend(c, nullptr, tau_of, V, ldv, dH, d + 1, 0, d, c->vec[6], nullptr,
                              nullptr)) < 0) {
@@ -462,6 +467,7 @@ void pp_opts_default(pp_opts *o) {
 
 void pp_destroy(pp_ctx *c) {
     if (!c) return;
+    if (c->twin) pp_destroy(c->twin);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (void *p : c->allocs) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -470,6 +476,13 @@ void pp_destroy(pp_ctx *c) {
 
 pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals,
                     const pp_opts *opts) {
+    return pp_create_internal(out, n, rowptr, colind, vals, opts, 1);
+}
+
+}  // extern "C"
+
+pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                             const double *vals, const pp_opts *opts, int make_twin) {
     if (!out || n <= 0 || !rowptr || !colind || !vals) return pp_fail(PP_EINVAL, "pp_create: bad arguments");
     *out = nullptr;
     int64_t nnz = rowptr[n];
@@ -596,9 +609,20 @@ pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_
         return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
     if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)n) * 130)) < 0) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: setup kernels failed"));
+    if (pr == ppk::F32 && make_twin) {
+        // FP64 twin on the same stream: the mixed-precision solve continues in FP64
+        // when the FP32 cycles cannot resolve the eigenvectors (u_32 kappa ~ 1)
+        pp_opts o = c->opts;
+        o.precision = PP_FP64;
+        o.sigma = c->sigma;
+        o.stream = c->stream;
+        if ((st = pp_create(&c->twin, n, rowptr, colind, vals, &o)) < 0) return fail(st);
+    }
     *out = c;
     return PP_OK;
 }
+
+extern "C" {
 
 int64_t pp_launch_count(const pp_ctx *c) { return c ? c->launches : 0; }
 

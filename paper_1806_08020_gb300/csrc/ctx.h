@@ -82,6 +82,7 @@ struct pp_ctx {
     unsigned *d_ticket = nullptr;
     double *d_small = nullptr;  // h1, h2, scal, misc (4 * 256 doubles)
     int64_t launches = 0;
+    pp_ctx *twin = nullptr;  // FP64 copy of an FP32 context (mixed-precision fallback)
     int64_t ldv() const { return (n + 31) / 32 * 32; }
 };
 
@@ -96,6 +97,11 @@ struct pp_poly {
     ~pp_poly() { delete inner; }
 };
 
+
+// pp_create with control over the FP64 twin of an FP32 context (the request
+// server creates contexts without it to save memory).
+pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                             const double *vals, const pp_opts *opts, int make_twin);
 
 namespace ppi {
 

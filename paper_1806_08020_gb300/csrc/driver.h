@@ -1,0 +1,459 @@
+// Per-instance Arnoldi driver pieces shared by pp_eigs (one instance) and the
+// batched engine: the wanted-set selection and thick restart of Section 4,
+// the FP64 Ritz test on A, and the FP64 refinement of the mixed-precision mode.
+#pragma once
+
+#include "ctx.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace ppi {
+
+// Wanted slots: a real Ritz pair occupies one slot, a conjugate pair two
+// (columns Re, Im of the Im > 0 member's vector).
+struct Slots {
+    int nw = 0;
+    std::vector<int> partner;  // partner column (itself for a real slot)
+    std::vector<double> sg;    // +1 Re column of a pair, -1 Im column, 0 real
+};
+
+struct RitzOut {
+    std::vector<double> lre, lim, res, ynrm;
+    int nconv = 0;
+    bool all = false;
+};
+
+struct Driver {
+    pp_ctx *c;
+    int64_t n, ldv;
+    int wcap;
+    std::vector<void *> mine;
+    // FP64 test buffers
+    double *Y64 = nullptr, *AY64 = nullptr;
+    void *Ys = nullptr;  // storage-precision Ritz vectors (mixed mode)
+    double *dQ = nullptr, *dq = nullptr, *dmu = nullptr;
+    int *dpartner = nullptr;
+    // refinement
+    double *Z = nullptr, *dG = nullptr;
+    static constexpr int kZcap = 128;
+
+    ~Driver() {
+        cudaStreamSynchronize(c->stream);
+        for (void *q : mine) dfree(c, q);
+    }
+    pp_status alloc(void **p, size_t bytes) {
+        pp_status st = dmalloc(c, p, bytes);
+        if (st >= 0) mine.push_back(*p);
+        return st;
+    }
+
+    // Buffers of the FP64 Ritz test (and the storage-precision Ritz vectors in
+    // mixed mode).  The refinement basis is allocated when first needed, unless
+    // the caller supplies a shared one (Z, dG).
+    pp_status alloc_test_buffers(bool mixed) {
+        CKS(alloc((void **)&Y64, (size_t)ldv * (wcap + 1) * 8));
+        CKS(alloc((void **)&AY64, (size_t)ldv * (wcap + 1) * 8));
+        if (mixed) CKS(alloc(&Ys, (size_t)ldv * (wcap + 1) * c->esz));
+        CKS(alloc((void **)&dQ, (size_t)kZcap * kZcap * 8));
+        CKS(alloc((void **)&dq, (size_t)4 * (wcap + 1) * 8));
+        CKS(alloc((void **)&dmu, (size_t)3 * (wcap + 1) * 8));
+        CKS(alloc((void **)&dpartner, (size_t)(wcap + 1) * 4));
+        CKS(ensure_part(c, std::max((size_t)ppk::cgs_grid((int)n) * 130, (size_t)(wcap + 1) * 3 * 1024)));
+        return PP_OK;
+    }
+
+    // Y64 = B S (B: mcols columns of precision pb), then FP64 Rayleigh quotients
+    // and residual norms on A for each slot.
+    pp_status ritz_test(const void *B, ppk::Prec pb, int mcols, const std::vector<double> &Sw, const Slots &sl,
+                        double rtol, RitzOut &out, pp_stats &S) {
+        const int nw = sl.nw;
+        CK(cudaMemcpyAsync(dQ, Sw.data(), Sw.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(dpartner, sl.partner.data(), nw * 4, cudaMemcpyHostToDevice, c->stream));
+        if (pb == ppk::F64) {
+            ppk::launch_rotate(ppk::F64, (int)n, B, ldv, mcols, dQ, nw, Y64, ldv, c->stream);
+            CKS(check_launch(c));
+        } else {
+            ppk::launch_rotate(ppk::F32, (int)n, B, ldv, mcols, dQ, nw, Ys, ldv, c->stream);
+            CKS(check_launch(c));
+            ppk::launch_convert(ppk::F32, ppk::F64, (int)(ldv * nw), Ys, Y64, c->stream);
+            CKS(check_launch(c));
+        }
+        for (int s = 0; s < nw; ++s) {
+            ppk::StepArgs a;
+            a.x = Y64 + (size_t)s * ldv;
+            a.y = AY64 + (size_t)s * ldv;
+            a.plain = 1;
+            ppk::launch_step(c->A64, a, c->stream);
+            CKS(check_launch(c));
+        }
+        S.mvps += nw;
+        S.vops += (int64_t)4 * mcols * nw;
+        ppk::ColDotArgs cda;
+        cda.n = (int)n;
+        cda.nw = nw;
+        cda.Y = Y64;
+        cda.AY = AY64;
+        cda.ld = ldv;
+        cda.partner = dpartner;
+        cda.q = dq;
+        cda.part = c->d_part;
+        cda.ticket = c->d_ticket;
+        cda.mode = 0;
+        ppk::launch_coldots(ppk::F64, cda, c->stream);
+        CKS(check_launch(c));
+        std::vector<double> q((size_t)4 * nw);
+        CK(cudaMemcpyAsync(q.data(), dq, q.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        auto &lre = out.lre, &lim = out.lim;
+        lre.assign(nw, 0);
+        lim.assign(nw, 0);
+        out.ynrm.assign(nw, 0);
+        for (int s = 0; s < nw;) {
+            if (sl.partner[s] == s) {
+                lre[s] = q[4 * s + 1] / q[4 * s];
+                out.ynrm[s] = q[4 * s];
+                s += 1;
+            } else {
+                double yy = q[4 * s] + q[4 * (s + 1)];
+                lre[s] = lre[s + 1] = (q[4 * s + 1] + q[4 * (s + 1) + 1]) / yy;
+                lim[s] = (q[4 * s + 2] - q[4 * (s + 1) + 2]) / yy;
+                lim[s + 1] = -lim[s];
+                out.ynrm[s] = out.ynrm[s + 1] = yy;
+                s += 2;
+            }
+        }
+        // residual columns: Re part AYr - mr Yr + mi Yi, Im part AYi - mr Yi - mi Yr
+        std::vector<double> mu((size_t)3 * nw, 0.0);
+        for (int s = 0; s < nw; ++s) {
+            mu[s] = lre[s];
+            mu[nw + s] = (sl.partner[s] == s) ? 0.0 : (sl.sg[s] > 0 ? lim[s] : lim[sl.partner[s]]);
+            mu[2 * nw + s] = sl.sg[s];
+        }
+        CK(cudaMemcpyAsync(dmu, mu.data(), mu.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        cda.mode = 1;
+        cda.mur = dmu;
+        cda.mui = dmu + nw;
+        cda.sg = dmu + 2 * nw;
+        ppk::launch_coldots(ppk::F64, cda, c->stream);
+        CKS(check_launch(c));
+        CK(cudaMemcpyAsync(q.data(), dq, q.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        out.res.assign(nw, 0);
+        out.all = true;
+        out.nconv = 0;
+        for (int s = 0; s < nw;) {
+            if (sl.partner[s] == s) {
+                out.res[s] = std::sqrt(std::max(q[4 * s + 3], 0.0) / out.ynrm[s]) / c->norm1;
+                s += 1;
+            } else {
+                double r2 = (q[4 * s + 3] + q[4 * (s + 1) + 3]) / out.ynrm[s];
+                out.res[s] = out.res[s + 1] = std::sqrt(std::max(r2, 0.0)) / c->norm1;
+                s += 2;
+            }
+        }
+        for (double r : out.res) {
+            bool ok = std::isfinite(r) && r <= rtol;
+            out.nconv += ok;
+            out.all = out.all && ok;
+        }
+        return PP_OK;
+    }
+
+    // FP64 refinement on A (mixed precision): block Krylov span{Y, AY, ..., A^s Y}
+    // with CGS2, Rayleigh-Ritz of A, Ritz pairs matched to the current estimates.
+    pp_status refine(Slots &sl, int nev, RitzOut &R, double rtol, int steps, int rounds, pp_stats &S) {
+        if (!Z) CKS(alloc((void **)&Z, (size_t)ldv * (kZcap + 1) * 8));
+        if (!dG) CKS(alloc((void **)&dG, (size_t)(kZcap + 1) * kZcap * 8));
+        steps = std::max(1, std::min(steps, kZcap / (nev + 1) - 1));
+        const int ldg = kZcap + 1;
+        double *W = AY64 + (size_t)(nev + 1) * ldv;  // spare FP64 column (context vectors are FP32 here)
+        for (int round = 0; round < rounds; ++round) {
+            const int nw = sl.nw;  // the wanted slots of this round (the layout may change)
+            int nz = 0;
+            CK(cudaMemsetAsync(dG, 0, (size_t)ldg * kZcap * 8, c->stream));
+            for (int s = 0; s < nw; ++s) {
+                CK(cudaMemcpyAsync(W, Y64 + (size_t)s * ldv, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+                CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, c->d_small + 2048));
+                nz++;
+            }
+            int b0 = 0, b1 = nz;
+            for (int st = 0; st < steps; ++st) {
+                for (int col = b0; col < b1; ++col) {
+                    ppk::StepArgs a;
+                    a.x = Z + (size_t)col * ldv;
+                    a.y = W;
+                    a.plain = 1;
+                    ppk::launch_step(c->A64, a, c->stream);
+                    CKS(check_launch(c));
+                    CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, dG + (size_t)col * ldg));
+                    S.dots += 2 * nz + 1;
+                    S.vops += 4 * nz + 2;
+                    nz++;
+                }
+                S.mvps += b1 - b0;
+                b0 = b1;
+                b1 = nz;
+            }
+            // last block: G[:, col] = Z^T A z_col (no new columns)
+            for (int col = b0; col < b1; ++col) {
+                ppk::StepArgs a;
+                a.x = Z + (size_t)col * ldv;
+                a.y = W;
+                a.plain = 1;
+                ppk::launch_step(c->A64, a, c->stream);
+                CKS(check_launch(c));
+                ppk::CgsArgs ca;
+                ca.mode = 0;
+                ca.n = (int)n;
+                ca.V = Z;
+                ca.ldv = ldv;
+                ca.j = nz;
+                ca.w = W;
+                ca.out = dG + (size_t)col * ldg;
+                ca.part = c->d_part;
+                ca.ticket = c->d_ticket;
+                ppk::launch_cgs(ppk::F64, ca, c->stream);
+                CKS(check_launch(c));
+                S.dots += nz;
+                S.vops += nz;
+            }
+            S.mvps += b1 - b0;
+            std::vector<double> Gfull((size_t)ldg * nz), G((size_t)nz * nz);
+            CK(cudaMemcpyAsync(Gfull.data(), dG, Gfull.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (int j = 0; j < nz; ++j)
+                for (int i = 0; i < nz; ++i) G[i + (size_t)j * nz] = Gfull[i + (size_t)j * ldg];
+            for (double v : G)
+                if (!std::isfinite(v)) return pp_fail(PP_ENUMERIC, "refinement: non-finite projection");
+            std::vector<double> wr(nz), wi(nz), Sv((size_t)nz * nz);
+            if (!ppd::dense_eig(nz, G.data(), nz, wr.data(), wi.data(), Sv.data(), nz))
+                return pp_fail(PP_ENUMERIC, "refinement: Rayleigh-Ritz QR failed");
+            // the refined wanted set: the Ritz values of G nearest the current
+            // estimates, a conjugate pair as one unit, until nev slots are filled
+            // (one more when the last unit is a pair); FP32 may have shown a pair
+            // where FP64 resolves two real values, so the slot layout is rebuilt
+            std::vector<cd> est;
+            for (int q = 0; q < sl.nw; ++q)
+                if (sl.partner[q] == q || sl.sg[q] > 0) est.push_back(cd(R.lre[q], std::fabs(R.lim[q])));
+            std::vector<int> units;
+            std::vector<double> dist;
+            for (int i = 0; i < nz; ++i) {
+                if (wi[i] < 0) continue;
+                double dmin = INFINITY;
+                for (const cd &e : est) dmin = std::min(dmin, std::abs(cd(wr[i], wi[i]) - e));
+                units.push_back(i);
+                dist.push_back(dmin);
+            }
+            std::vector<int> ord(units.size());
+            for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return dist[a] < dist[b]; });
+            Slots ns;
+            std::vector<int> pick;
+            for (int q : ord) {
+                if (ns.nw >= nev) break;
+                int i = units[q];
+                pick.push_back(i);
+                ns.nw += wi[i] != 0.0 ? 2 : 1;
+            }
+            if (ns.nw < nev) return pp_fail(PP_ENUMERIC, "refinement: fewer Ritz values than wanted");
+            ns.partner.assign(ns.nw, 0);
+            ns.sg.assign(ns.nw, 0.0);
+            std::vector<double> Sw((size_t)nz * ns.nw);
+            int s = 0;
+            for (int i : pick) {
+                std::copy(&Sv[(size_t)i * nz], &Sv[(size_t)i * nz] + nz, &Sw[(size_t)s * nz]);
+                if (wi[i] == 0.0) {
+                    ns.partner[s] = s;
+                    s += 1;
+                } else {
+                    std::copy(&Sv[(size_t)(i + 1) * nz], &Sv[(size_t)(i + 1) * nz] + nz, &Sw[(size_t)(s + 1) * nz]);
+                    ns.partner[s] = s + 1;
+                    ns.partner[s + 1] = s;
+                    ns.sg[s] = 1.0;
+                    ns.sg[s + 1] = -1.0;
+                    s += 2;
+                }
+            }
+            sl = ns;
+            CKS(ritz_test(Z, ppk::F64, nz, Sw, sl, rtol, R, S));
+            S.vops += (int64_t)nz * nw;
+            if (R.all) return PP_OK;
+        }
+        return PP_OK;
+    }
+};
+
+
+// When the FP32 cycles of the mixed mode hand over to the FP64 refinement:
+// within 10 rtol; at the FP32 floor (below 1e-6 and no longer halving per
+// cycle); after four cycles without halving at any level (an operator too
+// non-normal for FP32, or an FP32 apply swamped by the growth of the partial
+// products of a high-degree polynomial); or at the last cycle.
+struct MixedSwitch {
+    double rtol, best = INFINITY;
+    int stall = 0;
+    explicit MixedSwitch(double r) : rtol(r) {}
+    bool should_refine(const RitzOut &R, bool last_cycle) {
+        double mx = *std::max_element(R.res.begin(), R.res.end());
+        stall = (mx < 0.5 * best) ? 0 : stall + 1;
+        best = std::min(best, mx);
+        if (last_cycle || mx <= 10 * rtol) return true;
+        if (mx <= std::max(rtol, 1e-6) && stall >= 1) return true;
+        return stall >= 4;
+    }
+    // after a refinement that missed rtol, keep cycling in FP32 from here
+    void reset() {
+        stall = 0;
+        best = INFINITY;
+    }
+};
+
+// Ritz values of H_m (host FP64), the wanted set (nev slots, one more when a
+// conjugate pair would split) and its Ritz vectors' coefficients (Section 4).
+struct Cycle {
+    int m = 0;
+    std::vector<double> Hm, wr, wi, Sv, Sw;
+    std::vector<cd> nu;
+    std::vector<int> order;
+    Slots sl;
+};
+
+inline pp_status wanted_set(const std::vector<double> &H, int ldh, int m, int nev, double target, Cycle &cy) {
+    cy.m = m;
+    cy.Hm.assign((size_t)m * m, 0.0);
+    cy.wr.assign(m, 0.0);
+    cy.wi.assign(m, 0.0);
+    cy.Sv.assign((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j)
+        for (int i = 0; i < m; ++i) cy.Hm[i + (size_t)j * m] = H[i + (size_t)j * ldh];
+    for (double v : cy.Hm)
+        if (!std::isfinite(v)) return pp_fail(PP_ENUMERIC, "non-finite Hessenberg entry");
+    std::vector<double> Hc = cy.Hm;
+    if (!ppd::dense_eig(m, Hc.data(), m, cy.wr.data(), cy.wi.data(), cy.Sv.data(), m))
+        return pp_fail(PP_ENUMERIC, "Ritz values: QR failed");
+    cy.nu.resize(m);
+    for (int i = 0; i < m; ++i) cy.nu[i] = cd(cy.wr[i], cy.wi[i]);
+    cy.order = ppd::ritz_order(cy.nu, target);
+    Slots &sl = cy.sl;
+    sl.nw = nev + (cy.nu[cy.order[nev - 1]].imag() > 0 ? 1 : 0);
+    sl.partner.assign(sl.nw, 0);
+    sl.sg.assign(sl.nw, 0.0);
+    cy.Sw.assign((size_t)m * sl.nw, 0.0);
+    const auto &Sv = cy.Sv;
+    for (int s = 0; s < sl.nw;) {
+        int i = cy.order[s];
+        if (cy.wi[i] == 0.0) {
+            std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &cy.Sw[(size_t)s * m]);
+            sl.partner[s] = s;
+            s += 1;
+        } else {
+            int base = cy.wi[i] > 0 ? i : i - 1;
+            std::copy(&Sv[(size_t)base * m], &Sv[(size_t)base * m] + m, &cy.Sw[(size_t)s * m]);
+            std::copy(&Sv[(size_t)(base + 1) * m], &Sv[(size_t)(base + 1) * m] + m, &cy.Sw[(size_t)(s + 1) * m]);
+            sl.partner[s] = s + 1;
+            sl.partner[s + 1] = s;
+            sl.sg[s] = 1.0;
+            sl.sg[s + 1] = -1.0;
+            s += 2;
+        }
+    }
+    return PP_OK;
+}
+
+// Thick restart (Section 4): keep k Ritz vectors (k - 1 when a pair would
+// split), Q = qr([Re, Im] of their coefficients), Hn = [Q^T H_m Q ; h e_m^T Q].
+inline int restart_basis(const Cycle &cy, const std::vector<double> &H, int ldh, int k, std::vector<double> &Q,
+                         std::vector<double> &Hn) {
+    const int m = cy.m;
+    const auto &Sv = cy.Sv;
+    int kk = (cy.nu[cy.order[k - 1]].imag() > 0) ? k - 1 : k;
+    std::vector<double> B((size_t)m * kk);
+    int col = 0;
+    for (int s = 0; s < kk; ++s) {
+        int i = cy.order[s];
+        if (cy.wi[i] == 0.0) {
+            std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &B[(size_t)col * m]);
+            col++;
+        } else if (cy.wi[i] > 0) {
+            std::copy(&Sv[(size_t)i * m], &Sv[(size_t)i * m] + m, &B[(size_t)col * m]);
+            std::copy(&Sv[(size_t)(i + 1) * m], &Sv[(size_t)(i + 1) * m] + m, &B[(size_t)(col + 1) * m]);
+            col += 2;
+        }
+    }
+    Q.assign((size_t)m * kk, 0.0);
+    ppd::thin_qr(m, kk, B.data(), Q.data());
+    std::vector<double> HQ((size_t)m * kk, 0.0);
+    Hn.assign((size_t)ldh * m, 0.0);
+    for (int cc = 0; cc < kk; ++cc)
+        for (int r = 0; r < m; ++r) {
+            double s = 0;
+            for (int t = 0; t < m; ++t) s += cy.Hm[r + (size_t)t * m] * Q[t + (size_t)cc * m];
+            HQ[r + (size_t)cc * m] = s;
+        }
+    for (int cc = 0; cc < kk; ++cc) {
+        for (int r = 0; r < kk; ++r) {
+            double s = 0;
+            for (int t = 0; t < m; ++t) s += Q[t + (size_t)r * m] * HQ[t + (size_t)cc * m];
+            Hn[r + (size_t)cc * ldh] = s;
+        }
+        Hn[kk + (size_t)cc * ldh] = H[m + (size_t)(m - 1) * ldh] * Q[(m - 1) + (size_t)cc * m];
+    }
+    return kk;
+}
+
+// Outputs sorted by the target (SR: Re, |Im|, Im > 0 first; SM: |lam|, Re, Im > 0
+// first); X gets unit vectors (a pair's Re, Im columns scaled by its complex norm).
+inline void write_outputs(int target, int64_t n, const Slots &sl, const RitzOut &R, const std::vector<double> &Yh,
+                          double *lam_re, double *lam_im, double *resid, double *X, double &maxres) {
+    const int nw = sl.nw;
+    std::vector<int> srt(nw);
+    for (int s = 0; s < nw; ++s) srt[s] = s;
+    const auto &lre = R.lre, &lim = R.lim;
+    bool sr = target == PP_TARGET_SR;
+    std::stable_sort(srt.begin(), srt.end(), [&](int a, int b) {
+        double ka = sr ? lre[a] : std::hypot(lre[a], lim[a]), kb = sr ? lre[b] : std::hypot(lre[b], lim[b]);
+        if (ka != kb) return ka < kb;
+        if (sr) {
+            if (std::fabs(lim[a]) != std::fabs(lim[b])) return std::fabs(lim[a]) < std::fabs(lim[b]);
+        } else if (lre[a] != lre[b]) {
+            return lre[a] < lre[b];
+        }
+        return lim[a] > lim[b];
+    });
+    maxres = 0;
+    for (int s = 0; s < nw; ++s) {
+        int o = srt[s];
+        lam_re[s] = lre[o];
+        lam_im[s] = lim[o];
+        resid[s] = R.res[o];
+        maxres = std::max(maxres, R.res[o]);
+        if (X) {
+            bool pair = sl.partner[o] != o;
+            int cr = pair ? std::min(o, sl.partner[o]) : o, ci = pair ? cr + 1 : o;
+            double nrm2 = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                double a = Yh[(size_t)cr * n + i];
+                nrm2 += a * a;
+                if (pair) {
+                    double b = Yh[(size_t)ci * n + i];
+                    nrm2 += b * b;
+                }
+            }
+            double sc = 1.0 / std::sqrt(nrm2);
+            if (!pair) {
+                for (int64_t i = 0; i < n; ++i) X[(size_t)s * n + i] = Yh[(size_t)o * n + i] * sc;
+            } else {
+                bool first = lim[o] > 0 || (lim[o] == 0 && o == cr);
+                double sgn = (lim[cr] >= 0) ? 1.0 : -1.0;
+                const double *src = first ? &Yh[(size_t)cr * n] : &Yh[(size_t)ci * n];
+                double f = first ? sc : sgn * sc;
+                for (int64_t i = 0; i < n; ++i) X[(size_t)s * n + i] = src[i] * f;
+            }
+        }
+    }
+}
+
+}  // namespace ppi

@@ -120,14 +120,16 @@ __global__ void __launch_bounds__(kThreads) k_csr_step(CsrView A, StepArgs s) {
 // Deterministic grid reduction: every block writes `nout` partials to
 // part[block * nout + o]; the last block to arrive sums them in block order.
 // ---------------------------------------------------------------------------
-__device__ bool last_block(unsigned *ticket) {
+__device__ bool last_block(unsigned *ticket, unsigned nblocks) {
     __shared__ bool is_last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1);
+    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == nblocks - 1);
     __syncthreads();
     return is_last;
 }
+
+__device__ bool last_block(unsigned *ticket) { return last_block(ticket, gridDim.x * gridDim.y); }
 
 __device__ void reduce_partials(const double *part, int nblocks, int nout, double *out) {
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -147,8 +149,9 @@ __device__ void reduce_partials(const double *part, int nblocks, int nout, doubl
 constexpr int kRows = 64;
 constexpr int kQ = kRows / 32;
 
+// The sweep of block `bid` out of `nblk` blocks working on one basis.
 template <typename T, int CPW>
-__global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
+__device__ __forceinline__ void cgs_body(const CgsArgs &a, int bid, int nblk) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const T *V = (const T *)a.V;
     const T *w = (const T *)a.w;
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
     for (int cc = 0; cc < CPW; ++cc) acc[cc] = 0;
     double nrm = 0;
     const int ntiles = (n + kRows - 1) / kRows;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int tile = bid; tile < ntiles; tile += nblk) {
         const int r0 = tile * kRows;
         double vv[CPW][kQ];
 #pragma unroll
@@ -187,8 +190,9 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
             }
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc)
+                if (warp + kWarps * cc < j)  // warp-uniform: no FMAs on columns past j
 #pragma unroll
-                for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wv[q], acc[cc]);
+                    for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wv[q], acc[cc]);
             continue;
         }
         // w - V h for the tile rows: per-warp partial sums, then across warps
@@ -222,13 +226,14 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
         if (a.mode == 1) {
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc)
+                if (warp + kWarps * cc < j)
 #pragma unroll
-                for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wsh[lane + 32 * q], acc[cc]);
+                    for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wsh[lane + 32 * q], acc[cc]);
         }
     }
     // per-block partials
     const int nout = (a.mode == 0) ? j : (a.mode == 1 ? j + 1 : 1);
-    double *part = a.part + (size_t)blockIdx.x * nout;
+    double *part = a.part + (size_t)bid * nout;
     if (a.mode != 2) {
 #pragma unroll
         for (int cc = 0; cc < CPW; ++cc) {
@@ -250,8 +255,8 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
             part[a.mode == 1 ? j : 0] = s;
         }
     }
-    if (!last_block(a.ticket)) return;
-    reduce_partials(a.part, gridDim.x, nout, a.out);
+    if (!last_block(a.ticket, nblk)) return;
+    reduce_partials(a.part, nblk, nout, a.out);
     __syncthreads();
     if (tid == 0) *a.ticket = 0;
     if (a.mode == 2) {
@@ -263,6 +268,104 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
             a.hcol[j] = nn;
             a.scal[0] = nn > 0 ? 1.0 / nn : 0.0;
         }
+    }
+}
+
+template <typename T, int CPW>
+__global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
+    cgs_body<T, CPW>(a, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms: many independent instances in one launch.  Instance state is
+// in device tables, so one captured graph serves every cycle; instance i is
+// active at Arnoldi step jj when lo[i] <= jj < hi[i] (its restart column and
+// its subspace size; hi = 0 once it is done).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_instance(const BatchCgsInst *ci, int count, int b) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ci[mid].blk0 <= b)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int CPW>
+__global__ void __launch_bounds__(kThreads) k_cgs_batch(const BatchCgsInst *ci, int count, const int *lo,
+                                                        const int *hi, int mode, int jj) {
+    const int i = find_instance(ci, count, blockIdx.x);
+    if (jj < lo[i] || jj >= hi[i]) return;
+    const BatchCgsInst &I = ci[i];
+    CgsArgs a;
+    a.mode = mode;
+    a.n = I.n;
+    a.V = I.V;
+    a.ldv = I.ldv;
+    a.j = jj + 1;
+    a.w = I.W;
+    a.part = I.part;
+    a.ticket = I.ticket;
+    if (mode == 0) {
+        a.out = I.h1;
+    } else if (mode == 1) {
+        a.h = I.h1;
+        a.wout = I.W;
+        a.out = I.h2;
+    } else {
+        a.h = I.h2;
+        a.h1 = I.h1;
+        a.wout = (T *)I.V + (size_t)(jj + 1) * I.ldv;
+        a.out = I.nrm;
+        a.hcol = I.H + (size_t)jj * I.ldh;
+        a.scal = I.scal;
+    }
+    cgs_body<T, CPW>(a, blockIdx.x - I.blk0, I.nblk);
+}
+
+template <typename T>
+__global__ void k_scale_batch(const BatchCgsInst *ci, int count, const int *lo, const int *hi, int jj) {
+    const int i = find_instance(ci, count, blockIdx.x);
+    if (jj < lo[i] || jj >= hi[i]) return;
+    const BatchCgsInst &I = ci[i];
+    T *x = (T *)I.V + (size_t)(jj + 1) * I.ldv;
+    const double s = *I.scal;
+    for (int r = (blockIdx.x - I.blk0) * kThreads + threadIdx.x; r < I.n; r += I.nblk * kThreads)
+        x[r] = (T)((double)x[r] * s);
+}
+
+// One polynomial pass for every active instance: warp = one SELL slice of one
+// instance; blocks stride over (instance, 8-slice) work items.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pass_batch(const BatchPassInst *pi, const BatchPassEntry *tab,
+                                                         const int2 *items, int nitems, const int *lo,
+                                                         const int *hi, int jj) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 itm = items[it];
+        const BatchPassEntry e = tab[itm.x];
+        if (e.kind < 0 || jj < lo[itm.x] || jj >= hi[itm.x]) continue;
+        const BatchPassInst &I = pi[itm.x];
+        const int slice = itm.y + warp;
+        if (slice >= I.nslices) continue;
+        const int row = slice * 32 + lane;
+        if (row >= I.n) continue;
+        const T *bufs[5] = {(const T *)I.V + (size_t)jj * I.ldv, (const T *)I.W, (const T *)I.P0, (const T *)I.P1,
+                            (const T *)I.T};
+        const T *x = bufs[e.src];
+        T *y = (T *)bufs[e.dst];
+        SellView A{I.n, I.nslices, I.slice_ptr, I.col, I.val};
+        T u = sell_row<T, T, T>(A, x, row);
+        if (I.sigma != 0.0) u = fma(-(T)I.sigma, x[row], u);
+        if (e.kind == 0)
+            y[row] = u;
+        else if (e.kind == 1)
+            y[row] = fma(-(T)e.a2, u, x[row]);
+        else
+            y[row] = fma(-(T)e.a2, u, fma(-(T)e.a1, x[row], bufs[e.aux][row]));
     }
 }
 
@@ -508,6 +611,44 @@ void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st) {
         cgs_dispatch<double>(a, 0, st);
     else
         cgs_dispatch<float>(a, 0, st);
+}
+
+void launch_cgs_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int mode,
+                      int jj, cudaStream_t st) {
+    int cpw = (jj + 1 + kWarps - 1) / kWarps;
+#define PP_CB(T, C) k_cgs_batch<T, C><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj)
+    if (p == F64) {
+        if (cpw <= 2) PP_CB(double, 2); else if (cpw <= 4) PP_CB(double, 4); else if (cpw <= 8) PP_CB(double, 8); else PP_CB(double, 16);
+    } else {
+        if (cpw <= 2) PP_CB(float, 2); else if (cpw <= 4) PP_CB(float, 4); else if (cpw <= 8) PP_CB(float, 8); else PP_CB(float, 16);
+    }
+#undef PP_CB
+}
+
+void launch_scale_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int jj,
+                        cudaStream_t st) {
+    if (p == F64)
+        k_scale_batch<double><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, jj);
+    else
+        k_scale_batch<float><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, jj);
+}
+
+void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *tab, const int2 *items, int nitems,
+                       const int *lo, const int *hi, int jj, cudaStream_t st) {
+    int g = num_sms() * 8;
+    if (nitems < g) g = nitems;
+    if (g < 1) g = 1;
+    if (p == F64)
+        k_pass_batch<double><<<g, kThreads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
+    else
+        k_pass_batch<float><<<g, kThreads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
+}
+
+int cgs_batch_blocks(int n) {
+    // blocks for one instance: tiles of 64 rows, at most one wave share of 3 per SM
+    int tiles = (n + kRows - 1) / kRows;
+    int cap = num_sms() * 3;
+    return tiles < cap ? tiles : cap;
 }
 
 void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st) {

@@ -111,6 +111,50 @@ void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st);
 void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st);
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st);
 
+// Batched Arnoldi steps (many instances advance together, one launch per pass).
+// Per-instance CGS2 state: the basis V (ldv), the operator output W, the
+// Hessenberg matrix H (ldh), reduction scratch, and the instance's block range
+// [blk0, blk0 + nblk) in the batched grid.
+struct BatchCgsInst {
+    const void *V;
+    int64_t ldv;
+    int n;
+    void *W;
+    double *H;
+    int ldh;
+    double *h1, *h2, *nrm, *scal;
+    double *part;
+    unsigned *ticket;
+    int nblk, blk0;
+};
+// Per-instance data of a batched polynomial pass; buffers by id:
+// 0 = V[:, jj] (the step's input), 1 = W (output), 2 = P0, 3 = P1, 4 = T (pair temp).
+struct BatchPassInst {
+    int n, nslices;
+    const int *slice_ptr;
+    const int *col;
+    const void *val;
+    double sigma;
+    const void *V;
+    int64_t ldv;
+    void *W, *P0, *P1, *T;
+};
+// One pass of one instance: kind -1 none, 0 y = u, 1 y = x - a2 u, 2 y = aux - a1 x - a2 u.
+struct BatchPassEntry {
+    int kind, src, dst, aux;
+    double a1, a2;
+};
+int cgs_batch_blocks(int n);
+// Instance i takes part in step jj when lo[i] <= jj < hi[i] (device arrays).
+void launch_cgs_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int mode,
+                      int jj, cudaStream_t st);
+void launch_scale_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int jj,
+                        cudaStream_t st);
+#ifdef __CUDACC__
+void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *tab, const int2 *items, int nitems,
+                       const int *lo, const int *hi, int jj, cudaStream_t st);
+#endif
+
 // Out[:, c] = sum_r V[:, r] Q[r, c] (c < kk), Q column major m x kk on the device.
 void launch_rotate(Prec p, int n, const void *V, int64_t ldv, int m, const double *Q, int kk, void *out,
                    int64_t ldo, cudaStream_t st);

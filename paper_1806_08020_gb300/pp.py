@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpp.so")
 
-PP_OK, PP_ENOTCONV, PP_EBREAKDOWN = 0, 1, 2
+PP_OK, PP_ENOTCONV, PP_EBREAKDOWN, PP_EAGAIN = 0, 1, 2, 3
 PP_EINVAL, PP_ENOMEM, PP_ECUDA, PP_ETIMEOUT, PP_ENUMERIC = -1, -2, -3, -4, -5
 PP_FP64, PP_FP32, PP_FP32_BF16 = 0, 1, 2
 PP_FMT_AUTO, PP_FMT_CSR, PP_FMT_SELL = 0, 1, 2
@@ -33,7 +33,7 @@ class pp_stats(C.Structure):
     _fields_ = [("cycles", C.c_int64), ("mvps", C.c_int64), ("dots", C.c_int64), ("vops", C.c_int64),
                 ("kernel_launches", C.c_int64), ("converged", C.c_int32), ("nconv", C.c_int32),
                 ("t_total", C.c_double), ("t_apply", C.c_double), ("t_orth", C.c_double),
-                ("t_restart", C.c_double), ("max_resid", C.c_double)]
+                ("t_restart", C.c_double), ("max_resid", C.c_double), ("fp64_cycles", C.c_int64)]
 
     def to_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,6 +71,20 @@ _SIGS = {
                           C.POINTER(pp_stats)]),
     "pp_orthogonalize": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, _D]),
     "pp_orthogonalize_noalloc": (C.c_int, [C.c_int64, _P, C.c_int64, C.c_int, _P, _P, _P, _P]),
+    "pp_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, _I64, C.POINTER(_I64), C.POINTER(C.POINTER(C.c_int32)),
+                                  C.POINTER(_D), C.POINTER(pp_opts)]),
+    "pp_batch_solve": (C.c_int, [_P, _I, C.POINTER(_D), C.POINTER(_D), C.c_int, C.c_int, C.c_int, C.c_double,
+                                 C.POINTER(_D), C.POINTER(_D), C.POINTER(_D), C.POINTER(_D), _I, C.POINTER(pp_stats)]),
+    "pp_batch_launch_count": (C.c_int64, [_P]),
+    "pp_batch_destroy": (None, [_P]),
+    "pp_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(pp_opts), C.c_int64, C.c_int, C.c_int]),
+    "pp_server_submit": (C.c_int, [_P, C.c_int64, _I64, C.POINTER(C.c_int32), _D, C.c_int, C.c_int, C.c_int,
+                                   C.c_int, C.c_double, _D, _D, _I64]),
+    "pp_server_step": (C.c_int, [_P, _I, _I]),
+    "pp_server_result": (C.c_int, [_P, C.c_int64, _D, _D, _D, _D, _I, C.POINTER(pp_stats), _D]),
+    "pp_server_launch_count": (C.c_int64, [_P]),
+    "pp_server_request_bytes": (C.c_int64, [_P, C.c_int64, C.c_int64, C.c_int, C.c_int]),
+    "pp_server_destroy": (None, [_P]),
     "pp_dense_eig": (C.c_int, [C.c_int, _D, C.c_int, _D, _D, _D, C.c_int]),
     "pp_harmonic_ritz": (C.c_int, [C.c_int, _D, C.c_int, _D, _D]),
     "pp_leja_order": (C.c_int, [C.c_int, _D, _D, _D, _D]),
@@ -288,6 +302,167 @@ def pp_eigs(ctx: Context, p: Poly | None, nev: int, m: int, k: int, rtol: float,
     k_ = nout.value
     return EigsResult(lre[:k_] + 1j * lim[:k_], X[:k_].T.copy() if X is not None else None, res[:k_], status,
                       st.to_dict())
+
+
+# ---------------------------------------------------------------------------
+# Batching
+# ---------------------------------------------------------------------------
+class Batch:
+    """Owner of a pp_batch handle (count instances)."""
+
+    def __init__(self, handle: int, ns: list[int]):
+        self.handle = C.c_void_p(handle)
+        self.ns = ns
+
+    def close(self):
+        if self.handle:
+            LIB.pp_batch_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pp_batch_create(mats, **opts) -> Batch:
+    o = default_opts(**opts)
+    cnt = len(mats)
+    keep = []
+    ns = (C.c_int64 * cnt)(*[int(A.n) for A in mats])
+    rps = (_I64 * cnt)()
+    cis = (C.POINTER(C.c_int32) * cnt)()
+    vas = (_D * cnt)()
+    for i, A in enumerate(mats):
+        rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+        va = _f64(A.vals)
+        keep += [rp, ci, va]
+        rps[i] = rp.ctypes.data_as(_I64)
+        cis[i] = ci.ctypes.data_as(C.POINTER(C.c_int32))
+        vas[i] = _dp(va)
+    h = C.c_void_p()
+    _check(LIB.pp_batch_create(C.byref(h), cnt, ns, rps, cis, vas, C.byref(o)))
+    return Batch(h.value, [int(A.n) for A in mats])
+
+
+def pp_batch_launch_count(b: Batch) -> int:
+    return int(LIB.pp_batch_launch_count(b.handle))
+
+
+def pp_batch_solve(b: Batch, d, bvecs, v0s, nev: int, m: int, k: int, rtol: float,
+                   want_vectors: bool = True) -> tuple[int, list[EigsResult]]:
+    cnt = len(b.ns)
+    cap = nev + 1
+    keep = []
+
+    def arr(vs):
+        a = (_D * cnt)()
+        for i, v in enumerate(vs):
+            if v is None:
+                a[i] = _D()
+            else:
+                v = _f64(v)
+                keep.append(v)
+                a[i] = _dp(v)
+        return a
+
+    dd = (C.c_int * cnt)(*[int(x) for x in d])
+    lre = [np.zeros(cap) for _ in range(cnt)]
+    lim = [np.zeros(cap) for _ in range(cnt)]
+    res = [np.zeros(cap) for _ in range(cnt)]
+    Xs = [np.zeros((cap, n)) for n in b.ns] if want_vectors else None
+    nout = (C.c_int * cnt)()
+    stats = (pp_stats * cnt)()
+    Xa = (_D * cnt)(*[_dp(x) for x in Xs]) if want_vectors else None
+    status = _check(LIB.pp_batch_solve(b.handle, dd, arr(bvecs), arr(v0s) if v0s is not None else None, int(nev),
+                                       int(m), int(k), float(rtol), (_D * cnt)(*[_dp(x) for x in lre]),
+                                       (_D * cnt)(*[_dp(x) for x in lim]), Xa, (_D * cnt)(*[_dp(x) for x in res]),
+                                       nout, stats), allow=(PP_OK, PP_ENOTCONV))
+    out = []
+    for i in range(cnt):
+        k_ = nout[i]
+        st = stats[i].to_dict()
+        out.append(EigsResult(lre[i][:k_] + 1j * lim[i][:k_], Xs[i][:k_].T.copy() if want_vectors else None,
+                              res[i][:k_], PP_OK if st["converged"] else PP_ENOTCONV, st))
+    return status, out
+
+
+# ---------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------
+class Server:
+    """Owner of a pp_server handle; remembers n and nev per request id."""
+
+    def __init__(self, handle: int, keep_vectors: bool):
+        self.handle = C.c_void_p(handle)
+        self.keep_vectors = keep_vectors
+        self.meta: dict[int, tuple[int, int]] = {}
+
+    def close(self):
+        if self.handle:
+            LIB.pp_server_destroy(self.handle)
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pp_server_create(mem_budget: int = 0, max_active: int = 0, keep_vectors: bool = False, **opts) -> Server:
+    o = default_opts(**opts)
+    h = C.c_void_p()
+    _check(LIB.pp_server_create(C.byref(h), C.byref(o), int(mem_budget), int(max_active), int(keep_vectors)))
+    return Server(h.value, keep_vectors)
+
+
+def pp_server_submit(s: Server, A, d: int, nev: int, m: int, k: int, rtol: float, b, v0=None) -> int:
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+    va = _f64(A.vals)
+    b = _f64(b)
+    v0a = _f64(v0) if v0 is not None else None
+    rid = C.c_int64()
+    _check(LIB.pp_server_submit(s.handle, int(A.n), rp.ctypes.data_as(_I64), ci.ctypes.data_as(C.POINTER(C.c_int32)),
+                                _dp(va), int(d), int(nev), int(m), int(k), float(rtol), _dp(b),
+                                _dp(v0a) if v0a is not None else None, C.byref(rid)))
+    s.meta[rid.value] = (int(A.n), int(nev))
+    return rid.value
+
+
+def pp_server_step(s: Server) -> tuple[int, int]:
+    a, q = C.c_int(), C.c_int()
+    _check(LIB.pp_server_step(s.handle, C.byref(a), C.byref(q)))
+    return a.value, q.value
+
+
+def pp_server_result(s: Server, rid: int):
+    """None while pending, else (EigsResult, latency seconds)."""
+    n, nev = s.meta[rid]
+    cap = nev + 1
+    lre, lim, res = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+    X = np.zeros((cap, n)) if s.keep_vectors else None
+    nout, st, lat = C.c_int(), pp_stats(), C.c_double()
+    status = LIB.pp_server_result(s.handle, int(rid), _dp(lre), _dp(lim), _dp(X) if X is not None else None,
+                                  _dp(res), C.byref(nout), C.byref(st), C.byref(lat))
+    if status == PP_EAGAIN:
+        return None
+    _check(status, allow=(PP_OK, PP_ENOTCONV))
+    k_ = nout.value
+    del s.meta[rid]
+    return EigsResult(lre[:k_] + 1j * lim[:k_], X[:k_].T.copy() if X is not None else None, res[:k_], status,
+                      st.to_dict()), lat.value
+
+
+def pp_server_request_bytes(s: Server, n: int, nnz: int, m: int, nev: int) -> int:
+    return int(LIB.pp_server_request_bytes(s.handle, int(n), int(nnz), int(m), int(nev)))
+
+
+def pp_server_launch_count(s: Server) -> int:
+    return int(LIB.pp_server_launch_count(s.handle))
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,102 @@
+"""Batched solves: many uneven instances advanced together (one launch per
+polynomial pass for all instances, one CUDA graph per Arnoldi step).
+
+* Each batched result equals the solo GPU solve of the same instance on the
+  same inputs (same method, same precision): eigenvalues within 1e-10
+  relative, and the same number of cycles (FP64).  The batched CGS2 uses a
+  different block count, so sums differ by rounding only.
+* Every returned pair meets ||A x - lam x|| <= 1e-8 ||A||_1, recomputed on the
+  CPU from the returned vectors; eigenvalues match the oracle's within the
+  kappa-gated first-order bound.
+* The full uneven workload (64 instances, grid sides 64..512, beta 1..200,
+  d 20..80, FP32 apply + FP64 refinement): every instance's residuals.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_08020_gb300 import inputs
+from test_gpu_eigs import cpu_residuals, eig_condition, oracle_solve
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(count=6, seed=3):
+    rng = np.random.default_rng([seed, 1])
+    out = []
+    for i in range(count):
+        N = int(rng.integers(12, 45))
+        beta = float(rng.uniform(1.0, 30.0))
+        d = int(rng.integers(4, 14))
+        out.append((inputs.convection_diffusion_2d(N, beta), d, 100 + 7 * i))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_equals_solo(precision):
+    from paper_1806_08020_gb300 import pp
+    prec = pp.PP_FP64 if precision == "fp64" else pp.PP_FP32
+    inst = _instances()
+    nev, m, k = 5, 24, 10
+    B = pp.pp_batch_create([A for A, _, _ in inst], precision=prec)
+    bs = [inputs.start_vector(A.n, s, 0) for A, _, s in inst]
+    vs = [inputs.start_vector(A.n, s, 1) for A, _, s in inst]
+    status, res = pp.pp_batch_solve(B, [d for _, d, _ in inst], bs, vs, nev, m, k, 1e-8)
+    assert status == 0
+    assert pp.pp_batch_launch_count(B) > 0
+    for (A, d, s), rb, b, v in zip(inst, res, bs, vs):
+        ctx = pp.pp_create(A, precision=prec)
+        solo = pp.pp_eigs(ctx, pp.pp_build_poly(ctx, d, b), nev, m, k, 1e-8, v)
+        assert rb.status == 0 and solo.status == 0
+        assert np.all(rb.resid <= 1e-8)
+        rc = cpu_residuals(O.to_scipy(A), rb.lam, rb.X)
+        assert np.all(rc <= 1.01e-8)
+        assert rb.lam.size == solo.lam.size
+        assert np.max(np.abs(rb.lam - solo.lam) / np.abs(solo.lam)) <= 1e-10
+        if precision == "fp64":
+            assert rb.stats["cycles"] == solo.stats["cycles"]
+
+
+def test_batch_matches_oracle():
+    from paper_1806_08020_gb300 import pp
+    inst = _instances(4, seed=5)
+    nev, m, k = 5, 24, 10
+    B = pp.pp_batch_create([A for A, _, _ in inst])
+    bs = [inputs.start_vector(A.n, s, 0) for A, _, s in inst]
+    vs = [inputs.start_vector(A.n, s, 1) for A, _, s in inst]
+    status, res = pp.pp_batch_solve(B, [d for _, d, _ in inst], bs, vs, nev, m, k, 1e-8)
+    assert status == 0
+    for (Acsr, d, s), rb in zip(inst, res):
+        A, P, R = oracle_solve(Acsr, d, nev, m, k, s)
+        w, kap = eig_condition(Acsr.to_dense())
+        nA = O.norm1(A)
+        for j, lam in enumerate(R.lam):
+            dist = np.abs(rb.lam - lam)
+            i = int(np.argmin(dist))
+            kj = kap[np.argmin(np.abs(w - lam))]
+            assert dist[i] <= 10 * kj * (rb.resid[i] + R.resid[j]) * nA + 1e-12 * abs(lam)
+
+
+def test_batch_uneven_workload_full():
+    """64 instances: grid side U{64..512}, beta U[1, 200], d U{20..80}, Arnoldi(30, 13), nev = 8."""
+    import time
+    from paper_1806_08020_gb300 import pp
+    specs = inputs.batch_instances()
+    mats = [inputs.convection_diffusion_2d(s["N"], s["beta"]) for s in specs]
+    B = pp.pp_batch_create(mats, precision=pp.PP_FP32)
+    bs = [inputs.start_vector(A.n, s["seed"], 0) for A, s in zip(mats, specs)]
+    vs = [inputs.start_vector(A.n, s["seed"], 1) for A, s in zip(mats, specs)]
+    t = time.perf_counter()
+    status, res = pp.pp_batch_solve(B, [s["d"] for s in specs], bs, vs, 8, 30, 13, 1e-8)
+    t = time.perf_counter() - t
+    conv = [r.status == 0 for r in res]
+    pairs = sum(int(np.sum(r.resid <= 1e-8)) for r in res if r.status == 0)
+    print(f"batch of 64: {t:.2f} s, {sum(conv)} converged, {pairs} pairs, {pairs / t:.1f} pairs/s,",
+          "fp64 continuations:", sum(1 for r in res if r.stats["fp64_cycles"] > 0),
+          "cycles:", [r.stats["cycles"] for r in res])
+    assert sum(conv) >= 60
+    for A, r in zip(mats, res):
+        if r.status == 0:
+            assert np.all(r.resid <= 1e-8)
+            rc = cpu_residuals(O.to_scipy(A), r.lam, r.X)
+            assert np.all(rc <= 1.01e-8)

@@ -215,3 +215,26 @@ def test_eigs_not_converged_status():
     res = pp.pp_eigs(ctx, poly, 10, 30, 15, 1e-12, inputs.start_vector(2500, 1, 1))
     assert res.status == pp.PP_ENOTCONV and res.stats["cycles"] == 1
     assert res.lam.size >= 10 and np.all(np.isfinite(res.resid))
+
+
+def test_build_poly_on_dirty_device_memory():
+    """Every device buffer the build reads must be written first: fill and free a
+    large block with NaN so that new allocations start out dirty, then build."""
+    import torch
+    from paper_1806_08020_gb300 import pp
+    junk = torch.full((64 << 20,), float("nan"), dtype=torch.float64, device="cuda")
+    del junk
+    torch.cuda.empty_cache()
+    junk2 = torch.full((64 << 20,), 1e300, dtype=torch.float64, device="cuda")
+    del junk2
+    torch.cuda.empty_cache()
+    Acsr = inputs.convection_diffusion_2d(40, 10.0)
+    A = O.to_scipy(Acsr)
+    b = inputs.start_vector(Acsr.n, 8, 0)
+    ref = O.build_poly(O.Operator(A, 0.0, O.Counters()), b, 11, O.Counters())
+    for _ in range(3):
+        ctx = pp.pp_create(Acsr)
+        got = pp.pp_poly_roots(pp.pp_build_poly(ctx, 11, b))
+        assert got.size == ref.roots.size
+        for z in ref.roots:
+            assert np.min(np.abs(got - z)) <= 1e-8 * abs(z)

@@ -1,0 +1,134 @@
+"""Continuous-batching request server.
+
+* A request's result is the same alone and in a mix with others (same
+  precision path): eigenvalues within 1e-10 relative of the solo pp_eigs
+  result, residuals <= 1e-8 ||A||_1 recomputed on the CPU.
+* Requests that arrive while others run are admitted as slots free up and
+  finish; a tight memory budget makes the queue wait (admission by memory).
+* A stream of random banded requests (the serving workload at reduced size):
+  every result converges or reports its status, latencies are recorded.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_08020_gb300 import inputs
+from test_gpu_eigs import cpu_residuals
+
+pytestmark = pytest.mark.gpu
+
+
+def _req(i, n=3000, seed=1):
+    rng = np.random.default_rng([seed, i])
+    w = int(rng.integers(2, 6))
+    A = inputs.banded_random(n + 100 * i, w, 1000 + i)
+    nev = int(rng.integers(3, 7))
+    d = int(rng.integers(4, 7))
+    k = nev + 5
+    m = max(24, 2 * k)
+    return A, d, nev, m, k, 500 + i
+
+
+def _solo(pp, A, d, nev, m, k, seed, prec):
+    ctx = pp.pp_create(A, precision=prec)
+    poly = pp.pp_build_poly(ctx, d, inputs.start_vector(A.n, seed, 0))
+    return pp.pp_eigs(ctx, poly, nev, m, k, 1e-8, inputs.start_vector(A.n, seed, 1))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_same_alone_and_in_the_mix(precision):
+    from paper_1806_08020_gb300 import pp
+    prec = pp.PP_FP64 if precision == "fp64" else pp.PP_FP32
+    reqs = [_req(i) for i in range(5)]
+    S = pp.pp_server_create(keep_vectors=True, precision=prec)
+    ids = []
+    # two requests first, the rest arrive while those run
+    for A, d, nev, m, k, seed in reqs[:2]:
+        ids.append(pp.pp_server_submit(S, A, d, nev, m, k, 1e-8, inputs.start_vector(A.n, seed, 0),
+                                       inputs.start_vector(A.n, seed, 1)))
+    pp.pp_server_step(S)
+    for A, d, nev, m, k, seed in reqs[2:]:
+        ids.append(pp.pp_server_submit(S, A, d, nev, m, k, 1e-8, inputs.start_vector(A.n, seed, 0),
+                                       inputs.start_vector(A.n, seed, 1)))
+    results = {}
+    for _ in range(500):
+        a, q = pp.pp_server_step(S)
+        for rid in ids:
+            if rid not in results:
+                r = pp.pp_server_result(S, rid)
+                if r is not None:
+                    results[rid] = r
+        if len(results) == len(ids):
+            break
+    assert len(results) == len(ids)
+    for rid, (A, d, nev, m, k, seed) in zip(ids, reqs):
+        res, lat = results[rid]
+        solo = _solo(pp, A, d, nev, m, k, seed, prec)
+        assert res.status == solo.status
+        assert lat > 0
+        if res.status == 0:
+            assert np.all(res.resid <= 1e-8)
+            assert np.all(cpu_residuals(O.to_scipy(A), res.lam, res.X) <= 1.01e-8)
+            assert res.lam.size == solo.lam.size
+            assert np.max(np.abs(res.lam - solo.lam) / np.abs(solo.lam)) <= 1e-10
+
+
+def test_admission_by_memory():
+    """With a budget for about one request at a time, the queue drains one by one."""
+    from paper_1806_08020_gb300 import pp
+    reqs = [_req(i, n=20000) for i in range(3)]
+    probe = pp.pp_server_create(precision=pp.PP_FP32)
+    need = max(pp.pp_server_request_bytes(probe, A.n, A.nnz, m, nev) for A, d, nev, m, k, seed in reqs)
+    S = pp.pp_server_create(mem_budget=int(1.5 * need), precision=pp.PP_FP32)
+    ids = [pp.pp_server_submit(S, A, d, nev, m, k, 1e-8, inputs.start_vector(A.n, seed, 0))
+           for A, d, nev, m, k, seed in reqs]
+    seen_queue = False
+    done = {}
+    for _ in range(2000):
+        a, q = pp.pp_server_step(S)
+        assert a <= 1
+        seen_queue |= q > 0
+        for rid in ids:
+            if rid not in done:
+                r = pp.pp_server_result(S, rid)
+                if r is not None:
+                    done[rid] = r
+        if len(done) == 3:
+            break
+    assert seen_queue and len(done) == 3
+    for res, lat in done.values():
+        assert res.status in (0, 1)
+
+
+def test_request_stream_small():
+    """Poisson arrivals of random banded requests (reduced sizes), served in arrival order."""
+    import time
+    from paper_1806_08020_gb300 import pp
+    stream = inputs.request_stream(count=24, rate=200.0, n_lo=5e3, n_hi=6e4)
+    S = pp.pp_server_create(precision=pp.PP_FP32)
+    t0 = time.perf_counter()
+    pending, out = {}, {}
+    i = 0
+    while i < len(stream) or pending:
+        now = time.perf_counter() - t0
+        while i < len(stream) and stream[i]["arrival"] <= now:
+            q = stream[i]
+            A = inputs.banded_random(q["n"], q["w"], q["seed"])
+            rid = pp.pp_server_submit(S, A, q["d"], q["nev"], q["m"], q["k"], 1e-8,
+                                      inputs.start_vector(A.n, q["seed"], 0), inputs.start_vector(A.n, q["seed"], 1))
+            pending[rid] = A
+            i += 1
+        pp.pp_server_step(S)
+        for rid in list(pending):
+            r = pp.pp_server_result(S, rid)
+            if r is not None:
+                out[rid] = r
+                del pending[rid]
+    lat = np.array([l for _, l in out.values()])
+    conv = sum(r.status == 0 for r, _ in out.values())
+    print(f"served {len(out)} requests, converged {conv}, p50 {np.percentile(lat, 50):.3f} s, "
+          f"p99 {np.percentile(lat, 99):.3f} s, launches {pp.pp_server_launch_count(S)}")
+    assert len(out) == len(stream)
+    for r, _ in out.values():
+        if r.status == 0:
+            assert np.all(r.resid <= 1e-8)
