@@ -65,8 +65,11 @@ typedef struct {
     int add_roots;      /* 1 (default): Section 7 box, extra copies of roots with large pof */
     int max_cycles;     /* Arnoldi cycles before PP_ENOTCONV; default 2000 */
     int refine_steps;   /* FP64 refinement steps for the mixed-precision path; default 4 */
-    int sell_c;         /* SELL chunk height; 0 = tuner (32) */
-    int sell_sigma;     /* SELL sorting window; 0 or 1 = no sorting */
+    int sell_c;         /* SELL chunk height: 16 or 32; 0 (default) = the tuner picks C and the
+                           block size of the product kernels by timing them on this matrix */
+    int sell_sigma;     /* SELL sorting window: must be 0 or 1 (rows keep their order) */
+    int sell_index;     /* SELL column indices: 0 (default) = 16-bit offsets col - row when every
+                           |col - row| < 2^15, else 32-bit; 32 = always 32-bit */
     void *stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
 } pp_opts;
 
@@ -110,6 +113,15 @@ int64_t pp_launch_count(const pp_ctx *ctx);
 
 /* ||A||_1 (maximum absolute column sum) and the shift sigma used for the target. */
 pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);
+
+/*
+ * pp_format_info — the device format of A chosen at pp_create: fmt
+ * (PP_FMT_CSR or PP_FMT_SELL), the SELL chunk height (0 for CSR), the column
+ * index width in bits (16 or 32), the block size of the product kernels, and
+ * the stored entries including SELL padding.  Any output pointer may be NULL.
+ */
+pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bits, int *threads,
+                         int64_t *stored);
 
 /*
  * pp_build_poly — GMRES polynomial of degree d (Section 2 box, step 1):
@@ -202,7 +214,9 @@ pp_status pp_eigs(pp_ctx *ctx, const pp_poly *p, int nev, int m, int k, double r
  * h2 = V^T w1, w2 = w1 - V h2, and writes v = w2 / ||w2|| to v_dev (device, n;
  * may not alias V or w).  w is overwritten by w1.  h_host (host, j + 1
  * doubles) receives h1 + h2 followed by ||w2||.  Synchronises the stream.
- * Requires 1 <= j <= 128.
+ * Requires 1 <= j <= 128.  Arithmetic: FP64 throughout for FP64 contexts; for
+ * FP32 contexts, h1 and both updates in FP32, h2 as a compensated FP32 dot
+ * product (about twice FP32 precision), norms in FP64.
  */
 pp_status pp_orthogonalize(pp_ctx *ctx, const void *V_dev, int64_t ldv, int j, void *w_dev, void *v_dev,
                            double *h_host);

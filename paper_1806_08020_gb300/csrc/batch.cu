@@ -29,8 +29,10 @@ namespace {
 
 struct Req {
     int64_t id = -1;
-    pp_ctx *c = nullptr;
+    pp_ctx *c = nullptr;     // the context the request currently runs on
+    pp_ctx *home = nullptr;  // its own context (c, or c's FP64 twin after a switch)
     bool own_ctx = false;
+    bool to64 = false;       // leaves the FP32 engine for the FP64 one
     pp_poly *poly = nullptr;
     std::unique_ptr<Driver> D;
     void *V = nullptr, *V2 = nullptr;
@@ -38,7 +40,7 @@ struct Req {
     int d = 0, nev = 0, m = 0, k = 0;
     double rtol = 1e-8;
     int j0 = 0;
-    bool done = false, conv = false, written = false;
+    bool done = false, conv = false;
     pp_status status = PP_OK;
     Cycle cy;
     RitzOut R;
@@ -46,7 +48,7 @@ struct Req {
     pp_stats S{};
     std::vector<ppk::BatchPassEntry> passes;
     int nblk = 0, blk0 = 0;
-    int64_t launches0 = 0;
+    int64_t launches0 = 0, cycles32 = 0;
     bool want_x = false;
     std::vector<double> lam_re, lam_im, resid, X;  // results
     int nout = 0;
@@ -67,9 +69,18 @@ struct Req {
         dev.clear();
         delete poly;
         poly = nullptr;
-        if (own_ctx && c) pp_destroy(c);
-        if (own_ctx) c = nullptr;
+        if (own_ctx && home) pp_destroy(home);
+        if (own_ctx) c = home = nullptr;
     }
+    void dfree(void *p) {
+        for (auto it = dev.begin(); it != dev.end(); ++it)
+            if (*it == p) {
+                cudaFree(p);
+                dev.erase(it);
+                return;
+            }
+    }
+    int64_t launches_now() const { return home->launches + (home->twin ? home->twin->launches : 0); }
     pp_status dalloc(void **p, size_t bytes) {
         cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
         if (e != cudaSuccess) {
@@ -90,8 +101,9 @@ int64_t request_bytes(int64_t n, int64_t nnz, int m, int nev, int esz) {
     int64_t vecs = 8 * ldv * esz + 2 * (int64_t)(m + 1) * ldv * esz;
     int64_t test = 2 * (int64_t)(nev + 2) * ldv * 8 + (int64_t)(nev + 2) * ldv * esz;
     int64_t small = (int64_t)(m + 1) * m * 8 + 128 * 128 * 8 + 1300000 * 8;
-    int64_t twin = 0;  // FP64 copy of an FP32 request (used only if FP32 cannot reach rtol)
-    if (esz != 8) twin = nnz * 12 * 13 / 10 + nnz * 12 + 8 * n + 8 * ldv * 8 + 1300000 * 8;
+    int64_t twin = 0;  // FP64 copy of an FP32 request and its basis (if FP32 cannot reach rtol)
+    if (esz != 8)
+        twin = nnz * 12 * 13 / 10 + nnz * 12 + 8 * n + 8 * ldv * 8 + 1300000 * 8 + 2 * (int64_t)(m + 1) * ldv * (8 - esz);
     return mat + vecs + test + small + twin;
 }
 
@@ -152,11 +164,43 @@ class Engine {
     // Build the request's polynomial and Arnoldi state; it joins the set.
     pp_status start(Req *r, const double *b, const double *v0) {
         pp_ctx *c = r->c;
-        r->launches0 = c->launches;
+        r->home = c;
+        r->launches0 = r->launches_now();
         r->sw = MixedSwitch(r->rtol);
         r->t_start = now();
         CKS(pp_build_poly(c, r->d, b, &r->poly));
         r->passes = pass_schedule(r->poly);
+        return begin(r, v0);
+    }
+
+    // A request whose FP32 cycles and refinement could not reach rtol joins
+    // the FP64 engine: the FP32 basis is released and FP64 Arnoldi cycles on
+    // the FP64 twin start from the sum of the refined Ritz vectors (the same
+    // polynomial; the cycle count continues).
+    pp_status start64(Req *r) {
+        pp_ctx *c = r->c;
+        std::vector<double> Yh, w0(c->n, 0.0);
+        CKS(download_vecs(c, r->D->Y64, c->ldv(), r->cy.sl.nw, Yh, ppk::F64));
+        for (int q = 0; q < r->cy.sl.nw; ++q)
+            for (int64_t x = 0; x < c->n; ++x) w0[x] += Yh[(size_t)q * c->n + x];
+        r->D.reset();
+        r->dfree(r->V);
+        r->dfree(r->V2);
+        r->dfree(r->dH);
+        r->c = c->twin;
+        r->to64 = false;
+        r->done = false;
+        r->conv = false;
+        r->status = PP_OK;
+        r->cycles32 = r->S.cycles;
+        return begin(r, w0.data());
+    }
+
+  private:
+    // Basis slabs, Hessenberg and test buffers on the request's current
+    // context, v_1 = v0 / ||v0|| (all ones when v0 is null); joins the set.
+    pp_status begin(Req *r, const double *v0) {
+        pp_ctx *c = r->c;
         const int64_t ldv = c->ldv();
         const int ldh = r->m + 1;
         CKS(r->dalloc(&r->V, (size_t)ldv * (r->m + 1) * c->esz));
@@ -172,12 +216,15 @@ class Engine {
         if (!(nv > 0)) return pp_fail(PP_EINVAL, "zero start vector");
         CKS(upload_vec(c, v.data(), 1.0 / nv, r->V));
         CK(cudaMemsetAsync(r->dH, 0, (size_t)ldh * r->m * 8, st));
-        r->S.dots = 1;
-        r->S.vops = 2;
+        r->j0 = 0;
+        r->S.dots += 1;
+        r->S.vops += 2;
         act.push_back(r);
         dirty = true;
         return PP_OK;
     }
+
+  public:
 
     // Drop finished requests from the set; returns them.
     std::vector<Req *> retire() {
@@ -235,11 +282,14 @@ class Engine {
     DevArray<ppk::BatchCgsInst> d_cinst;
     DevArray<ppk::BatchPassEntry> d_tab;
     DevArray<int2> d_items;
+    DevArray<ppk::BatchPassEntry> d_tune_tab;
     DevArray<int> d_lo, d_hi;
+    int64_t tuned_rows = 0;
     std::vector<ppk::BatchPassInst> pinst;
     std::vector<ppk::BatchCgsInst> cinst;
     std::vector<cudaGraphExec_t> graphs;
     int Pmax = 0, blocks = 0, nitems = 0;
+    int groups = 8, grid_per_sm = 8;  // batched-pass block shape (tuned)
     bool dirty = true;
     ppk::Prec pr = ppk::F32;
     double *Z = nullptr, *dG = nullptr;
@@ -254,7 +304,8 @@ class Engine {
     void launch_step(int jj) {
         const int count = (int)act.size();
         for (int t = 0; t < Pmax; ++t)
-            ppk::launch_pass_batch(pr, d_pinst.p, d_tab.p + (size_t)t * count, d_items.p, nitems, d_lo.p, d_hi.p, jj, st);
+            ppk::launch_pass_batch(pr, d_pinst.p, d_tab.p + (size_t)t * count, d_items.p, nitems, d_lo.p, d_hi.p, jj,
+                                   groups, grid_per_sm, st);
         for (int mode = 0; mode < 3; ++mode)
             ppk::launch_cgs_batch(pr, d_cinst.p, count, blocks, d_lo.p, d_hi.p, mode, jj, st);
         ppk::launch_scale_batch(pr, d_cinst.p, count, blocks, d_lo.p, d_hi.p, jj, st);
@@ -269,15 +320,13 @@ class Engine {
         pinst.assign(count, {});
         cinst.assign(count, {});
         std::vector<ppk::BatchPassEntry> tab((size_t)Pmax * count);
-        std::vector<int2> items;
-        blocks = 0;
+            blocks = 0;
         for (int i = 0; i < count; ++i) {
             Req *r = act[i];
             pp_ctx *c = r->c;
             if (c->A.prec != pr || c->A.fmt != 2) return pp_fail(PP_EINVAL, "engine: mixed precisions or non-SELL matrix");
             const auto &A = c->A.sell;
-            pinst[i] = {A.n, A.nslices, A.slice_ptr, A.col, A.val, c->sigma, r->V, c->ldv(), c->vec[6], c->vec[0],
-                        c->vec[1], c->vec[2]};
+            pinst[i] = {A, c->sigma, r->V, c->ldv(), c->vec[6], c->vec[0], c->vec[1], c->vec[2]};
             r->nblk = ppk::cgs_batch_blocks((int)c->n);
             r->blk0 = blocks;
             blocks += r->nblk;
@@ -286,21 +335,88 @@ class Engine {
             for (int t = 0; t < Pmax; ++t)
                 tab[(size_t)t * count + i] =
                     t < (int)r->passes.size() ? r->passes[t] : ppk::BatchPassEntry{-1, 0, 0, 0, 0, 0};
-            for (int s0 = 0; s0 < A.nslices; s0 += 8) items.push_back(make_int2(i, s0));
         }
-        nitems = (int)items.size();
         CKS(d_pinst.ensure(count));
         CKS(d_cinst.ensure(count));
         CKS(d_tab.ensure(tab.size()));
-        CKS(d_items.ensure(items.size()));
         CKS(d_lo.ensure(count));
         CKS(d_hi.ensure(count));
         CK(cudaMemcpyAsync(d_pinst.p, pinst.data(), sizeof(pinst[0]) * count, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(d_cinst.p, cinst.data(), sizeof(cinst[0]) * count, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(d_tab.p, tab.data(), sizeof(tab[0]) * tab.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(d_items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
+        int64_t rows = 0;
+        for (Req *r : act) rows += r->c->n;
+        if (tuned_rows == 0 || rows > 2 * tuned_rows || 2 * rows < tuned_rows) {
+            CKS(tune_pass());
+            tuned_rows = rows;
+        }
+        CKS(upload_items(groups));
         CK(cudaStreamSynchronize(st));
         dirty = false;
+        return PP_OK;
+    }
+
+    // Work items (instance, first 32-row group), `g` groups per block.
+    pp_status upload_items(int g) {
+        std::vector<int2> items;
+        for (int i = 0; i < (int)act.size(); ++i) {
+            const int ngroups = (int)((act[i]->c->n + 31) / 32);
+            for (int g0 = 0; g0 < ngroups; g0 += g) items.push_back(make_int2(i, g0));
+        }
+        nitems = (int)items.size();
+        CKS(d_items.ensure(items.size()));
+        CK(cudaMemcpyAsync(d_items.p, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
+        return PP_OK;
+    }
+
+    // Batched-pass tuner: the block shape (32-row groups per block: 64 to 512
+    // threads) and the grid (blocks per SM) that run one product with A of
+    // every instance fastest, timed with CUDA events on the engine's stream
+    // (fastest of five launches after two warm-up ones).  The timed pass reads
+    // v_1 and writes the operator output, which the first real step overwrites.
+    // Re-run when the set's total size changes by more than 2x.
+    pp_status tune_pass() {
+        const int count = (int)act.size();
+        std::vector<ppk::BatchPassEntry> tab(count, ppk::BatchPassEntry{0, 0, 1, 0, 0.0, 0.0});
+        std::vector<int> lo(count, 0), hi(count, 1);
+        CKS(d_tune_tab.ensure(count));
+        CK(cudaMemcpyAsync(d_tune_tab.p, tab.data(), sizeof(tab[0]) * count, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_lo.p, lo.data(), 4 * count, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_hi.p, hi.data(), 4 * count, cudaMemcpyHostToDevice, st));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        double best = INFINITY;
+        for (int g : {2, 4, 8, 16}) {
+            pp_status s = upload_items(g);
+            if (s < 0) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return s;
+            }
+            for (int gps : {4, 8, 16}) {
+                double t = INFINITY;
+                for (int it = 0; it < 7; ++it) {
+                    cudaEventRecord(e0, st);
+                    ppk::launch_pass_batch(pr, d_pinst.p, d_tune_tab.p, d_items.p, nitems, d_lo.p, d_hi.p, 0, g, gps,
+                                           st);
+                    cudaEventRecord(e1, st);
+                    float ms = 0;
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (it >= 2) t = std::min(t, (double)ms);
+                }
+                launches += 7;
+                if (t < best) {
+                    best = t;
+                    groups = g;
+                    grid_per_sm = gps;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CK(cudaGetLastError());
         return PP_OK;
     }
 
@@ -324,7 +440,6 @@ class Engine {
         pp_ctx *c = r->c;
         r->done = true;
         r->t_done = now();
-        if (r->written) return;
         const int cap = r->nev + 1;
         r->lam_re.assign(cap, 0.0);
         r->lam_im.assign(cap, 0.0);
@@ -348,9 +463,9 @@ class Engine {
         r->nout = r->cy.sl.nw;
         r->S.converged = r->conv ? 1 : 0;
         r->S.max_resid = maxres;
-        r->S.kernel_launches = c->launches - r->launches0;
+        r->S.kernel_launches = r->launches_now() - r->launches0;
         r->S.t_total = r->t_done - r->t_start;
-        r->S.fp64_cycles = c->A.prec == ppk::F64 ? r->S.cycles : 0;
+        r->S.fp64_cycles = c->A.prec == ppk::F64 ? r->S.cycles - r->cycles32 : 0;
     }
 
     pp_status host_step(int i) {
@@ -375,6 +490,7 @@ class Engine {
             return PP_OK;
         }
         r->S.nconv = r->R.nconv;
+        trace_cycle("req", r, r->S.cycles, c->A.prec == ppk::F64 ? 64 : 32, r->R, r->R.all ? "converged" : nullptr);
         if (r->R.all) {
             r->conv = true;
             r->status = PP_OK;
@@ -384,11 +500,16 @@ class Engine {
         const bool last = r->S.cycles >= max_cycles;
         if (c->A.prec != ppk::F64 && r->sw.should_refine(r->R, last)) {
             CKS(shared_refinement_basis(r));
-            s = r->D->refine(r->cy.sl, r->nev, r->R, r->rtol, refine_steps, 3, r->S);
+            s = r->D->refine(r->poly, r->cy.sl, r->nev, r->R, r->rtol, refine_steps, 3, r->S);
+            trace_cycle("req", r, r->S.cycles, 64, r->R, r->R.all ? "refined: converged" : "refined");
             r->conv = s >= 0 && r->R.all;
             r->status = s < 0 ? s : (r->conv ? PP_OK : PP_ENOTCONV);
-            if (s < 0 || r->conv || last || c->twin) {
-                if (s >= 0 && !r->conv && c->twin && !last) fp64_continuation(r);
+            if (s >= 0 && !r->conv && c->twin && !last) {
+                r->to64 = true;  // continues in the FP64 engine (start64)
+                r->done = true;
+                return PP_OK;
+            }
+            if (s < 0 || r->conv || last) {
                 finish(r);
                 return PP_OK;
             }
@@ -417,42 +538,6 @@ class Engine {
         CK(cudaMemcpyAsync(d_pinst.p + i, &pinst[i], sizeof(pinst[i]), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(d_cinst.p + i, &cinst[i], sizeof(cinst[i]), cudaMemcpyHostToDevice, st));
         return PP_OK;
-    }
-
-    // Too non-normal for FP32: finish this request in FP64 (pp_eigs on the FP64
-    // twin, started from the sum of the refined Ritz vectors).
-    void fp64_continuation(Req *r) {
-        pp_ctx *c = r->c;
-        std::vector<double> Yh, w0(c->n, 0.0);
-        if (download_vecs(c, r->D->Y64, c->ldv(), r->cy.sl.nw, Yh, ppk::F64) < 0) return;
-        for (int q = 0; q < r->cy.sl.nw; ++q)
-            for (int64_t x = 0; x < c->n; ++x) w0[x] += Yh[(size_t)q * c->n + x];
-        pp_ctx *tw = c->twin;
-        const int maxc = tw->opts.max_cycles;
-        tw->opts.max_cycles = std::max<int>(1, max_cycles - (int)r->S.cycles);
-        const int cap = r->nev + 1;
-        r->lam_re.assign(cap, 0.0);
-        r->lam_im.assign(cap, 0.0);
-        r->resid.assign(cap, 0.0);
-        if (r->want_x) r->X.assign((size_t)c->n * cap, 0.0);
-        pp_stats S2{};
-        int64_t l0 = tw->launches;
-        pp_status s = pp_eigs(tw, r->poly, r->nev, r->m, r->k, r->rtol, w0.data(), r->lam_re.data(), r->lam_im.data(),
-                              r->want_x ? r->X.data() : nullptr, r->resid.data(), &r->nout, &S2);
-        tw->opts.max_cycles = maxc;
-        launches += tw->launches - l0;
-        if (s < 0) return;
-        r->status = s;
-        r->conv = s == PP_OK;
-        r->written = true;
-        S2.fp64_cycles = S2.cycles;
-        S2.cycles += r->S.cycles;
-        S2.mvps += r->S.mvps;
-        S2.dots += r->S.dots;
-        S2.vops += r->S.vops;
-        S2.kernel_launches = (c->launches - r->launches0) + (tw->launches - l0);
-        S2.t_total = now() - r->t_start;
-        r->S = S2;
     }
 };
 
@@ -490,7 +575,7 @@ struct pp_server {
     std::deque<std::unique_ptr<Req>> queue;
     std::vector<std::unique_ptr<Req>> running;
     std::map<int64_t, std::unique_ptr<Req>> finished;
-    Engine eng;
+    Engine eng, eng64;  // FP32 (or FP64) cycles; FP64 continuations of FP32 requests
     ~pp_server() {
         if (stream) cudaStreamSynchronize(stream);
         running.clear();
@@ -546,10 +631,12 @@ pp_status pp_batch_solve(pp_batch *b, const int *d, const double *const *bvec, c
         return pp_fail(PP_EINVAL, "pp_batch_solve: need 1 <= nev < k < m <= 127, rtol > 0 and outputs");
     for (pp_ctx *c : b->ctx)
         if (m >= c->n) return pp_fail(PP_EINVAL, "pp_batch_solve: m must be below every n");
-    Engine eng;
-    eng.st = b->stream;
-    eng.max_cycles = b->opts.max_cycles;
-    eng.refine_steps = b->opts.refine_steps;
+    Engine eng, eng64;  // FP32 (or FP64) cycles; FP64 continuations of FP32 requests
+    for (Engine *e : {&eng, &eng64}) {
+        e->st = b->stream;
+        e->max_cycles = b->opts.max_cycles;
+        e->refine_steps = b->opts.refine_steps;
+    }
     std::vector<std::unique_ptr<Req>> reqs;
     int64_t l0 = 0;
     for (pp_ctx *c : b->ctx) l0 += c->launches + (c->twin ? c->twin->launches : 0);
@@ -565,9 +652,12 @@ pp_status pp_batch_solve(pp_batch *b, const int *d, const double *const *bvec, c
         CKS(eng.start(r.get(), bvec[i], v0 ? v0[i] : nullptr));
         reqs.push_back(std::move(r));
     }
-    while (!eng.act.empty()) {
+    while (!eng.act.empty() || !eng64.act.empty()) {
         CKS(eng.cycle());
-        eng.retire();
+        CKS(eng64.cycle());
+        for (Req *r : eng.retire())
+            if (r->to64) CKS(eng64.start64(r));
+        eng64.retire();
     }
     pp_status worst = PP_OK;
     for (int i = 0; i < b->count; ++i) {
@@ -583,7 +673,7 @@ pp_status pp_batch_solve(pp_batch *b, const int *d, const double *const *bvec, c
     }
     int64_t l1 = 0;
     for (pp_ctx *c : b->ctx) l1 += c->launches + (c->twin ? c->twin->launches : 0);
-    b->launches += eng.launches + (l1 - l0);
+    b->launches += eng.launches + eng64.launches + (l1 - l0);
     if (worst == PP_ENOTCONV) return pp_fail(PP_ENOTCONV, "pp_batch_solve: some instances did not converge");
     return worst;
 }
@@ -611,9 +701,11 @@ pp_status pp_server_create(pp_server **out, const pp_opts *opts, int64_t mem_bud
     s->budget = mem_budget;
     s->max_active = max_active > 0 ? max_active : 256;
     s->keep_vectors = keep_vectors;
-    s->eng.st = s->stream;
-    s->eng.max_cycles = s->opts.max_cycles;
-    s->eng.refine_steps = s->opts.refine_steps;
+    for (Engine *e : {&s->eng, &s->eng64}) {
+        e->st = s->stream;
+        e->max_cycles = s->opts.max_cycles;
+        e->refine_steps = s->opts.refine_steps;
+    }
     *out = s;
     return PP_OK;
 }
@@ -686,7 +778,17 @@ pp_status pp_server_step(pp_server *s, int *active, int *queued) {
         s->running.push_back(std::move(r));
     }
     CKS(s->eng.cycle());
+    CKS(s->eng64.cycle());
+    std::vector<Req *> out = s->eng64.retire();
     for (Req *r : s->eng.retire()) {
+        if (!r->to64) {
+            out.push_back(r);
+        } else if (s->eng64.start64(r) < 0) {
+            r->status = PP_ECUDA;
+            out.push_back(r);
+        }
+    }
+    for (Req *r : out) {
         for (auto it = s->running.begin(); it != s->running.end(); ++it)
             if (it->get() == r) {
                 std::unique_ptr<Req> own = std::move(*it);
@@ -725,7 +827,7 @@ pp_status pp_server_result(pp_server *s, int64_t id, double *lam_re, double *lam
     return r->status;
 }
 
-int64_t pp_server_launch_count(const pp_server *s) { return s ? s->eng.launches : 0; }
+int64_t pp_server_launch_count(const pp_server *s) { return s ? s->eng.launches + s->eng64.launches : 0; }
 
 int64_t pp_server_request_bytes(const pp_server *s, int64_t n, int64_t nnz, int m, int nev) {
     if (!s) return -1;

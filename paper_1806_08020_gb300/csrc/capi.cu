@@ -481,6 +481,85 @@ pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_
 
 }  // extern "C"
 
+// Stored entries of SELL-C (C = 1 << cs): each slice padded to its longest row.
+static int64_t sell_padded(int64_t n, const int64_t *rowptr, int cs) {
+    const int64_t C = (int64_t)1 << cs;
+    int64_t tot = 0;
+    for (int64_t s0 = 0; s0 < n; s0 += C) {
+        int64_t w = 0;
+        for (int64_t i = s0; i < std::min(n, s0 + C); ++i) w = std::max(w, rowptr[i + 1] - rowptr[i]);
+        tot += w * C;
+    }
+    return tot;
+}
+
+// SELL-C of the device CSR: slice pointers on the host, fill on the device;
+// the allocations are returned in mem (the tuner frees the losers).
+static pp_status build_sell(pp_ctx *c, ppk::Prec pr, int64_t n, const int64_t *rowptr, int cs, bool off16,
+                            const int *d_rowptr, const int *d_col, const double *d_val, ppk::SellView &out,
+                            std::vector<void *> &mem) {
+    const int64_t C = (int64_t)1 << cs;
+    const int nslices = (int)((n + C - 1) / C);
+    std::vector<int> sptr(nslices + 1, 0);
+    for (int s = 0; s < nslices; ++s) {
+        int64_t w = 0;
+        for (int64_t i = s * C; i < std::min(n, (s + 1) * C); ++i) w = std::max(w, rowptr[i + 1] - rowptr[i]);
+        sptr[s + 1] = sptr[s] + (int)(w * C);
+    }
+    const int64_t padded = sptr[nslices];
+    int *d_sptr = nullptr, *d_scol = nullptr;
+    short *d_soff = nullptr;
+    void *d_sval = nullptr;
+    pp_status st;
+    if ((st = dmalloc(c, (void **)&d_sptr, (nslices + 1) * 4)) < 0) return st;
+    mem.push_back(d_sptr);
+    if (off16) {
+        if ((st = dmalloc(c, (void **)&d_soff, padded * 2)) < 0) return st;
+        mem.push_back(d_soff);
+    } else {
+        if ((st = dmalloc(c, (void **)&d_scol, padded * 4)) < 0) return st;
+        mem.push_back(d_scol);
+    }
+    if ((st = dmalloc(c, &d_sval, padded * c->esz)) < 0) return st;
+    mem.push_back(d_sval);
+    CK(cudaMemcpyAsync(d_sptr, sptr.data(), (nslices + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+    ppk::launch_sell_fill(pr, (int)n, nslices, cs, d_rowptr, d_col, d_val, d_sptr, d_scol, d_soff, d_sval, c->stream);
+    CK(cudaGetLastError());
+    out = {(int)n, nslices, cs, d_sptr, d_scol, d_soff, d_sval};
+    return PP_OK;
+}
+
+// Seconds per product y = A x with this format and block size: the fastest of
+// five launches after two warm-up ones, CUDA events on the context's stream.
+static double time_product(pp_ctx *c, const ppk::Matrix &M) {
+    ppk::StepArgs a;
+    a.x = c->vec[0];
+    a.y = c->vec[1];
+    a.plain = 1;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return -1;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return -1;
+    }
+    double best = INFINITY;
+    for (int it = 0; it < 7; ++it) {
+        cudaEventRecord(e0, c->stream);
+        ppk::launch_step(M, a, c->stream);
+        cudaEventRecord(e1, c->stream);
+        float ms = 0;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            best = -1;
+            break;
+        }
+        if (it >= 2) best = std::min(best, (double)ms * 1e-3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return best;
+}
+
 pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind,
                              const double *vals, const pp_opts *opts, int make_twin) {
     if (!out || n <= 0 || !rowptr || !colind || !vals) return pp_fail(PP_EINVAL, "pp_create: bad arguments");
@@ -550,22 +629,41 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     if ((st = dmalloc(c, (void **)&d_rowptr, (n + 1) * 4)) < 0 || (st = dmalloc(c, (void **)&d_col, nnz * 4)) < 0 ||
         (st = dmalloc(c, (void **)&d_val, nnz * 8)) < 0)
         return fail(st);
-    if (cudaMemcpy(d_rowptr, rp32.data(), (n + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d_col, colind, nnz * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d_val, vals, nnz * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+    // stream-ordered uploads: the context's stream does not synchronise with the legacy stream
+    if (cudaMemcpyAsync(d_rowptr, rp32.data(), (n + 1) * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_col, colind, nnz * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_val, vals, nnz * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return fail(pp_fail(PP_ECUDA, "pp_create: upload failed"));
-    // format choice: SELL-32 unless its padding exceeds 30 % (then CSR)
-    int nslices = (int)((n + 31) / 32);
-    std::vector<int> slen(nslices, 0);
-    for (int64_t i = 0; i < n; ++i) {
-        int l = (int)(rowptr[i + 1] - rowptr[i]);
-        slen[i / 32] = std::max(slen[i / 32], l);
+    // format: SELL-C unless its padding exceeds 30 % (then CSR); C and the
+    // block size of the product kernels from the tuner unless opts fix C
+    if (c->opts.sell_c != 0 && c->opts.sell_c != 16 && c->opts.sell_c != 32)
+        return fail(pp_fail(PP_EINVAL, "pp_create: sell_c must be 0, 16 or 32"));
+    if (c->opts.sell_sigma > 1) return fail(pp_fail(PP_EINVAL, "pp_create: sell_sigma must be 0 or 1"));
+    if (c->opts.sell_index != 0 && c->opts.sell_index != 32)
+        return fail(pp_fail(PP_EINVAL, "pp_create: sell_index must be 0 or 32"));
+    std::vector<int> cands;
+    if (c->opts.sell_c) cands.push_back(c->opts.sell_c == 16 ? 4 : 5);
+    else cands = {5, 4};
+    int64_t best_pad = INT64_MAX;
+    {
+        std::vector<int> fit;  // candidates whose padded size fits 32-bit slice pointers
+        for (int cs : cands) {
+            int64_t pd = sell_padded(n, rowptr, cs);
+            best_pad = std::min(best_pad, pd);
+            if (pd < ((int64_t)1 << 31)) fit.push_back(cs);
+        }
+        cands = fit;
     }
-    int64_t padded = 0;
-    for (int s = 0; s < nslices; ++s) padded += (int64_t)slen[s] * 32;
     int fmt = c->opts.format;
-    if (fmt == PP_FMT_AUTO) fmt = (padded <= (int64_t)(1.3 * (double)nnz) + 32 * 8) ? PP_FMT_SELL : PP_FMT_CSR;
-    if (padded >= ((int64_t)1 << 31)) fmt = PP_FMT_CSR;
+    if (fmt == PP_FMT_AUTO) fmt = (best_pad <= (int64_t)(1.3 * (double)nnz) + 32 * 8) ? PP_FMT_SELL : PP_FMT_CSR;
+    if (cands.empty()) fmt = PP_FMT_CSR;
+    bool off16 = c->opts.sell_index == 0;
+    for (int64_t i = 0; i < n && off16; ++i)
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            if (std::llabs((long long)colind[k] - (long long)i) > 32767) {
+                off16 = false;
+                break;
+            }
     ppk::Matrix M;
     M.n = (int)n;
     M.prec = pr;
@@ -576,20 +674,46 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         ppk::launch_csr_convert(pr, nnz, d_val, v32, c->stream);
         M.csr.val = v32;
     }
+    // scratch vectors (the tuner times products with them)
+    for (int i = 0; i < 8; ++i)
+        if ((st = dmalloc(c, &c->vec[i], (size_t)c->ldv() * c->esz)) < 0) return fail(st);
+    if (cudaMemsetAsync(c->vec[0], 0, (size_t)c->ldv() * c->esz, c->stream) != cudaSuccess)
+        return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
+    c->stored = nnz;
     if (fmt == PP_FMT_SELL) {
-        std::vector<int> sptr(nslices + 1, 0);
-        for (int s = 0; s < nslices; ++s) sptr[s + 1] = sptr[s] + slen[s] * 32;
-        int *d_sptr = nullptr, *d_scol = nullptr;
-        void *d_sval = nullptr;
-        if ((st = dmalloc(c, (void **)&d_sptr, (nslices + 1) * 4)) < 0 ||
-            (st = dmalloc(c, (void **)&d_scol, padded * 4)) < 0 || (st = dmalloc(c, &d_sval, padded * c->esz)) < 0)
-            return fail(st);
-        if (cudaMemcpy(d_sptr, sptr.data(), (nslices + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(pp_fail(PP_ECUDA, "pp_create: upload failed"));
-        ppk::launch_sell_fill(pr, (int)n, d_rowptr, d_col, d_val, d_sptr, d_scol, d_sval, c->stream);
-        if (cudaGetLastError() != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: SELL fill failed"));
         M.fmt = 2;
-        M.sell = {(int)n, nslices, d_sptr, d_scol, d_sval};
+        std::vector<int> threads = {256};
+        if (!c->opts.sell_c) threads = {128, 256, 512};
+        const bool tune = cands.size() * threads.size() > 1;
+        double best_t = INFINITY;
+        int best_threads = 256;
+        ppk::SellView best{};
+        std::vector<void *> best_mem;
+        for (int cs : cands) {
+            ppk::SellView sv{};
+            std::vector<void *> mem;
+            if ((st = build_sell(c, pr, n, rowptr, cs, off16, d_rowptr, d_col, d_val, sv, mem)) < 0) return fail(st);
+            M.sell = sv;
+            bool better = false;
+            for (int t : threads) {
+                M.threads = t;
+                double tt = tune ? time_product(c, M) : 0.0;
+                if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
+                if (tt < best_t) {
+                    best_t = tt;
+                    best_threads = t;
+                    better = true;
+                }
+            }
+            for (void *q : better ? best_mem : mem) dfree(c, q);
+            if (better) {
+                best = sv;
+                best_mem = mem;
+            }
+        }
+        M.sell = best;
+        M.threads = best_threads;
+        c->stored = sell_padded(n, rowptr, best.cshift);
     } else {
         M.fmt = 1;
     }
@@ -600,12 +724,10 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     c->A64.fmt = 1;
     c->A64.csr = {(int)n, d_rowptr, d_col, d_val};
     if (pr == ppk::F64) c->A64 = M;
-    // scratch vectors
-    for (int i = 0; i < 8; ++i)
-        if ((st = dmalloc(c, &c->vec[i], (size_t)c->ldv() * c->esz)) < 0) return fail(st);
     if ((st = dmalloc(c, (void **)&c->d_ticket, 64)) < 0 || (st = dmalloc(c, (void **)&c->d_small, 4096 * 8)) < 0)
         return fail(st);
-    if (cudaMemset(c->d_ticket, 0, 64) != cudaSuccess || cudaMemset(c->d_small, 0, 4096 * 8) != cudaSuccess)
+    if (cudaMemsetAsync(c->d_ticket, 0, 64, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_small, 0, 4096 * 8, c->stream) != cudaSuccess)
         return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
     if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)n) * 130)) < 0) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: setup kernels failed"));
@@ -672,6 +794,17 @@ pp_status pp_matrix_info(const pp_ctx *c, double *norm1, double *sigma) {
     if (!c) return pp_fail(PP_EINVAL, "pp_matrix_info: null context");
     if (norm1) *norm1 = c->norm1;
     if (sigma) *sigma = c->sigma;
+    return PP_OK;
+}
+
+pp_status pp_format_info(const pp_ctx *c, int *fmt, int *chunk, int *index_bits, int *threads, int64_t *stored) {
+    if (!c) return pp_fail(PP_EINVAL, "pp_format_info: null context");
+    const bool sell = c->A.fmt == 2;
+    if (fmt) *fmt = sell ? PP_FMT_SELL : PP_FMT_CSR;
+    if (chunk) *chunk = sell ? 1 << c->A.sell.cshift : 0;
+    if (index_bits) *index_bits = (sell && c->A.sell.off) ? 16 : 32;
+    if (threads) *threads = sell ? c->A.threads : 256;
+    if (stored) *stored = c->stored;
     return PP_OK;
 }
 

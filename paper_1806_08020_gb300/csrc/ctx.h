@@ -83,6 +83,7 @@ struct pp_ctx {
     double *d_small = nullptr;  // h1, h2, scal, misc (4 * 256 doubles)
     int64_t launches = 0;
     pp_ctx *twin = nullptr;  // FP64 copy of an FP32 context (mixed-precision fallback)
+    int64_t stored = 0;      // matrix entries held on the device (with SELL padding)
     int64_t ldv() const { return (n + 31) / 32 * 32; }
 };
 

@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -33,11 +35,10 @@ struct Driver {
     std::vector<void *> mine;
     // FP64 test buffers
     double *Y64 = nullptr, *AY64 = nullptr;
-    void *Ys = nullptr;  // storage-precision Ritz vectors (mixed mode)
     double *dQ = nullptr, *dq = nullptr, *dmu = nullptr;
     int *dpartner = nullptr;
     // refinement
-    double *Z = nullptr, *dG = nullptr;
+    double *Z = nullptr, *dG = nullptr, *Yb = nullptr;
     static constexpr int kZcap = 128;
 
     ~Driver() {
@@ -56,7 +57,6 @@ struct Driver {
     pp_status alloc_test_buffers(bool mixed) {
         CKS(alloc((void **)&Y64, (size_t)ldv * (wcap + 1) * 8));
         CKS(alloc((void **)&AY64, (size_t)ldv * (wcap + 1) * 8));
-        if (mixed) CKS(alloc(&Ys, (size_t)ldv * (wcap + 1) * c->esz));
         CKS(alloc((void **)&dQ, (size_t)kZcap * kZcap * 8));
         CKS(alloc((void **)&dq, (size_t)4 * (wcap + 1) * 8));
         CKS(alloc((void **)&dmu, (size_t)3 * (wcap + 1) * 8));
@@ -72,15 +72,9 @@ struct Driver {
         const int nw = sl.nw;
         CK(cudaMemcpyAsync(dQ, Sw.data(), Sw.size() * 8, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(dpartner, sl.partner.data(), nw * 4, cudaMemcpyHostToDevice, c->stream));
-        if (pb == ppk::F64) {
-            ppk::launch_rotate(ppk::F64, (int)n, B, ldv, mcols, dQ, nw, Y64, ldv, c->stream);
-            CKS(check_launch(c));
-        } else {
-            ppk::launch_rotate(ppk::F32, (int)n, B, ldv, mcols, dQ, nw, Ys, ldv, c->stream);
-            CKS(check_launch(c));
-            ppk::launch_convert(ppk::F32, ppk::F64, (int)(ldv * nw), Ys, Y64, c->stream);
-            CKS(check_launch(c));
-        }
+        // FP64 arithmetic and output whatever the basis precision
+        ppk::launch_rotate64(pb, (int)n, B, ldv, mcols, dQ, nw, Y64, ldv, c->stream);
+        CKS(check_launch(c));
         for (int s = 0; s < nw; ++s) {
             ppk::StepArgs a;
             a.x = Y64 + (size_t)s * ldv;
@@ -162,75 +156,104 @@ struct Driver {
         return PP_OK;
     }
 
-    // FP64 refinement on A (mixed precision): block Krylov span{Y, AY, ..., A^s Y}
-    // with CGS2, Rayleigh-Ritz of A, Ritz pairs matched to the current estimates.
-    pp_status refine(Slots &sl, int nev, RitzOut &R, double rtol, int steps, int rounds, pp_stats &S) {
+    // FP64 refinement on A (mixed precision): Rayleigh-Ritz of A itself on a
+    // search space built in FP64 from the wanted Ritz vectors Y.  With an FP64
+    // copy of the operator the space is span{pi(A) Y}: the polynomial keeps
+    // the wanted part of Y and damps the FP32 rounding noise in the unwanted
+    // part of the spectrum (one step of subspace iteration on pi(A)).  Without
+    // one it is the block Krylov space span{Y, A Y, ..., A^s Y}.  The Ritz
+    // pairs nearest the current estimates replace them, for up to `rounds`
+    // rounds; a round that does not lower the largest residual is undone and
+    // ends the refinement, so the estimates never get worse.  A failed dense
+    // eigensolve or too few candidates also end it.
+    pp_status refine(const pp_poly *p, Slots &sl, int nev, RitzOut &R, double rtol, int steps, int rounds,
+                     pp_stats &S) {
         if (!Z) CKS(alloc((void **)&Z, (size_t)ldv * (kZcap + 1) * 8));
         if (!dG) CKS(alloc((void **)&dG, (size_t)(kZcap + 1) * kZcap * 8));
+        if (!Yb) CKS(alloc((void **)&Yb, (size_t)ldv * (wcap + 1) * 8));
+        pp_ctx *tw = (p && c->twin) ? c->twin : nullptr;
         steps = std::max(1, std::min(steps, kZcap / (nev + 1) - 1));
         const int ldg = kZcap + 1;
         double *W = AY64 + (size_t)(nev + 1) * ldv;  // spare FP64 column (context vectors are FP32 here)
+        auto project = [&](int col, int nz) -> pp_status {  // G[:, col] = Z^T A z_col
+            ppk::StepArgs a;
+            a.x = Z + (size_t)col * ldv;
+            a.y = W;
+            a.plain = 1;
+            ppk::launch_step(c->A64, a, c->stream);
+            CKS(check_launch(c));
+            ppk::CgsArgs ca;
+            ca.mode = 0;
+            ca.n = (int)n;
+            ca.V = Z;
+            ca.ldv = ldv;
+            ca.j = nz;
+            ca.w = W;
+            ca.out = dG + (size_t)col * ldg;
+            ca.part = c->d_part;
+            ca.ticket = c->d_ticket;
+            ppk::launch_cgs(ppk::F64, ca, c->stream);
+            CKS(check_launch(c));
+            S.mvps += 1;
+            S.dots += nz;
+            S.vops += nz;
+            return PP_OK;
+        };
+        // the best state so far (the input): slots, residuals and Y
+        Slots sl_best = sl;
+        RitzOut R_best = R;
+        double best = R.res.empty() ? INFINITY : *std::max_element(R.res.begin(), R.res.end());
+        CK(cudaMemcpyAsync(Yb, Y64, (size_t)ldv * sl.nw * 8, cudaMemcpyDeviceToDevice, c->stream));
         for (int round = 0; round < rounds; ++round) {
             const int nw = sl.nw;  // the wanted slots of this round (the layout may change)
             int nz = 0;
             CK(cudaMemsetAsync(dG, 0, (size_t)ldg * kZcap * 8, c->stream));
-            for (int s = 0; s < nw; ++s) {
-                CK(cudaMemcpyAsync(W, Y64 + (size_t)s * ldv, n * 8, cudaMemcpyDeviceToDevice, c->stream));
-                CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, c->d_small + 2048));
-                nz++;
-            }
-            int b0 = 0, b1 = nz;
-            for (int st = 0; st < steps; ++st) {
-                for (int col = b0; col < b1; ++col) {
-                    ppk::StepArgs a;
-                    a.x = Z + (size_t)col * ldv;
-                    a.y = W;
-                    a.plain = 1;
-                    ppk::launch_step(c->A64, a, c->stream);
-                    CKS(check_launch(c));
-                    CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, dG + (size_t)col * ldg));
+            if (tw) {
+                for (int s = 0; s < nw; ++s) {
+                    CKS(op_apply(tw, p, Y64 + (size_t)s * ldv, W));
+                    CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, c->d_small + 2048));
                     S.dots += 2 * nz + 1;
                     S.vops += 4 * nz + 2;
                     nz++;
                 }
-                S.mvps += b1 - b0;
-                b0 = b1;
-                b1 = nz;
+                S.mvps += op_mvps(p) * nw;
+                for (int col = 0; col < nz; ++col) CKS(project(col, nz));
+            } else {
+                for (int s = 0; s < nw; ++s) {
+                    CK(cudaMemcpyAsync(W, Y64 + (size_t)s * ldv, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+                    CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, c->d_small + 2048));
+                    nz++;
+                }
+                int b0 = 0, b1 = nz;
+                for (int st = 0; st < steps; ++st) {
+                    for (int col = b0; col < b1; ++col) {
+                        ppk::StepArgs a;
+                        a.x = Z + (size_t)col * ldv;
+                        a.y = W;
+                        a.plain = 1;
+                        ppk::launch_step(c->A64, a, c->stream);
+                        CKS(check_launch(c));
+                        CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, dG + (size_t)col * ldg));
+                        S.dots += 2 * nz + 1;
+                        S.vops += 4 * nz + 2;
+                        nz++;
+                    }
+                    S.mvps += b1 - b0;
+                    b0 = b1;
+                    b1 = nz;
+                }
+                // the Arnoldi coefficients gave G's first columns; the last block's remain
+                for (int col = b0; col < b1; ++col) CKS(project(col, nz));
             }
-            // last block: G[:, col] = Z^T A z_col (no new columns)
-            for (int col = b0; col < b1; ++col) {
-                ppk::StepArgs a;
-                a.x = Z + (size_t)col * ldv;
-                a.y = W;
-                a.plain = 1;
-                ppk::launch_step(c->A64, a, c->stream);
-                CKS(check_launch(c));
-                ppk::CgsArgs ca;
-                ca.mode = 0;
-                ca.n = (int)n;
-                ca.V = Z;
-                ca.ldv = ldv;
-                ca.j = nz;
-                ca.w = W;
-                ca.out = dG + (size_t)col * ldg;
-                ca.part = c->d_part;
-                ca.ticket = c->d_ticket;
-                ppk::launch_cgs(ppk::F64, ca, c->stream);
-                CKS(check_launch(c));
-                S.dots += nz;
-                S.vops += nz;
-            }
-            S.mvps += b1 - b0;
             std::vector<double> Gfull((size_t)ldg * nz), G((size_t)nz * nz);
             CK(cudaMemcpyAsync(Gfull.data(), dG, Gfull.size() * 8, cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
             for (int j = 0; j < nz; ++j)
                 for (int i = 0; i < nz; ++i) G[i + (size_t)j * nz] = Gfull[i + (size_t)j * ldg];
             for (double v : G)
-                if (!std::isfinite(v)) return pp_fail(PP_ENUMERIC, "refinement: non-finite projection");
+                if (!std::isfinite(v)) return PP_OK;
             std::vector<double> wr(nz), wi(nz), Sv((size_t)nz * nz);
-            if (!ppd::dense_eig(nz, G.data(), nz, wr.data(), wi.data(), Sv.data(), nz))
-                return pp_fail(PP_ENUMERIC, "refinement: Rayleigh-Ritz QR failed");
+            if (!ppd::dense_eig(nz, G.data(), nz, wr.data(), wi.data(), Sv.data(), nz)) return PP_OK;
             // the refined wanted set: the Ritz values of G nearest the current
             // estimates, a conjugate pair as one unit, until nev slots are filled
             // (one more when the last unit is a pair); FP32 may have shown a pair
@@ -258,7 +281,7 @@ struct Driver {
                 pick.push_back(i);
                 ns.nw += wi[i] != 0.0 ? 2 : 1;
             }
-            if (ns.nw < nev) return pp_fail(PP_ENUMERIC, "refinement: fewer Ritz values than wanted");
+            if (ns.nw < nev) return PP_OK;
             ns.partner.assign(ns.nw, 0);
             ns.sg.assign(ns.nw, 0.0);
             std::vector<double> Sw((size_t)nz * ns.nw);
@@ -281,15 +304,42 @@ struct Driver {
             CKS(ritz_test(Z, ppk::F64, nz, Sw, sl, rtol, R, S));
             S.vops += (int64_t)nz * nw;
             if (R.all) return PP_OK;
+            const double mx = *std::max_element(R.res.begin(), R.res.end());
+            if (!(mx < best)) break;
+            best = mx;
+            sl_best = sl;
+            R_best = R;
+            CK(cudaMemcpyAsync(Yb, Y64, (size_t)ldv * sl.nw * 8, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        // undo the last round if it did not improve
+        const double mx = R.res.empty() ? INFINITY : *std::max_element(R.res.begin(), R.res.end());
+        if (!(mx <= best)) {
+            sl = sl_best;
+            R = R_best;
+            CK(cudaMemcpyAsync(Y64, Yb, (size_t)ldv * sl.nw * 8, cudaMemcpyDeviceToDevice, c->stream));
         }
         return PP_OK;
     }
 };
 
 
+// Per-cycle trace on stderr when the environment sets PP_TRACE (diagnostics
+// only: the arithmetic is the same either way).
+inline bool trace_on() {
+    static const bool on = std::getenv("PP_TRACE") != nullptr;
+    return on;
+}
+inline void trace_cycle(const char *who, const void *id, int64_t cycle, int prec_bits, const RitzOut &R,
+                        const char *event) {
+    if (!trace_on()) return;
+    double mx = R.res.empty() ? 0.0 : *std::max_element(R.res.begin(), R.res.end());
+    std::fprintf(stderr, "[pp] %s %p cycle %lld fp%d max_resid %.3e nconv %d %s\n", who, id, (long long)cycle,
+                 prec_bits, mx, R.nconv, event ? event : "");
+}
+
 // When the FP32 cycles of the mixed mode hand over to the FP64 refinement:
 // within 10 rtol; at the FP32 floor (below 1e-6 and no longer halving per
-// cycle); after four cycles without halving at any level (an operator too
+// cycle); after three cycles without halving at any level (an operator too
 // non-normal for FP32, or an FP32 apply swamped by the growth of the partial
 // products of a high-degree polynomial); or at the last cycle.
 struct MixedSwitch {
@@ -302,7 +352,7 @@ struct MixedSwitch {
         best = std::min(best, mx);
         if (last_cycle || mx <= 10 * rtol) return true;
         if (mx <= std::max(rtol, 1e-6) && stall >= 1) return true;
-        return stall >= 4;
+        return stall >= 3;
     }
     // after a refinement that missed rtol, keep cycling in FP32 from here
     void reset() {

@@ -33,7 +33,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
     const bool mixed = c->A.prec != ppk::F64;
     const double target = p ? 1.0 : 0.0;
     pp_stats S{};
-    int64_t launches0 = c->launches;
+    const int64_t launches0 = c->launches, twin0 = c->twin ? c->twin->launches : 0;
     Driver D{c, n, ldv, nev + 1};
     void *V = nullptr, *V2 = nullptr, *W = (p && p->inner) ? c->vec[0] : c->vec[6];
     double *dH = nullptr;
@@ -78,14 +78,16 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
         CKS(wanted_set(H, ldh, m, nev, target, cy));
         CKS(D.ritz_test(V, c->A.prec, m, cy.Sw, cy.sl, rtol, R, S));
         S.nconv = R.nconv;
+        trace_cycle("eigs", c, cycle, mixed ? 32 : 64, R, R.all ? "converged" : nullptr);
         if (R.all) {
             converged = true;
             S.t_restart += now() - th0;
             break;
         }
         if (mixed && sw.should_refine(R, cycle == c->opts.max_cycles)) {
-            CKS(D.refine(cy.sl, nev, R, rtol, c->opts.refine_steps, 3, S));
+            CKS(D.refine(p, cy.sl, nev, R, rtol, c->opts.refine_steps, 3, S));
             S.nconv = R.nconv;
+            trace_cycle("eigs", c, cycle, 64, R, R.all ? "refined: converged" : "refined");
             converged = R.all;
             if (converged || cycle == c->opts.max_cycles) {
                 S.t_restart += now() - th0;
@@ -103,7 +105,6 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
                 const int max_c = tw->opts.max_cycles;
                 tw->opts.max_cycles = (int)std::max<int64_t>(1, c->opts.max_cycles - cycle);
                 pp_stats S2{};
-                int64_t l0 = tw->launches;
                 pp_status st2 = pp_eigs(tw, p, nev, m, k, rtol, w0.data(), lam_re, lam_im, X, resid, nout, &S2);
                 tw->opts.max_cycles = max_c;
                 if (st2 < 0) return st2;
@@ -115,7 +116,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
                 S2.t_apply += S.t_apply;
                 S2.t_orth += S.t_orth;
                 S2.t_restart += S.t_restart + (now() - th0);
-                S2.kernel_launches = (c->launches - launches0) + (tw->launches - l0);
+                S2.kernel_launches = (c->launches - launches0) + (tw->launches - twin0);
                 S2.t_total = now() - t_start;
                 if (stats) *stats = S2;
                 return st2;
@@ -147,7 +148,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
     S.converged = converged ? 1 : 0;
     S.max_resid = maxres;
     S.fp64_cycles = mixed ? 0 : S.cycles;
-    S.kernel_launches = c->launches - launches0;
+    S.kernel_launches = (c->launches - launches0) + (c->twin ? c->twin->launches - twin0 : 0);
     S.t_total = now() - t_start;
     if (stats) *stats = S;
     if (!converged) return pp_fail(PP_ENOTCONV, "pp_eigs: not converged in %lld cycles", (long long)S.cycles);

@@ -1,10 +1,11 @@
 // CUDA kernels of the hot path (sm_103a).
 //
-//  * k_sell_step / k_csr_step: one fused pass of the factored GMRES polynomial
-//    (Eq. (2.1)): SpMV with A - sigma I plus the root-step axpy and the running
-//    sum (Section 2 footnote 2) in the same pass; conjugate pairs use two passes
-//    in real arithmetic; the double polynomial's outer step (Section 8) is
-//    fused into the last inner pass.
+//  * k_pass / k_step: one fused pass of the factored GMRES polynomial
+//    (Eq. (2.1)) on SELL-C (16- or 32-bit column indices) or CSR: SpMV with
+//    A - sigma I plus the root-step axpy and the running sum (Section 2
+//    footnote 2) in the same pass; conjugate pairs use two passes in real
+//    arithmetic; the double polynomial's outer step (Section 8) is fused into
+//    the last inner pass.
 //  * k_cgs: the three passes of classical Gram-Schmidt with one
 //    reorthogonalisation (Section 4), each a single sweep over the basis with
 //    a deterministic two-level reduction finished by the last block.
@@ -55,21 +56,50 @@ __device__ __forceinline__ void step_epilogue(int row, Acc u, const StepArgs &s)
     }
 }
 
-// Row sum u = sum_k A(row, col_k) x(col_k) over a SELL-32 slice row (the
-// slice width is warp-uniform).  Kept to ~30 registers so that 8 blocks of
-// 256 threads stay resident per SM: the gathers are latency-bound and need the
-// warps more than a wider unroll.
-template <typename T, typename V, typename Acc>
+// Row sum u = sum_k A(row, col_k) x(col_k) over a SELL-C slice row (the
+// slice width is uniform across the slice).  Kept to ~30 registers so that
+// 2048 threads stay resident per SM: the gathers are latency-bound and need
+// the warps more than a wider unroll.  The sum runs over the row's entries in
+// CSR order whatever C, the index width or the block size (padding adds
+// 0 * x exactly), so every format gives bit-identical results.
+template <typename T, typename V, typename Acc, bool OFF16>
 __device__ __forceinline__ Acc sell_row(const SellView &A, const T *__restrict__ x, int row) {
-    const int sl = row >> 5, lane = row & 31;
+    const int cs = A.cshift;
+    const int sl = row >> cs, lane = row & ((1 << cs) - 1);
     const int beg = __ldg(A.slice_ptr + sl);
-    const int len = (__ldg(A.slice_ptr + sl + 1) - beg) >> 5;
-    const int *col = A.col + beg + lane;
+    const int len = (__ldg(A.slice_ptr + sl + 1) - beg) >> cs;
     const V *val = (const V *)A.val + beg + lane;
     Acc acc = 0;
+    if (OFF16) {
+        const short *off = A.off + beg + lane;
+        const T *xr = x + row;
 #pragma unroll 4
-    for (int k = 0; k < len; ++k) acc = fma((Acc)__ldg(val + 32 * k), (Acc)__ldg(x + __ldg(col + 32 * k)), acc);
+        for (int k = 0; k < len; ++k)
+            acc = fma((Acc)__ldg(val + (k << cs)), (Acc)__ldg(xr + __ldg(off + (k << cs))), acc);
+    } else {
+        const int *col = A.col + beg + lane;
+#pragma unroll 4
+        for (int k = 0; k < len; ++k)
+            acc = fma((Acc)__ldg(val + (k << cs)), (Acc)__ldg(x + __ldg(col + (k << cs))), acc);
+    }
     return acc;
+}
+
+constexpr int kPassMaxThreads = 512;
+
+// Row sum of the matrix in format FMT: 0 CSR, 1 SELL with 32-bit columns,
+// 2 SELL with 16-bit offsets.  All three sum a row's entries in CSR order.
+template <typename T, typename V, typename Acc, int FMT>
+__device__ __forceinline__ Acc row_sum(const SellView &S, const CsrView &R, const T *__restrict__ x, int row) {
+    if constexpr (FMT == 0) {
+        const int beg = __ldg(R.rowptr + row), end = __ldg(R.rowptr + row + 1);
+        const V *val = (const V *)R.val;
+        Acc acc = 0;
+        for (int k = beg; k < end; ++k) acc = fma((Acc)__ldg(val + k), (Acc)__ldg(x + __ldg(R.col + k)), acc);
+        return acc;
+    } else {
+        return sell_row<T, V, Acc, FMT == 2>(S, x, row);
+    }
 }
 
 // Specialised passes of the factored polynomial (the hot cases):
@@ -77,12 +107,12 @@ __device__ __forceinline__ Acc sell_row(const SellView &A, const T *__restrict__
 //   KIND 1 real:   y = x - a2 u                (a2 = 1/theta)
 //   KIND 2 pair 2: y = aux - a1 x - a2 u        (x = t, aux = p, a1 = c1, a2 = -c2)
 // with u = A x - sigma x when SIGMA.
-template <typename T, typename V, typename Acc, int KIND, bool SIGMA>
-__global__ void __launch_bounds__(kThreads) k_sell_pass(SellView A, StepArgs s) {
-    const int row = blockIdx.x * kThreads + threadIdx.x;
-    if (row >= A.n) return;
+template <typename T, typename V, typename Acc, int KIND, bool SIGMA, int FMT>
+__global__ void __launch_bounds__(kPassMaxThreads) k_pass(SellView S, CsrView R, StepArgs s) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (FMT == 0 ? R.n : S.n)) return;
     const T *x = (const T *)s.x;
-    Acc u = sell_row<T, V, Acc>(A, x, row);
+    Acc u = row_sum<T, V, Acc, FMT>(S, R, x, row);
     if (SIGMA) u = fma(-(Acc)s.sigma, (Acc)x[row], u);
     T *y = (T *)s.y;
     if (KIND == 0) {
@@ -96,23 +126,11 @@ __global__ void __launch_bounds__(kThreads) k_sell_pass(SellView A, StepArgs s) 
 }
 
 // General pass (running sum, optional output, outer epilogue): see StepArgs.
-template <typename T, typename V, typename Acc>
-__global__ void __launch_bounds__(kThreads) k_sell_step(SellView A, StepArgs s) {
-    int row = blockIdx.x * kThreads + threadIdx.x;
-    if (row >= A.n) return;
-    Acc acc = sell_row<T, V, Acc>(A, (const T *)s.x, row);
-    step_epilogue<T, Acc>(row, acc, s);
-}
-
-template <typename T, typename V, typename Acc>
-__global__ void __launch_bounds__(kThreads) k_csr_step(CsrView A, StepArgs s) {
-    int row = blockIdx.x * kThreads + threadIdx.x;
-    if (row >= A.n) return;
-    int beg = __ldg(A.rowptr + row), end = __ldg(A.rowptr + row + 1);
-    const V *val = (const V *)A.val;
-    const T *x = (const T *)s.x;
-    Acc acc = 0;
-    for (int k = beg; k < end; ++k) acc = fma((Acc)__ldg(val + k), (Acc)__ldg(x + __ldg(A.col + k)), acc);
+template <typename T, typename V, typename Acc, int FMT>
+__global__ void __launch_bounds__(kPassMaxThreads) k_step(SellView S, CsrView R, StepArgs s) {
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (FMT == 0 ? R.n : S.n)) return;
+    Acc acc = row_sum<T, V, Acc, FMT>(S, R, (const T *)s.x, row);
     step_epilogue<T, Acc>(row, acc, s);
 }
 
@@ -149,89 +167,15 @@ __device__ void reduce_partials(const double *part, int nblocks, int nout, doubl
 constexpr int kRows = 64;
 constexpr int kQ = kRows / 32;
 
-// The sweep of block `bid` out of `nblk` blocks working on one basis.
-template <typename T, int CPW>
-__device__ __forceinline__ void cgs_body(const CgsArgs &a, int bid, int nblk) {
+// Per-block partial sums of a sweep, then the last block's reduction and (mode
+// 2) the Hessenberg column.  acc[cc] is the block-local projection on column
+// warp + kWarps cc; nrm the squared norm of the updated vector's rows.
+template <int CPW>
+__device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, const double (&acc)[CPW],
+                                           double nrm) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
-    const T *V = (const T *)a.V;
-    const T *w = (const T *)a.w;
-    T *wout = (T *)a.wout;
-    const int j = a.j, n = a.n;
-    __shared__ double red[kWarps][kRows];
-    __shared__ double wsh[kRows];
-    __shared__ double hs[8 * CPW];
+    const int j = a.j;
     __shared__ double nrm_sh[kWarps];
-    if (a.mode != 0)
-        for (int c = tid; c < j; c += kThreads) hs[c] = a.h[c];
-    __syncthreads();
-    double acc[CPW];
-#pragma unroll
-    for (int cc = 0; cc < CPW; ++cc) acc[cc] = 0;
-    double nrm = 0;
-    const int ntiles = (n + kRows - 1) / kRows;
-    for (int tile = bid; tile < ntiles; tile += nblk) {
-        const int r0 = tile * kRows;
-        double vv[CPW][kQ];
-#pragma unroll
-        for (int cc = 0; cc < CPW; ++cc) {
-            int c = warp + kWarps * cc;
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) {
-                int row = r0 + lane + 32 * q;
-                vv[cc][q] = (c < j && row < n) ? ld_acc(V, (size_t)c * a.ldv + row) : 0.0;
-            }
-        }
-        if (a.mode == 0) {
-            double wv[kQ];
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) {
-                int row = r0 + lane + 32 * q;
-                wv[q] = row < n ? ld_acc(w, row) : 0.0;
-            }
-#pragma unroll
-            for (int cc = 0; cc < CPW; ++cc)
-                if (warp + kWarps * cc < j)  // warp-uniform: no FMAs on columns past j
-#pragma unroll
-                    for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wv[q], acc[cc]);
-            continue;
-        }
-        // w - V h for the tile rows: per-warp partial sums, then across warps
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            double s = 0;
-#pragma unroll
-            for (int cc = 0; cc < CPW; ++cc) {
-                int c = warp + kWarps * cc;
-                if (c < j) s = fma(vv[cc][q], hs[c], s);
-            }
-            red[warp][lane + 32 * q] = s;
-        }
-        __syncthreads();
-        if (tid < kRows) {
-            int row = r0 + tid;
-            double v = 0;
-            if (row < n) {
-                double s = 0;
-#pragma unroll
-                for (int ww = 0; ww < kWarps; ++ww) s += red[ww][tid];
-                v = ld_acc(w, row) - s;
-                T vt = (T)v;
-                wout[row] = vt;
-                v = (double)vt;
-                nrm = fma(v, v, nrm);
-            }
-            wsh[tid] = v;
-        }
-        __syncthreads();
-        if (a.mode == 1) {
-#pragma unroll
-            for (int cc = 0; cc < CPW; ++cc)
-                if (warp + kWarps * cc < j)
-#pragma unroll
-                    for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wsh[lane + 32 * q], acc[cc]);
-        }
-    }
-    // per-block partials
     const int nout = (a.mode == 0) ? j : (a.mode == 1 ? j + 1 : 1);
     double *part = a.part + (size_t)bid * nout;
     if (a.mode != 2) {
@@ -269,6 +213,201 @@ __device__ __forceinline__ void cgs_body(const CgsArgs &a, int bid, int nblk) {
             a.scal[0] = nn > 0 ? 1.0 / nn : 0.0;
         }
     }
+}
+
+// The sweep of block `bid` out of `nblk` blocks working on an FP64 basis:
+// FP64 throughout.
+template <int CPW>
+__device__ __forceinline__ void cgs_body_f64(const CgsArgs &a, int bid, int nblk) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const double *V = (const double *)a.V;
+    const double *w = (const double *)a.w;
+    double *wout = (double *)a.wout;
+    const int j = a.j, n = a.n;
+    __shared__ double red[kWarps][kRows];
+    __shared__ double wsh[kRows];
+    __shared__ double hs[8 * CPW];
+    if (a.mode != 0)
+        for (int c = tid; c < j; c += kThreads) hs[c] = a.h[c];
+    __syncthreads();
+    double acc[CPW];
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) acc[cc] = 0;
+    double nrm = 0;
+    const int ntiles = (n + kRows - 1) / kRows;
+    for (int tile = bid; tile < ntiles; tile += nblk) {
+        const int r0 = tile * kRows;
+        double vv[CPW][kQ];
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+            int c = warp + kWarps * cc;
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                int row = r0 + lane + 32 * q;
+                vv[cc][q] = (c < j && row < n) ? __ldg(V + (size_t)c * a.ldv + row) : 0.0;
+            }
+        }
+        if (a.mode == 0) {
+            double wv[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                int row = r0 + lane + 32 * q;
+                wv[q] = row < n ? __ldg(w + row) : 0.0;
+            }
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc)
+                if (warp + kWarps * cc < j)  // warp-uniform: no FMAs on columns past j
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wv[q], acc[cc]);
+            continue;
+        }
+        // w - V h for the tile rows: per-warp partial sums, then across warps
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            double s = 0;
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) {
+                int c = warp + kWarps * cc;
+                if (c < j) s = fma(vv[cc][q], hs[c], s);
+            }
+            red[warp][lane + 32 * q] = s;
+        }
+        __syncthreads();
+        if (tid < kRows) {
+            int row = r0 + tid;
+            double v = 0;
+            if (row < n) {
+                double s = 0;
+#pragma unroll
+                for (int ww = 0; ww < kWarps; ++ww) s += red[ww][tid];
+                v = __ldg(w + row) - s;
+                wout[row] = v;
+                nrm = fma(v, v, nrm);
+            }
+            wsh[tid] = v;
+        }
+        __syncthreads();
+        if (a.mode == 1) {
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc)
+                if (warp + kWarps * cc < j)
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wsh[lane + 32 * q], acc[cc]);
+        }
+    }
+    cgs_finish<CPW>(a, bid, nblk, acc, nrm);
+}
+
+// One term of the compensated dot product Dot2 (Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005)): the
+// product's rounding error from an FMA (TwoProduct), the sum's from Knuth's
+// TwoSum; the errors accumulate in c, so s + c is the dot product as if
+// computed in twice the working precision.  The _rn intrinsics keep the
+// compiler from contracting or reassociating the error-free steps.
+__device__ __forceinline__ void dot2_term(float x, float y, float &s, float &c) {
+    float p = __fmul_rn(x, y);
+    float e = fmaf(x, y, -p);
+    float t = __fadd_rn(s, p);
+    float z = __fsub_rn(t, s);
+    float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
+// The sweep over an FP32 basis.  The first projection h1 = V^T w and both
+// updates w - V h run in FP32 (FP32 FMAs are many times faster than FP64 ones
+// on this part); the reorthogonalising projection h2 = V^T w1 uses Dot2, so
+// the second Gram-Schmidt pass is accurate to about twice FP32 precision.
+// Squared norms accumulate in FP64.
+template <int CPW>
+__device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const float *V = (const float *)a.V;
+    const float *w = (const float *)a.w;
+    float *wout = (float *)a.wout;
+    const int j = a.j, n = a.n;
+    __shared__ float red[kWarps][kRows];
+    __shared__ float wsh[kRows];
+    __shared__ float hs[8 * CPW];
+    if (a.mode != 0)
+        for (int c = tid; c < j; c += kThreads) hs[c] = (float)a.h[c];
+    __syncthreads();
+    float hi[CPW], lo[CPW];
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) hi[cc] = lo[cc] = 0.f;
+    double nrm = 0;
+    const int ntiles = (n + kRows - 1) / kRows;
+    for (int tile = bid; tile < ntiles; tile += nblk) {
+        const int r0 = tile * kRows;
+        float vv[CPW][kQ];
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+            int c = warp + kWarps * cc;
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                int row = r0 + lane + 32 * q;
+                vv[cc][q] = (c < j && row < n) ? __ldg(V + (size_t)c * a.ldv + row) : 0.f;
+            }
+        }
+        if (a.mode == 0) {
+            float wv[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                int row = r0 + lane + 32 * q;
+                wv[q] = row < n ? __ldg(w + row) : 0.f;
+            }
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc)
+                if (warp + kWarps * cc < j)
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) hi[cc] = fmaf(vv[cc][q], wv[q], hi[cc]);
+            continue;
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            float s = 0;
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) {
+                int c = warp + kWarps * cc;
+                if (c < j) s = fmaf(vv[cc][q], hs[c], s);
+            }
+            red[warp][lane + 32 * q] = s;
+        }
+        __syncthreads();
+        if (tid < kRows) {
+            int row = r0 + tid;
+            float v = 0;
+            if (row < n) {
+                float s = 0;
+#pragma unroll
+                for (int ww = 0; ww < kWarps; ++ww) s += red[ww][tid];
+                v = __ldg(w + row) - s;
+                wout[row] = v;
+                nrm = fma((double)v, (double)v, nrm);
+            }
+            wsh[tid] = v;
+        }
+        __syncthreads();
+        if (a.mode == 1) {
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc)
+                if (warp + kWarps * cc < j)
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) dot2_term(vv[cc][q], wsh[lane + 32 * q], hi[cc], lo[cc]);
+        }
+    }
+    double acc[CPW];
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) acc[cc] = (double)hi[cc] + (double)lo[cc];
+    cgs_finish<CPW>(a, bid, nblk, acc, nrm);
+}
+
+template <typename T, int CPW>
+__device__ __forceinline__ void cgs_body(const CgsArgs &a, int bid, int nblk) {
+    if constexpr (sizeof(T) == 8)
+        cgs_body_f64<CPW>(a, bid, nblk);
+    else
+        cgs_body_f32<CPW>(a, bid, nblk);
 }
 
 template <typename T, int CPW>
@@ -337,28 +476,26 @@ __global__ void k_scale_batch(const BatchCgsInst *ci, int count, const int *lo, 
         x[r] = (T)((double)x[r] * s);
 }
 
-// One polynomial pass for every active instance: warp = one SELL slice of one
-// instance; blocks stride over (instance, 8-slice) work items.
+// One polynomial pass for every active instance: warp = 32 consecutive rows
+// of one instance; a block takes blockDim/32 such groups of one instance
+// (a work item) and blocks stride over the work items.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pass_batch(const BatchPassInst *pi, const BatchPassEntry *tab,
-                                                         const int2 *items, int nitems, const int *lo,
-                                                         const int *hi, int jj) {
+__global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassInst *pi, const BatchPassEntry *tab,
+                                                                const int2 *items, int nitems, const int *lo,
+                                                                const int *hi, int jj) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 itm = items[it];
         const BatchPassEntry e = tab[itm.x];
         if (e.kind < 0 || jj < lo[itm.x] || jj >= hi[itm.x]) continue;
         const BatchPassInst &I = pi[itm.x];
-        const int slice = itm.y + warp;
-        if (slice >= I.nslices) continue;
-        const int row = slice * 32 + lane;
-        if (row >= I.n) continue;
+        const int row = (itm.y + warp) * 32 + lane;
+        if (row >= I.A.n) continue;
         const T *bufs[5] = {(const T *)I.V + (size_t)jj * I.ldv, (const T *)I.W, (const T *)I.P0, (const T *)I.P1,
                             (const T *)I.T};
         const T *x = bufs[e.src];
         T *y = (T *)bufs[e.dst];
-        SellView A{I.n, I.nslices, I.slice_ptr, I.col, I.val};
-        T u = sell_row<T, T, T>(A, x, row);
+        T u = I.A.off ? sell_row<T, T, T, true>(I.A, x, row) : sell_row<T, T, T, false>(I.A, x, row);
         if (I.sigma != 0.0) u = fma(-(T)I.sigma, x[row], u);
         if (e.kind == 0)
             y[row] = u;
@@ -378,27 +515,29 @@ __global__ void k_scale(int n, T *x, const double *scal) {
 
 // ---------------------------------------------------------------------------
 // Out = V[:, 0:m] Q  (tile of 32 rows per block iteration; Q and the V tile in
-// shared memory; warp w computes output columns w, w+8, ...)
+// shared memory; warp w computes output columns w, w+8, ...).  Acc is the
+// arithmetic: FP64 for FP64 bases; FP32 for FP32 bases, whose columns are
+// rounded to FP32 on store anyway (an FP64 FMA costs many FP32 ones here).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename TO, typename Acc>
 __global__ void __launch_bounds__(kThreads) k_rotate(int n, const T *V, int64_t ldv, int m, const double *Q,
-                                                     int kk, T *out, int64_t ldo) {
-    extern __shared__ double sm[];
-    double *Qs = sm;               // m * kk
-    double *Vs = sm + (size_t)m * kk;  // m * 32
+                                                     int kk, TO *out, int64_t ldo) {
+    extern __shared__ double sm_raw[];
+    Acc *Qs = (Acc *)sm_raw;          // m * kk
+    Acc *Vs = Qs + (size_t)m * kk;    // m * 32
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < m * kk; i += kThreads) Qs[i] = Q[i];
+    for (int i = threadIdx.x; i < m * kk; i += kThreads) Qs[i] = (Acc)Q[i];
     const int ntiles = (n + 31) / 32;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int row = tile * 32 + lane;
         __syncthreads();
-        for (int r = warp; r < m; r += kWarps) Vs[r * 32 + lane] = row < n ? ld_acc(V, (size_t)r * ldv + row) : 0.0;
+        for (int r = warp; r < m; r += kWarps) Vs[r * 32 + lane] = row < n ? (Acc)__ldg(V + (size_t)r * ldv + row) : (Acc)0;
         __syncthreads();
         for (int c = warp; c < kk; c += kWarps) {
-            double acc = 0;
-            const double *qc = Qs + (size_t)c * m;
+            Acc acc = 0;
+            const Acc *qc = Qs + (size_t)c * m;
             for (int r = 0; r < m; ++r) acc = fma(Vs[r * 32 + lane], qc[r], acc);
-            if (row < n) out[(size_t)c * ldo + row] = (T)acc;
+            if (row < n) out[(size_t)c * ldo + row] = (TO)acc;
         }
     }
 }
@@ -474,33 +613,22 @@ __global__ void __launch_bounds__(kThreads) k_coldots(ColDotArgs a) {
 // ---------------------------------------------------------------------------
 // SELL-32 construction
 // ---------------------------------------------------------------------------
-__global__ void k_sell_slice_len(int n, const int *rowptr, int *slice_len) {
-    int row = blockIdx.x * kThreads + threadIdx.x;
-    int len = row < n ? rowptr[row + 1] - rowptr[row] : 0;
-#pragma unroll
-    for (int off = 16; off; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
-    if ((threadIdx.x & 31) == 0 && row - (int)(threadIdx.x & 31) < n) slice_len[row >> 5] = len;
-}
-
 template <typename V>
-__global__ void k_sell_fill(int n, const int *rowptr, const int *col, const double *val, const int *slice_ptr,
-                            int *scol, V *sval) {
-    int row = blockIdx.x * kThreads + threadIdx.x;
-    int sl = row >> 5, lane = row & 31;
-    if ((row & ~31) >= n) return;
-    int beg = slice_ptr[sl], width = (slice_ptr[sl + 1] - beg) >> 5;
+__global__ void k_sell_fill(int n, int nslices, int cshift, const int *rowptr, const int *col, const double *val,
+                            const int *slice_ptr, int *scol, short *soff, V *sval) {
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (nslices << cshift)) return;
+    int sl = row >> cshift, lane = row & ((1 << cshift) - 1);
+    int beg = slice_ptr[sl], width = (slice_ptr[sl + 1] - beg) >> cshift;
     int rb = row < n ? rowptr[row] : 0, re = row < n ? rowptr[row + 1] : 0;
     int last = row < n ? (re > rb ? col[re - 1] : row) : 0;
     for (int k = 0; k < width; ++k) {
         int src = rb + k;
-        size_t dst = (size_t)beg + 32 * k + lane;
-        if (src < re) {
-            scol[dst] = col[src];
-            sval[dst] = (V)val[src];
-        } else {
-            scol[dst] = last;  // padding: repeat a valid column, value 0
-            sval[dst] = (V)0;
-        }
+        size_t dst = (size_t)beg + ((size_t)k << cshift) + lane;
+        int cc = src < re ? col[src] : last;  // padding: repeat a valid column, value 0
+        if (scol) scol[dst] = cc;
+        if (soff) soff[dst] = row < n ? (short)(cc - row) : (short)0;  // rows past n are never read
+        sval[dst] = src < re ? (V)val[src] : (V)0;
     }
 }
 
@@ -531,21 +659,18 @@ int num_sms() {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <typename T>
-static void sell_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
-    int blocks = (A.n + kThreads - 1) / kThreads;
+template <typename T, int FMT>
+static void pass_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    const int threads = A.threads;
+    const int blocks = (A.n + threads - 1) / threads;
     const bool general = s.r || s.oy || !s.y;
     const bool sig = s.sigma != 0.0;
-    if (general) {
-        k_sell_step<T, T, T><<<blocks, kThreads, 0, st>>>(A.sell, s);
+    if (general || (!s.plain && !s.aux && s.a1 != 0.0)) {  // not one of the specialised forms
+        k_step<T, T, T, FMT><<<blocks, threads, 0, st>>>(A.sell, A.csr, s);
         return;
     }
     int kind = s.plain ? 0 : (s.aux ? 2 : 1);
-    if (!s.plain && !s.aux && s.a1 != 0.0) {  // not one of the specialised forms
-        k_sell_step<T, T, T><<<blocks, kThreads, 0, st>>>(A.sell, s);
-        return;
-    }
-#define PP_PASS(K, S) k_sell_pass<T, T, T, K, S><<<blocks, kThreads, 0, st>>>(A.sell, s)
+#define PP_PASS(K, S) k_pass<T, T, T, K, S, FMT><<<blocks, threads, 0, st>>>(A.sell, A.csr, s)
     if (kind == 0) {
         if (sig) PP_PASS(0, true); else PP_PASS(0, false);
     } else if (kind == 1) {
@@ -556,19 +681,21 @@ static void sell_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
 #undef PP_PASS
 }
 
+template <typename T>
+static void pass_format(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    if (A.fmt != 2)
+        pass_dispatch<T, 0>(A, s, st);
+    else if (A.sell.off)
+        pass_dispatch<T, 2>(A, s, st);
+    else
+        pass_dispatch<T, 1>(A, s, st);
+}
+
 void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st) {
-    int blocks = (A.n + kThreads - 1) / kThreads;
-    if (A.fmt == 2) {
-        if (A.prec == F64)
-            sell_dispatch<double>(A, s, st);
-        else
-            sell_dispatch<float>(A, s, st);
-    } else {
-        if (A.prec == F64)
-            k_csr_step<double, double, double><<<blocks, kThreads, 0, st>>>(A.csr, s);
-        else
-            k_csr_step<float, float, float><<<blocks, kThreads, 0, st>>>(A.csr, s);
-    }
+    if (A.prec == F64)
+        pass_format<double>(A, s, st);
+    else
+        pass_format<float>(A, s, st);
 }
 
 int cgs_grid(int n) {
@@ -634,14 +761,15 @@ void launch_scale_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, 
 }
 
 void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *tab, const int2 *items, int nitems,
-                       const int *lo, const int *hi, int jj, cudaStream_t st) {
-    int g = num_sms() * 8;
+                       const int *lo, const int *hi, int jj, int groups, int grid_per_sm, cudaStream_t st) {
+    int g = num_sms() * grid_per_sm;
     if (nitems < g) g = nitems;
     if (g < 1) g = 1;
+    const int threads = 32 * groups;
     if (p == F64)
-        k_pass_batch<double><<<g, kThreads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
+        k_pass_batch<double><<<g, threads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
     else
-        k_pass_batch<float><<<g, kThreads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
+        k_pass_batch<float><<<g, threads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
 }
 
 int cgs_batch_blocks(int n) {
@@ -668,16 +796,33 @@ void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st) {
 
 void launch_rotate(Prec p, int n, const void *V, int64_t ldv, int m, const double *Q, int kk, void *out,
                    int64_t ldo, cudaStream_t st) {
+    const size_t acc_bytes = p == F64 ? sizeof(double) : sizeof(float);
+    size_t smem = ((size_t)m * kk + (size_t)m * 32) * acc_bytes;
+    int tiles = (n + 31) / 32;
+    int g = num_sms() * 2;
+    if (tiles < g) g = tiles;
+    if (p == F64) {
+        cudaFuncSetAttribute(k_rotate<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rotate<double, double, double><<<g, kThreads, smem, st>>>(n, (const double *)V, ldv, m, Q, kk,
+                                                                    (double *)out, ldo);
+    } else {
+        cudaFuncSetAttribute(k_rotate<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rotate<float, float, float><<<g, kThreads, smem, st>>>(n, (const float *)V, ldv, m, Q, kk, (float *)out,
+                                                                 ldo);
+    }
+}
+
+void launch_rotate64(Prec p, int n, const void *V, int64_t ldv, int m, const double *Q, int kk, double *out,
+                     int64_t ldo, cudaStream_t st) {
     size_t smem = ((size_t)m * kk + (size_t)m * 32) * sizeof(double);
     int tiles = (n + 31) / 32;
     int g = num_sms() * 2;
     if (tiles < g) g = tiles;
     if (p == F64) {
-        cudaFuncSetAttribute(k_rotate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rotate<double><<<g, kThreads, smem, st>>>(n, (const double *)V, ldv, m, Q, kk, (double *)out, ldo);
+        launch_rotate(p, n, V, ldv, m, Q, kk, out, ldo, st);
     } else {
-        cudaFuncSetAttribute(k_rotate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_rotate<float><<<g, kThreads, smem, st>>>(n, (const float *)V, ldv, m, Q, kk, (float *)out, ldo);
+        cudaFuncSetAttribute(k_rotate<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rotate<float, double, double><<<g, kThreads, smem, st>>>(n, (const float *)V, ldv, m, Q, kk, out, ldo);
     }
 }
 
@@ -693,18 +838,16 @@ void launch_coldots(Prec p, const ColDotArgs &a, cudaStream_t st) {
         k_coldots<float><<<grid, kThreads, 0, st>>>(a);
 }
 
-void launch_sell_slice_len(int n, const int *rowptr, int *slice_len, cudaStream_t st) {
-    int blocks = (n + kThreads - 1) / kThreads;
-    k_sell_slice_len<<<blocks, kThreads, 0, st>>>(n, rowptr, slice_len);
-}
-
-void launch_sell_fill(Prec p, int n, const int *rowptr, const int *col, const double *val, const int *slice_ptr,
-                      int *scol, void *sval, cudaStream_t st) {
-    int blocks = (n + kThreads - 1) / kThreads;
+void launch_sell_fill(Prec p, int n, int nslices, int cshift, const int *rowptr, const int *col, const double *val,
+                      const int *slice_ptr, int *scol, short *soff, void *sval, cudaStream_t st) {
+    const int rows = nslices << cshift;
+    const int blocks = (rows + kThreads - 1) / kThreads;
     if (p == F64)
-        k_sell_fill<double><<<blocks, kThreads, 0, st>>>(n, rowptr, col, val, slice_ptr, scol, (double *)sval);
+        k_sell_fill<double><<<blocks, kThreads, 0, st>>>(n, nslices, cshift, rowptr, col, val, slice_ptr, scol, soff,
+                                                         (double *)sval);
     else
-        k_sell_fill<float><<<blocks, kThreads, 0, st>>>(n, rowptr, col, val, slice_ptr, scol, (float *)sval);
+        k_sell_fill<float><<<blocks, kThreads, 0, st>>>(n, nslices, cshift, rowptr, col, val, slice_ptr, scol, soff,
+                                                        (float *)sval);
 }
 
 void launch_csr_convert(Prec p, int64_t nnz, const double *val, void *out, cudaStream_t st) {

@@ -34,15 +34,19 @@ namespace ppk {
 // Storage precisions of device vectors / matrix values.
 enum Prec { F64 = 0, F32 = 1 };
 
-// SELL-C-sigma matrix with C = 32: slice s holds rows [32 s, 32 s + 32);
-// entries of slice s occupy [slice_ptr[s], slice_ptr[s+1]) laid out column
-// major within the slice (entry k of lane l at slice_ptr[s] + 32 k + l).
-// perm (optional) maps sorted row r -> original row perm[r].
+// SELL-C matrix (sigma = 1: rows keep their order) with chunk height
+// C = 1 << cshift (16 or 32): slice s holds rows [C s, C s + C); its entries
+// occupy [slice_ptr[s], slice_ptr[s+1]) column major within the slice (entry
+// k of lane l at slice_ptr[s] + C k + l).  Column indices are 32-bit (col),
+// or 16-bit offsets col - row (off) when every |col - row| < 2^15; padding
+// repeats the row's last column (its own row when empty) with value 0.
 struct SellView {
     int n;
     int nslices;
+    int cshift;
     const int *slice_ptr;
     const int *col;
+    const short *off;
     const void *val;
 };
 
@@ -77,6 +81,7 @@ struct StepArgs {
 struct Matrix {
     int n = 0;
     int fmt = 2;  // 1 CSR, 2 SELL
+    int threads = 256;  // block size of the SELL pass kernels (64..512, chosen by the tuner)
     Prec prec = F64;
     SellView sell{};
     CsrView csr{};
@@ -127,13 +132,11 @@ struct BatchCgsInst {
     unsigned *ticket;
     int nblk, blk0;
 };
-// Per-instance data of a batched polynomial pass; buffers by id:
+// Per-instance data of a batched polynomial pass (work items are groups of
+// 32 rows, whatever the instance's chunk height); buffers by id:
 // 0 = V[:, jj] (the step's input), 1 = W (output), 2 = P0, 3 = P1, 4 = T (pair temp).
 struct BatchPassInst {
-    int n, nslices;
-    const int *slice_ptr;
-    const int *col;
-    const void *val;
+    SellView A;
     double sigma;
     const void *V;
     int64_t ldv;
@@ -151,13 +154,19 @@ void launch_cgs_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, co
 void launch_scale_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int jj,
                         cudaStream_t st);
 #ifdef __CUDACC__
+// items: (instance, first 32-row group); each block takes `groups` groups
+// (32 * groups threads), grid = min(nitems, grid_per_sm * SMs).
 void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *tab, const int2 *items, int nitems,
-                       const int *lo, const int *hi, int jj, cudaStream_t st);
+                       const int *lo, const int *hi, int jj, int groups, int grid_per_sm, cudaStream_t st);
 #endif
 
-// Out[:, c] = sum_r V[:, r] Q[r, c] (c < kk), Q column major m x kk on the device.
+// Out[:, c] = sum_r V[:, r] Q[r, c] (c < kk), Q column major m x kk on the device,
+// in the basis' storage precision and arithmetic.
 void launch_rotate(Prec p, int n, const void *V, int64_t ldv, int m, const double *Q, int kk, void *out,
                    int64_t ldo, cudaStream_t st);
+// The same product into an FP64 output with FP64 arithmetic (Ritz vectors).
+void launch_rotate64(Prec p, int n, const void *V, int64_t ldv, int m, const double *Q, int kk, double *out,
+                     int64_t ldo, cudaStream_t st);
 
 // Column dots for the convergence test (Section 4).
 //  mode 0: q[4c+0] = Y_c.Y_c, q[4c+1] = Y_c.AY_c, q[4c+2] = Y_c.AY_{pc}
@@ -179,10 +188,10 @@ struct ColDotArgs {
 };
 void launch_coldots(Prec p, const ColDotArgs &a, cudaStream_t st);
 
-// SELL construction from a device CSR (row lengths -> slice widths -> fill).
-void launch_sell_slice_len(int n, const int *rowptr, int *slice_len, cudaStream_t st);
-void launch_sell_fill(Prec p, int n, const int *rowptr, const int *col, const double *val,
-                      const int *slice_ptr, int *scol, void *sval, cudaStream_t st);
+// SELL-C fill from a device CSR (slice pointers computed on the host); writes
+// scol (32-bit) or soff (16-bit offsets), whichever is non-null.
+void launch_sell_fill(Prec p, int n, int nslices, int cshift, const int *rowptr, const int *col, const double *val,
+                      const int *slice_ptr, int *scol, short *soff, void *sval, cudaStream_t st);
 void launch_csr_convert(Prec p, int64_t nnz, const double *val, void *out, cudaStream_t st);
 // y = x converted between storage precisions
 void launch_convert(Prec from, Prec to, int n, const void *x, void *y, cudaStream_t st);

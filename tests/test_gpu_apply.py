@@ -153,3 +153,81 @@ def test_orthogonalize_matches_oracle_cgs2(n, j):
     v = vd.cpu().numpy()
     assert np.abs(v - w2 / np.linalg.norm(w2)).max() <= tol / np.linalg.norm(w2) * 4
     assert np.abs(Q.T @ v).max() <= 1e-12 * np.sqrt(n)
+
+
+@pytest.mark.parametrize("n,j", [(1000, 7), (100003, 51), (20000, 128)])
+def test_orthogonalize_fp32_matches_oracle_cgs2(n, j):
+    """CGS2 on an FP32 basis (FP32 first pass, compensated second pass) vs the
+    oracle's FP64 cgs2 on the same FP32-rounded V and w.
+
+    h1 + h2 equals V^T w up to V^T of the rounding of w1 = w - V h1 to FP32
+    (|.| <= a few u32 ||w||); the compensated second pass adds O(u32^2).
+    """
+    import torch
+    from paper_1806_08020_gb300 import pp
+    u32 = 2.0 ** -24
+    rng = np.random.default_rng(n + 3 * j)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, j)))
+    Q = Q.astype(np.float32).astype(np.float64)
+    w = (rng.standard_normal(n) + Q @ rng.standard_normal(j) * 10).astype(np.float32).astype(np.float64)
+    ctx = pp.pp_create(inputs.diagonal(np.ones(n)), stream=torch.cuda.current_stream().cuda_stream,
+                       precision=pp.PP_FP32)
+    ldv = (n + 31) // 32 * 32
+    Vd = torch.zeros((j, ldv), dtype=torch.float32, device="cuda")
+    Vd[:, :n] = torch.tensor(Q.T, dtype=torch.float32)
+    wd = torch.tensor(w, dtype=torch.float32, device="cuda")
+    vd = torch.empty(n, dtype=torch.float32, device="cuda")
+    h = pp.pp_orthogonalize(ctx, Vd.data_ptr(), ldv, j, wd.data_ptr(), vd.data_ptr())
+    w2, href = O.cgs2(Q, w, O.Counters())
+    nw = np.linalg.norm(w)
+    tol = 16 * u32 * nw
+    assert np.abs(h[:j] - href).max() <= tol
+    assert abs(h[j] - np.linalg.norm(w2)) <= tol
+    v = vd.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(v - w2 / np.linalg.norm(w2)) <= 16 * u32 * nw / np.linalg.norm(w2)
+    assert np.abs(Q.T @ v).max() <= 16 * u32 * nw / np.linalg.norm(w2)
+
+
+def _wide_band_matrix():
+    """2-D CD (N = 200) plus a few couplings 35,000 rows away: |col - row| >= 2^15,
+    so 16-bit column offsets cannot hold it."""
+    import scipy.sparse as sp
+    base = O.to_scipy(inputs.convection_diffusion_2d(200, 20.0))
+    n = base.shape[0]
+    rows = np.arange(0, n - 35000, 997)
+    far = sp.csr_matrix((np.full(rows.size, 1e-3), (rows, rows + 35000)), shape=(n, n))
+    A = (base + far).tocsr()
+    A.sort_indices()
+    return inputs.CSR(n, A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("kind", ["cd", "band", "wide"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sell_formats_bit_identical(kind, precision):
+    """Every device format gives the same pi(A) x bit for bit: CSR, SELL with
+    chunk height 16 or 32, 16- or 32-bit column indices, and whatever chunk
+    height and block size the tuner picks.  Each row sums its entries in CSR
+    order in every format (SELL padding adds 0 * x = 0 exactly)."""
+    from paper_1806_08020_gb300 import pp
+    A = {"cd": lambda: inputs.convection_diffusion_2d(150, 50.0),
+         "band": lambda: inputs.banded_random(30011, 9, 5),
+         "wide": _wide_band_matrix}[kind]()
+    ref_ctx = pp.pp_create(A, precision=precision)
+    roots = pp.pp_poly_roots(pp.pp_build_poly(ref_ctx, 12, inputs.start_vector(A.n, 3, 0)))
+    x = inputs.start_vector(A.n, 3, 1)
+    variants = {"csr": dict(format=pp.PP_FMT_CSR), "c16": dict(format=pp.PP_FMT_SELL, sell_c=16),
+                "c32": dict(format=pp.PP_FMT_SELL, sell_c=32),
+                "c32_i32": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32),
+                "tuned": dict(format=pp.PP_FMT_SELL)}
+    out, info = {}, {}
+    for name, o in variants.items():
+        ctx = pp.pp_create(A, precision=precision, **o)
+        info[name] = pp.pp_format_info(ctx)
+        out[name] = pp.pp_apply_host(pp.pp_poly_from_roots(ctx, roots), x)
+    assert info["csr"]["fmt"] == pp.PP_FMT_CSR
+    assert info["c16"]["chunk"] == 16 and info["c32"]["chunk"] == 32
+    assert info["c32_i32"]["index_bits"] == 32
+    assert info["c32"]["index_bits"] == (32 if kind == "wide" else 16)
+    assert info["tuned"]["chunk"] in (16, 32) and info["tuned"]["threads"] in (128, 256, 512)
+    for name in variants:
+        assert np.array_equal(out[name], out["csr"]), name
