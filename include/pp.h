@@ -70,6 +70,8 @@ typedef struct {
     int sell_sigma;     /* SELL sorting window: must be 0 or 1 (rows keep their order) */
     int sell_index;     /* SELL column indices: 0 (default) = 16-bit offsets col - row when every
                            |col - row| < 2^15, else 32-bit; 32 = always 32-bit */
+    int sell_loop;      /* SELL row loop: 0 (default) = the tuner picks; 1 = unrolled by four;
+                           2 = loads of up to eight entries issued together */
     void *stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
 } pp_opts;
 
@@ -117,10 +119,12 @@ pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);
 /*
  * pp_format_info — the device format of A chosen at pp_create: fmt
  * (PP_FMT_CSR or PP_FMT_SELL), the SELL chunk height (0 for CSR), the column
- * index width in bits (16 or 32), the block size of the product kernels, and
- * the stored entries including SELL padding.  Any output pointer may be NULL.
+ * index width in bits (16 or 32), the block size of the product kernels, the
+ * SELL row loop (0: unrolled by four; 1: the loads of up to eight entries
+ * issued together), and the stored entries including SELL padding.  Any
+ * output pointer may be NULL.
  */
-pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bits, int *threads,
+pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bits, int *threads, int *row_loop,
                          int64_t *stored);
 
 /*

@@ -36,7 +36,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     inc = ["-I", os.path.join(ROOT, "include"), "-I", SRC]
     cu, cpp = sources()
-    deps = [os.path.join(SRC, f) for f in cu + cpp + ["pp_internal.h", "ctx.h"]] + [os.path.join(ROOT, "include", "pp.h")]
+    deps = [os.path.join(SRC, f) for f in cu + cpp + ["pp_internal.h", "ctx.h", "driver.h", "device_common.cuh"]]
+    deps.append(os.path.join(ROOT, "include", "pp.h"))
     newest = max(os.path.getmtime(p) for p in deps)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB

@@ -233,6 +233,7 @@ pp_status cgs2_step(pp_ctx *c, ppk::Prec pr, void *V, int64_t ldv, int j, void *
     a.j = j;
     a.part = c->d_part;
     a.ticket = c->d_ticket;
+    a.err = c->err();
     // pass 1: h1 = V^T w
     a.mode = 0;
     a.w = w;
@@ -343,6 +344,17 @@ pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vec
     return PP_OK;
 }
 
+pp_status check_sweeps(pp_ctx *c) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, c->err(), sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!e) return PP_OK;
+    CK(cudaMemsetAsync(c->err(), 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->d_ticket, 0, 64, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return pp_fail(PP_ETIMEOUT, "CGS2 sweep: a bounded wait for staged basis tiles expired");
+}
+
 // GMRES(d) Arnoldi on Op from b (host), then harmonic Ritz roots, Leja, added roots.
 pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, pp_poly *out) {
     if (d < 1 || d > 127) return pp_fail(PP_EINVAL, "degree must be in [1, 127] (got %d)", d);
@@ -388,6 +400,7 @@ pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cleanup();
     if (e != cudaSuccess) return pp_fail(PP_ECUDA, "build: %s", cudaGetErrorString(e));
+    CKS(check_sweeps(c));
     for (double v : H)
         if (!std::isfinite(v)) return pp_fail(PP_ENUMERIC, "build: non-finite Hessenberg entry");
     // lucky breakdown: h_{j+1,j} <= 1e-14 ||H(0:j+2, 0:j+1)||_F
@@ -641,6 +654,8 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     if (c->opts.sell_sigma > 1) return fail(pp_fail(PP_EINVAL, "pp_create: sell_sigma must be 0 or 1"));
     if (c->opts.sell_index != 0 && c->opts.sell_index != 32)
         return fail(pp_fail(PP_EINVAL, "pp_create: sell_index must be 0 or 32"));
+    if (c->opts.sell_loop < 0 || c->opts.sell_loop > 2)
+        return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop must be 0, 1 or 2"));
     std::vector<int> cands;
     if (c->opts.sell_c) cands.push_back(c->opts.sell_c == 16 ? 4 : 5);
     else cands = {5, 4};
@@ -684,9 +699,11 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         M.fmt = 2;
         std::vector<int> threads = {256};
         if (!c->opts.sell_c) threads = {128, 256, 512};
-        const bool tune = cands.size() * threads.size() > 1;
+        std::vector<int> loops = {0, 1};
+        if (c->opts.sell_loop) loops = {c->opts.sell_loop - 1};
+        const bool tune = cands.size() * threads.size() * loops.size() > 1;
         double best_t = INFINITY;
-        int best_threads = 256;
+        int best_threads = 256, best_wide = 0;
         ppk::SellView best{};
         std::vector<void *> best_mem;
         for (int cs : cands) {
@@ -695,16 +712,19 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
             if ((st = build_sell(c, pr, n, rowptr, cs, off16, d_rowptr, d_col, d_val, sv, mem)) < 0) return fail(st);
             M.sell = sv;
             bool better = false;
-            for (int t : threads) {
-                M.threads = t;
-                double tt = tune ? time_product(c, M) : 0.0;
-                if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
-                if (tt < best_t) {
-                    best_t = tt;
-                    best_threads = t;
-                    better = true;
+            for (int wide : loops)
+                for (int t : threads) {
+                    M.threads = t;
+                    M.wide = wide;
+                    double tt = tune ? time_product(c, M) : 0.0;
+                    if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
+                    if (tt < best_t) {
+                        best_t = tt;
+                        best_threads = t;
+                        best_wide = wide;
+                        better = true;
+                    }
                 }
-            }
             for (void *q : better ? best_mem : mem) dfree(c, q);
             if (better) {
                 best = sv;
@@ -713,6 +733,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         }
         M.sell = best;
         M.threads = best_threads;
+        M.wide = best_wide;
         c->stored = sell_padded(n, rowptr, best.cshift);
     } else {
         M.fmt = 1;
@@ -763,6 +784,7 @@ pp_status pp_orthogonalize(pp_ctx *c, const void *V, int64_t ldv, int j, void *w
     a.j = j;
     a.part = c->d_part;
     a.ticket = c->d_ticket;
+    a.err = c->err();
     a.mode = 0;
     a.w = w;
     a.out = h1;
@@ -787,7 +809,7 @@ pp_status pp_orthogonalize(pp_ctx *c, const void *V, int64_t ldv, int j, void *w
     CKS(check_launch(c));
     CK(cudaMemcpyAsync(h_host, dh, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    return PP_OK;
+    return check_sweeps(c);
 }
 
 pp_status pp_matrix_info(const pp_ctx *c, double *norm1, double *sigma) {
@@ -797,13 +819,15 @@ pp_status pp_matrix_info(const pp_ctx *c, double *norm1, double *sigma) {
     return PP_OK;
 }
 
-pp_status pp_format_info(const pp_ctx *c, int *fmt, int *chunk, int *index_bits, int *threads, int64_t *stored) {
+pp_status pp_format_info(const pp_ctx *c, int *fmt, int *chunk, int *index_bits, int *threads, int *row_loop,
+                         int64_t *stored) {
     if (!c) return pp_fail(PP_EINVAL, "pp_format_info: null context");
     const bool sell = c->A.fmt == 2;
     if (fmt) *fmt = sell ? PP_FMT_SELL : PP_FMT_CSR;
     if (chunk) *chunk = sell ? 1 << c->A.sell.cshift : 0;
     if (index_bits) *index_bits = (sell && c->A.sell.off) ? 16 : 32;
     if (threads) *threads = sell ? c->A.threads : 256;
+    if (row_loop) *row_loop = sell ? c->A.wide : 0;
     if (stored) *stored = c->stored;
     return PP_OK;
 }

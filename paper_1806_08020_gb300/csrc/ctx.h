@@ -85,6 +85,8 @@ struct pp_ctx {
     pp_ctx *twin = nullptr;  // FP64 copy of an FP32 context (mixed-precision fallback)
     int64_t stored = 0;      // matrix entries held on the device (with SELL padding)
     int64_t ldv() const { return (n + 31) / 32 * 32; }
+    // device error word of the TMA-staged sweeps (set when a bounded wait expired)
+    int *err() const { return (int *)(d_small + 4000); }
 };
 
 struct pp_poly {
@@ -129,5 +131,8 @@ pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, voi
 void accumulate_times(Timers &tm, std::vector<std::pair<int, int>> &marks, double &t_apply, double &t_orth);
 pp_status upload_vec(pp_ctx *c, const double *h, double s, void *d);
 pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vector<double> &out, ppk::Prec pr);
+// PP_ETIMEOUT (and the error word and reduction ticket cleared) when a
+// TMA-staged sweep gave up waiting since the last check; synchronises the stream.
+pp_status check_sweeps(pp_ctx *c);
 
 }  // namespace ppi

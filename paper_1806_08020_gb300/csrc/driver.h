@@ -192,6 +192,7 @@ struct Driver {
             ca.out = dG + (size_t)col * ldg;
             ca.part = c->d_part;
             ca.ticket = c->d_ticket;
+            ca.err = c->err();
             ppk::launch_cgs(ppk::F64, ca, c->stream);
             CKS(check_launch(c));
             S.mvps += 1;
@@ -248,6 +249,7 @@ struct Driver {
             std::vector<double> Gfull((size_t)ldg * nz), G((size_t)nz * nz);
             CK(cudaMemcpyAsync(Gfull.data(), dG, Gfull.size() * 8, cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
+            CKS(check_sweeps(c));
             for (int j = 0; j < nz; ++j)
                 for (int i = 0; i < nz; ++i) G[i + (size_t)j * nz] = Gfull[i + (size_t)j * ldg];
             for (double v : G)

@@ -74,6 +74,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
         double th0 = now();
         CK(cudaMemcpyAsync(H.data(), dH, H.size() * 8, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        CKS(check_sweeps(c));
         accumulate_times(tm, marks, S.t_apply, S.t_orth);
         CKS(wanted_set(H, ldh, m, nev, target, cy));
         CKS(D.ritz_test(V, c->A.prec, m, cy.Sw, cy.sl, rtol, R, S));

@@ -1,137 +1,25 @@
-// CUDA kernels of the hot path (sm_103a).
+// Kernels of the orthogonalisation and the restart (sm_103a).
 //
-//  * k_pass / k_step: one fused pass of the factored GMRES polynomial
-//    (Eq. (2.1)) on SELL-C (16- or 32-bit column indices) or CSR: SpMV with
-//    A - sigma I plus the root-step axpy and the running sum (Section 2
-//    footnote 2) in the same pass; conjugate pairs use two passes in real
-//    arithmetic; the double polynomial's outer step (Section 8) is fused into
-//    the last inner pass.
 //  * k_cgs: the three passes of classical Gram-Schmidt with one
 //    reorthogonalisation (Section 4), each a single sweep over the basis with
-//    a deterministic two-level reduction finished by the last block.
+//    a deterministic two-level reduction finished by the last block;
+//    k_cgs_tma stages the basis tiles in shared memory with the bulk-copy
+//    engine; k_cgs_batch serves many instances in one launch.
 //  * k_rotate: V_m Q_k for the thick restart and Ritz vectors (Section 4).
 //  * k_coldots: Rayleigh quotients and residual norms on A (Section 4).
+#include "device_common.cuh"
 #include "pp_internal.h"
 
-#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdlib>
 
 namespace ppk {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-
 template <typename T>
 __device__ __forceinline__ double ld_acc(const T *p, size_t i) {
     return (double)__ldg(p + i);
-}
-
-// ---------------------------------------------------------------------------
-// Fused root step
-// ---------------------------------------------------------------------------
-template <typename T, typename Acc>
-__device__ __forceinline__ void step_epilogue(int row, Acc u, const StepArgs &s) {
-    const T *x = (const T *)s.x;
-    Acc xi = (Acc)x[row];
-    if (s.sigma != 0.0) u = u - (Acc)s.sigma * xi;
-    if (s.plain) {
-        ((T *)s.y)[row] = (T)u;
-        return;
-    }
-    Acc delta = (Acc)s.a1 * xi + (Acc)s.a2 * u;
-    if (s.y) {
-        Acc base = s.aux ? (Acc)((const T *)s.aux)[row] : xi;
-        ((T *)s.y)[row] = (T)(base - delta);
-    }
-    if (s.r) {
-        T *r = (T *)s.r;
-        Acc rv = s.r_init ? delta : (Acc)r[row] + delta;
-        if (s.r_write) r[row] = (T)rv;
-        if (s.oy) {
-            Acc od = (Acc)s.b2 * rv;
-            if (s.ox) od += (Acc)s.b1 * (Acc)((const T *)s.ox)[row];
-            ((T *)s.oy)[row] = (T)((Acc)((const T *)s.obase)[row] - od);
-        }
-    }
-}
-
-// Row sum u = sum_k A(row, col_k) x(col_k) over a SELL-C slice row (the
-// slice width is uniform across the slice).  Kept to ~30 registers so that
-// 2048 threads stay resident per SM: the gathers are latency-bound and need
-// the warps more than a wider unroll.  The sum runs over the row's entries in
-// CSR order whatever C, the index width or the block size (padding adds
-// 0 * x exactly), so every format gives bit-identical results.
-template <typename T, typename V, typename Acc, bool OFF16>
-__device__ __forceinline__ Acc sell_row(const SellView &A, const T *__restrict__ x, int row) {
-    const int cs = A.cshift;
-    const int sl = row >> cs, lane = row & ((1 << cs) - 1);
-    const int beg = __ldg(A.slice_ptr + sl);
-    const int len = (__ldg(A.slice_ptr + sl + 1) - beg) >> cs;
-    const V *val = (const V *)A.val + beg + lane;
-    Acc acc = 0;
-    if (OFF16) {
-        const short *off = A.off + beg + lane;
-        const T *xr = x + row;
-#pragma unroll 4
-        for (int k = 0; k < len; ++k)
-            acc = fma((Acc)__ldg(val + (k << cs)), (Acc)__ldg(xr + __ldg(off + (k << cs))), acc);
-    } else {
-        const int *col = A.col + beg + lane;
-#pragma unroll 4
-        for (int k = 0; k < len; ++k)
-            acc = fma((Acc)__ldg(val + (k << cs)), (Acc)__ldg(x + __ldg(col + (k << cs))), acc);
-    }
-    return acc;
-}
-
-constexpr int kPassMaxThreads = 512;
-
-// Row sum of the matrix in format FMT: 0 CSR, 1 SELL with 32-bit columns,
-// 2 SELL with 16-bit offsets.  All three sum a row's entries in CSR order.
-template <typename T, typename V, typename Acc, int FMT>
-__device__ __forceinline__ Acc row_sum(const SellView &S, const CsrView &R, const T *__restrict__ x, int row) {
-    if constexpr (FMT == 0) {
-        const int beg = __ldg(R.rowptr + row), end = __ldg(R.rowptr + row + 1);
-        const V *val = (const V *)R.val;
-        Acc acc = 0;
-        for (int k = beg; k < end; ++k) acc = fma((Acc)__ldg(val + k), (Acc)__ldg(x + __ldg(R.col + k)), acc);
-        return acc;
-    } else {
-        return sell_row<T, V, Acc, FMT == 2>(S, x, row);
-    }
-}
-
-// Specialised passes of the factored polynomial (the hot cases):
-//   KIND 0 plain:  y = u
-//   KIND 1 real:   y = x - a2 u                (a2 = 1/theta)
-//   KIND 2 pair 2: y = aux - a1 x - a2 u        (x = t, aux = p, a1 = c1, a2 = -c2)
-// with u = A x - sigma x when SIGMA.
-template <typename T, typename V, typename Acc, int KIND, bool SIGMA, int FMT>
-__global__ void __launch_bounds__(kPassMaxThreads) k_pass(SellView S, CsrView R, StepArgs s) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= (FMT == 0 ? R.n : S.n)) return;
-    const T *x = (const T *)s.x;
-    Acc u = row_sum<T, V, Acc, FMT>(S, R, x, row);
-    if (SIGMA) u = fma(-(Acc)s.sigma, (Acc)x[row], u);
-    T *y = (T *)s.y;
-    if (KIND == 0) {
-        y[row] = (T)u;
-    } else if (KIND == 1) {
-        y[row] = (T)fma(-(Acc)s.a2, u, (Acc)x[row]);
-    } else {
-        Acc v = fma(-(Acc)s.a1, (Acc)x[row], (Acc)((const T *)s.aux)[row]);
-        y[row] = (T)fma(-(Acc)s.a2, u, v);
-    }
-}
-
-// General pass (running sum, optional output, outer epilogue): see StepArgs.
-template <typename T, typename V, typename Acc, int FMT>
-__global__ void __launch_bounds__(kPassMaxThreads) k_step(SellView S, CsrView R, StepArgs s) {
-    int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= (FMT == 0 ? R.n : S.n)) return;
-    Acc acc = row_sum<T, V, Acc, FMT>(S, R, (const T *)s.x, row);
-    step_epilogue<T, Acc>(row, acc, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -416,6 +304,199 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// CGS2 sweeps with the basis staged in shared memory by the bulk-copy (TMA)
+// engine.  Each block owns the 64-row tiles bid, bid + nblk, ...; for every
+// full tile one warp issues j + 1 bulk copies (the tile's rows of V[:, c] for
+// c < j, and of w) into a pipeline stage whose mbarrier counts the bytes;
+// `stages` tiles are in flight while the block computes on the oldest.  The
+// arithmetic is that of cgs_body_f64 / cgs_body_f32 on the same rows in the
+// same order, so both paths give bit-identical sweeps.  A ragged last tile
+// (n not a multiple of 64) is read with plain loads.  Every wait on an
+// mbarrier is bounded: on expiry the block records the failure in *err,
+// waits (bounded) for its copies still in flight, contributes zero partials
+// so the grid reduction completes, and the host reports PP_ETIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int kMaxStages = 4;
+constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls; a healthy tile needs a few
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+    for (long long it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <typename T>
+struct CgsArith;
+template <>
+struct CgsArith<double> {  // FP64 throughout
+    using A = double;
+    struct Dot {
+        double s = 0;
+        __device__ void add_first(double x, double y) { s = fma(x, y, s); }
+        __device__ void add_second(double x, double y) { s = fma(x, y, s); }
+        __device__ double value() const { return s; }
+    };
+};
+template <>
+struct CgsArith<float> {  // FP32 first pass and updates, Dot2 second pass
+    using A = float;
+    struct Dot {
+        float s = 0.f, c = 0.f;
+        __device__ void add_first(float x, float y) { s = fmaf(x, y, s); }
+        __device__ void add_second(float x, float y) { dot2_term(x, y, s, c); }
+        __device__ double value() const { return (double)s + (double)c; }
+    };
+};
+
+template <typename T, int CPW>
+__global__ void __launch_bounds__(kThreads) k_cgs_tma(CgsArgs a, int stages, int *err) {
+    using Acc = typename CgsArith<T>::A;
+    using Dot = typename CgsArith<T>::Dot;
+    extern __shared__ __align__(128) unsigned char tma_smem[];
+    __shared__ unsigned long long full[kMaxStages];
+    __shared__ Acc red[kWarps][kRows];
+    __shared__ Acc wsh[kRows];
+    __shared__ Acc hs[8 * CPW];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int j = a.j, n = a.n, bid = blockIdx.x, nblk = gridDim.x;
+    const size_t stage_elems = (size_t)(j + 1) * kRows;  // V tile columns, then the w tile
+    T *const stage0 = (T *)tma_smem;
+    const int nfull = n / kRows;
+    const int mine = bid < nfull ? (nfull - 1 - bid) / nblk + 1 : 0;  // this block's full tiles
+    if (a.mode != 0)
+        for (int c = tid; c < j; c += kThreads) hs[c] = (Acc)a.h[c];
+    if (tid == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // local tile k -> stage k % stages (issued by warp 0)
+    auto issue = [&](int k) {
+        const int s = k % stages;
+        const size_t r0 = (size_t)(bid + (size_t)k * nblk) * kRows;
+        T *dst = stage0 + (size_t)s * stage_elems;
+        if (lane == 0) mbar_arrive_expect(&full[s], (unsigned)(stage_elems * sizeof(T)));
+        __syncwarp();
+        for (int c = lane; c <= j; c += 32) {
+            const T *src = c < j ? (const T *)a.V + (size_t)c * a.ldv + r0 : (const T *)a.w + r0;
+            bulk_copy_g2s(dst + (size_t)c * kRows, src, kRows * sizeof(T), &full[s]);
+        }
+    };
+    Dot acc[CPW];
+    double nrm = 0;
+    // one tile: V(c, i) and W(i) give rows r0 + i of V[:, c] and w (zero past n)
+    auto tile = [&](int r0, auto V, auto W) {
+        if (a.mode == 0) {
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc)
+                if (warp + kWarps * cc < j)
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) acc[cc].add_first(V(warp + kWarps * cc, lane + 32 * q), W(lane + 32 * q));
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            Acc s = 0;
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc) {
+                int c = warp + kWarps * cc;
+                if (c < j) s = fma(V(c, lane + 32 * q), hs[c], s);
+            }
+            red[warp][lane + 32 * q] = s;
+        }
+        __syncthreads();
+        if (tid < kRows) {
+            int row = r0 + tid;
+            Acc v = 0;
+            if (row < n) {
+                Acc s = 0;
+#pragma unroll
+                for (int ww = 0; ww < kWarps; ++ww) s += red[ww][tid];
+                v = W(tid) - s;
+                ((T *)a.wout)[row] = (T)v;
+                nrm = fma((double)v, (double)v, nrm);
+            }
+            wsh[tid] = v;
+        }
+        __syncthreads();
+        if (a.mode == 1) {
+#pragma unroll
+            for (int cc = 0; cc < CPW; ++cc)
+                if (warp + kWarps * cc < j)
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) acc[cc].add_second(V(warp + kWarps * cc, lane + 32 * q), wsh[lane + 32 * q]);
+        }
+    };
+    if (warp == 0)
+        for (int k = 0; k < stages - 1 && k < mine; ++k) issue(k);
+    int k = 0;
+    bool bad = false;
+    for (; k < mine; ++k) {
+        if (warp == 0 && k + stages - 1 < mine) issue(k + stages - 1);
+        const bool ok = mbar_wait_bounded(&full[k % stages], (unsigned)(k / stages) & 1u);
+        if (__syncthreads_or(!ok)) {
+            bad = true;
+            break;
+        }
+        const T *Vs = stage0 + (size_t)(k % stages) * stage_elems;
+        const T *Ws = Vs + (size_t)j * kRows;
+        tile((bid + k * nblk) * kRows, [&](int c, int i) { return (Acc)Vs[(size_t)c * kRows + i]; },
+             [&](int i) { return (Acc)Ws[i]; });
+        __syncthreads();  // the stage is free for the copy issued next iteration
+    }
+    if (bad) {
+        // record, drain this block's copies still in flight (bounded), drop its partials
+        if (tid == 0) atomicExch(err, 1);
+        for (int kk = k; kk < mine && kk < k + stages; ++kk)
+            mbar_wait_bounded(&full[kk % stages], (unsigned)(kk / stages) & 1u);
+        __syncthreads();
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) acc[cc] = Dot();
+        nrm = 0;
+    } else if (n % kRows != 0 && (nfull % nblk) == bid) {
+        // ragged last tile: plain loads
+        const int r0 = nfull * kRows;
+        const T *V = (const T *)a.V;
+        const T *w = (const T *)a.w;
+        tile(r0,
+             [&](int c, int i) { return r0 + i < n ? (Acc)__ldg(V + (size_t)c * a.ldv + r0 + i) : (Acc)0; },
+             [&](int i) { return r0 + i < n ? (Acc)__ldg(w + r0 + i) : (Acc)0; });
+    }
+    double accd[CPW];
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) accd[cc] = acc[cc].value();
+    cgs_finish<CPW>(a, bid, nblk, accd, nrm);
+}
+
+// ---------------------------------------------------------------------------
 // Batched forms: many independent instances in one launch.  Instance state is
 // in device tables, so one captured graph serves every cycle; instance i is
 // active at Arnoldi step jj when lo[i] <= jj < hi[i] (its restart column and
@@ -474,36 +555,6 @@ __global__ void k_scale_batch(const BatchCgsInst *ci, int count, const int *lo, 
     const double s = *I.scal;
     for (int r = (blockIdx.x - I.blk0) * kThreads + threadIdx.x; r < I.n; r += I.nblk * kThreads)
         x[r] = (T)((double)x[r] * s);
-}
-
-// One polynomial pass for every active instance: warp = 32 consecutive rows
-// of one instance; a block takes blockDim/32 such groups of one instance
-// (a work item) and blocks stride over the work items.
-template <typename T>
-__global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassInst *pi, const BatchPassEntry *tab,
-                                                                const int2 *items, int nitems, const int *lo,
-                                                                const int *hi, int jj) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int2 itm = items[it];
-        const BatchPassEntry e = tab[itm.x];
-        if (e.kind < 0 || jj < lo[itm.x] || jj >= hi[itm.x]) continue;
-        const BatchPassInst &I = pi[itm.x];
-        const int row = (itm.y + warp) * 32 + lane;
-        if (row >= I.A.n) continue;
-        const T *bufs[5] = {(const T *)I.V + (size_t)jj * I.ldv, (const T *)I.W, (const T *)I.P0, (const T *)I.P1,
-                            (const T *)I.T};
-        const T *x = bufs[e.src];
-        T *y = (T *)bufs[e.dst];
-        T u = I.A.off ? sell_row<T, T, T, true>(I.A, x, row) : sell_row<T, T, T, false>(I.A, x, row);
-        if (I.sigma != 0.0) u = fma(-(T)I.sigma, x[row], u);
-        if (e.kind == 0)
-            y[row] = u;
-        else if (e.kind == 1)
-            y[row] = fma(-(T)e.a2, u, x[row]);
-        else
-            y[row] = fma(-(T)e.a2, u, fma(-(T)e.a1, x[row], bufs[e.aux][row]));
-    }
 }
 
 template <typename T>
@@ -610,94 +661,11 @@ __global__ void __launch_bounds__(kThreads) k_coldots(ColDotArgs a) {
     if (threadIdx.x == 0) *a.ticket = 0;
 }
 
-// ---------------------------------------------------------------------------
-// SELL-32 construction
-// ---------------------------------------------------------------------------
-template <typename V>
-__global__ void k_sell_fill(int n, int nslices, int cshift, const int *rowptr, const int *col, const double *val,
-                            const int *slice_ptr, int *scol, short *soff, V *sval) {
-    int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= (nslices << cshift)) return;
-    int sl = row >> cshift, lane = row & ((1 << cshift) - 1);
-    int beg = slice_ptr[sl], width = (slice_ptr[sl + 1] - beg) >> cshift;
-    int rb = row < n ? rowptr[row] : 0, re = row < n ? rowptr[row + 1] : 0;
-    int last = row < n ? (re > rb ? col[re - 1] : row) : 0;
-    for (int k = 0; k < width; ++k) {
-        int src = rb + k;
-        size_t dst = (size_t)beg + ((size_t)k << cshift) + lane;
-        int cc = src < re ? col[src] : last;  // padding: repeat a valid column, value 0
-        if (scol) scol[dst] = cc;
-        if (soff) soff[dst] = row < n ? (short)(cc - row) : (short)0;  // rows past n are never read
-        sval[dst] = src < re ? (V)val[src] : (V)0;
-    }
-}
-
-template <typename V>
-__global__ void k_convert_vals(int64_t nnz, const double *val, V *out) {
-    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * kThreads)
-        out[i] = (V)val[i];
-}
-
-template <typename A, typename B>
-__global__ void k_convert(int n, const A *x, B *y) {
-    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) y[i] = (B)x[i];
-}
-
-int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 132;
-    }
-    return sms;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <typename T, int FMT>
-static void pass_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
-    const int threads = A.threads;
-    const int blocks = (A.n + threads - 1) / threads;
-    const bool general = s.r || s.oy || !s.y;
-    const bool sig = s.sigma != 0.0;
-    if (general || (!s.plain && !s.aux && s.a1 != 0.0)) {  // not one of the specialised forms
-        k_step<T, T, T, FMT><<<blocks, threads, 0, st>>>(A.sell, A.csr, s);
-        return;
-    }
-    int kind = s.plain ? 0 : (s.aux ? 2 : 1);
-#define PP_PASS(K, S) k_pass<T, T, T, K, S, FMT><<<blocks, threads, 0, st>>>(A.sell, A.csr, s)
-    if (kind == 0) {
-        if (sig) PP_PASS(0, true); else PP_PASS(0, false);
-    } else if (kind == 1) {
-        if (sig) PP_PASS(1, true); else PP_PASS(1, false);
-    } else {
-        if (sig) PP_PASS(2, true); else PP_PASS(2, false);
-    }
-#undef PP_PASS
-}
-
-template <typename T>
-static void pass_format(const Matrix &A, const StepArgs &s, cudaStream_t st) {
-    if (A.fmt != 2)
-        pass_dispatch<T, 0>(A, s, st);
-    else if (A.sell.off)
-        pass_dispatch<T, 2>(A, s, st);
-    else
-        pass_dispatch<T, 1>(A, s, st);
-}
-
-void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st) {
-    if (A.prec == F64)
-        pass_format<double>(A, s, st);
-    else
-        pass_format<float>(A, s, st);
-}
-
 int cgs_grid(int n) {
     int tiles = (n + kRows - 1) / kRows;
     int g = num_sms() * 4;
@@ -720,8 +688,51 @@ static int resident_grid(int n, int cap) {
     return tiles < g ? tiles : g;
 }
 
+// TMA-staged sweeps need 16-byte aligned column starts and w, a context's
+// error word, and at least one full tile; PP_NO_TMA in the environment turns
+// them off (the plain sweeps compute the same values).
+static bool tma_usable(const CgsArgs &a, size_t esz) {
+    static const bool off = std::getenv("PP_NO_TMA") != nullptr;
+    return !off && a.err && a.n >= kRows && ((uintptr_t)a.V % 16) == 0 && ((uintptr_t)a.w % 16) == 0 &&
+           (a.ldv * (int64_t)esz) % 16 == 0 && a.j >= 1 && a.j <= 128;
+}
+
+template <typename T, int CPW>
+static void cgs_tma_launch(const CgsArgs &a, int cap, cudaStream_t st) {
+    static bool attr = false;  // one per instantiation
+    if (!attr) {
+        cudaFuncSetAttribute(k_cgs_tma<T, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    const size_t stage = (size_t)(a.j + 1) * kRows * sizeof(T);
+    int stages = (int)(96 * 1024 / stage);
+    stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
+    const size_t smem = stage * stages;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_tma<T, CPW>, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;
+    const int tiles = (a.n + kRows - 1) / kRows;
+    int g = per_sm * num_sms();
+    if (cap > 0 && g > cap) g = cap;
+    if (g > tiles) g = tiles;
+    k_cgs_tma<T, CPW><<<g, kThreads, smem, st>>>(a, stages, a.err);
+}
+
 template <typename T>
 static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
+    if (tma_usable(a, sizeof(T))) {
+        int cpw = (a.j + kWarps - 1) / kWarps;
+        if (cpw <= 2)
+            cgs_tma_launch<T, 2>(a, cap, st);
+        else if (cpw <= 4)
+            cgs_tma_launch<T, 4>(a, cap, st);
+        else if (cpw <= 8)
+            cgs_tma_launch<T, 8>(a, cap, st);
+        else
+            cgs_tma_launch<T, 16>(a, cap, st);
+        return;
+    }
     int cpw = (a.j + kWarps - 1) / kWarps;
     if (cpw <= 2)
         k_cgs<T, 2><<<resident_grid<T, 2>(a.n, cap), kThreads, 0, st>>>(a);
@@ -758,18 +769,6 @@ void launch_scale_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, 
         k_scale_batch<double><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, jj);
     else
         k_scale_batch<float><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, jj);
-}
-
-void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *tab, const int2 *items, int nitems,
-                       const int *lo, const int *hi, int jj, int groups, int grid_per_sm, cudaStream_t st) {
-    int g = num_sms() * grid_per_sm;
-    if (nitems < g) g = nitems;
-    if (g < 1) g = 1;
-    const int threads = 32 * groups;
-    if (p == F64)
-        k_pass_batch<double><<<g, threads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
-    else
-        k_pass_batch<float><<<g, threads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
 }
 
 int cgs_batch_blocks(int n) {
@@ -836,35 +835,6 @@ void launch_coldots(Prec p, const ColDotArgs &a, cudaStream_t st) {
         k_coldots<double><<<grid, kThreads, 0, st>>>(a);
     else
         k_coldots<float><<<grid, kThreads, 0, st>>>(a);
-}
-
-void launch_sell_fill(Prec p, int n, int nslices, int cshift, const int *rowptr, const int *col, const double *val,
-                      const int *slice_ptr, int *scol, short *soff, void *sval, cudaStream_t st) {
-    const int rows = nslices << cshift;
-    const int blocks = (rows + kThreads - 1) / kThreads;
-    if (p == F64)
-        k_sell_fill<double><<<blocks, kThreads, 0, st>>>(n, nslices, cshift, rowptr, col, val, slice_ptr, scol, soff,
-                                                         (double *)sval);
-    else
-        k_sell_fill<float><<<blocks, kThreads, 0, st>>>(n, nslices, cshift, rowptr, col, val, slice_ptr, scol, soff,
-                                                        (float *)sval);
-}
-
-void launch_csr_convert(Prec p, int64_t nnz, const double *val, void *out, cudaStream_t st) {
-    int g = num_sms() * 4;
-    if (p == F32) k_convert_vals<float><<<g, kThreads, 0, st>>>(nnz, val, (float *)out);
-}
-
-void launch_convert(Prec from, Prec to, int n, const void *x, void *y, cudaStream_t st) {
-    int g = num_sms() * 4;
-    if (from == F64 && to == F32)
-        k_convert<double, float><<<g, kThreads, 0, st>>>(n, (const double *)x, (float *)y);
-    else if (from == F32 && to == F64)
-        k_convert<float, double><<<g, kThreads, 0, st>>>(n, (const float *)x, (double *)y);
-    else if (from == F64)
-        k_convert<double, double><<<g, kThreads, 0, st>>>(n, (const double *)x, (double *)y);
-    else
-        k_convert<float, float><<<g, kThreads, 0, st>>>(n, (const float *)x, (float *)y);
 }
 
 }  // namespace ppk

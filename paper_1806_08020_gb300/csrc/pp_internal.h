@@ -82,6 +82,7 @@ struct Matrix {
     int n = 0;
     int fmt = 2;  // 1 CSR, 2 SELL
     int threads = 256;  // block size of the SELL pass kernels (64..512, chosen by the tuner)
+    int wide = 0;       // SELL row loop: 0 unrolled by four, 1 chunks of eight loads (tuner)
     Prec prec = F64;
     SellView sell{};
     CsrView csr{};
@@ -109,6 +110,7 @@ struct CgsArgs {
     double *out = nullptr;
     double *part = nullptr;
     unsigned *ticket = nullptr;
+    int *err = nullptr;  // set to 1 by a TMA-staged sweep whose bounded wait expired (null: plain sweeps only)
 };
 int cgs_grid(int n);
 void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st);

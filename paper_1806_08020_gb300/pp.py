@@ -26,7 +26,8 @@ PP_TARGET_SM, PP_TARGET_SR = 0, 1
 class pp_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("format", C.c_int), ("target", C.c_int), ("sigma", C.c_double),
                 ("add_roots", C.c_int), ("max_cycles", C.c_int), ("refine_steps", C.c_int),
-                ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sell_index", C.c_int), ("stream", C.c_void_p)]
+                ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sell_index", C.c_int), ("sell_loop", C.c_int),
+                ("stream", C.c_void_p)]
 
 
 class pp_stats(C.Structure):
@@ -56,7 +57,7 @@ _SIGS = {
     "pp_create": (C.c_int, [C.POINTER(_P), C.c_int64, _I64, C.POINTER(C.c_int32), _D, C.POINTER(pp_opts)]),
     "pp_destroy": (None, [_P]),
     "pp_matrix_info": (C.c_int, [_P, _D, _D]),
-    "pp_format_info": (C.c_int, [_P, _I, _I, _I, _I, _I64]),
+    "pp_format_info": (C.c_int, [_P, _I, _I, _I, _I, _I, _I64]),
     "pp_launch_count": (C.c_int64, [_P]),
     "pp_build_poly": (C.c_int, [_P, C.c_int, _D, C.POINTER(_P)]),
     "pp_build_poly2": (C.c_int, [_P, C.c_int, C.c_int, _D, C.POINTER(_P)]),
@@ -197,11 +198,13 @@ def pp_matrix_info(ctx: Context) -> tuple[float, float]:
 
 
 def pp_format_info(ctx: Context) -> dict:
-    """Device format of A: fmt, chunk height, index bits, block size, stored entries."""
-    f, c, ib, t = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    """Device format of A: fmt, chunk height, index bits, block size, row loop, stored entries."""
+    f, c, ib, t, w = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
     st = C.c_int64()
-    _check(LIB.pp_format_info(ctx.handle, C.byref(f), C.byref(c), C.byref(ib), C.byref(t), C.byref(st)))
-    return {"fmt": f.value, "chunk": c.value, "index_bits": ib.value, "threads": t.value, "stored": st.value}
+    _check(LIB.pp_format_info(ctx.handle, C.byref(f), C.byref(c), C.byref(ib), C.byref(t), C.byref(w),
+                              C.byref(st)))
+    return {"fmt": f.value, "chunk": c.value, "index_bits": ib.value, "threads": t.value, "row_loop": w.value,
+            "stored": st.value}
 
 
 def pp_launch_count(ctx: Context) -> int:

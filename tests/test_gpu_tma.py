@@ -1,0 +1,62 @@
+"""CGS2 sweeps with the basis staged by the bulk-copy (TMA) engine against the
+plain sweeps (PP_NO_TMA), through the C-ABI.
+
+Both compute the same projections on the same rows; only the grid (and so
+the order of the block partial sums) may differ, so they agree to rounding.
+The plain run happens in a child process because the switch is read once.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import json, sys
+import numpy as np, torch
+sys.path.insert(0, %r)
+from paper_1806_08020_gb300 import inputs, pp
+out = {}
+for prec, dt in ((0, torch.float64), (1, torch.float32)):
+    for n, j in ((4099, 33), (100003, 51), (20000, 128), (64, 3)):
+        rng = np.random.default_rng(n + j + prec)
+        Q, _ = np.linalg.qr(rng.standard_normal((n, j)))
+        w = rng.standard_normal(n) + Q @ rng.standard_normal(j) * 10
+        ctx = pp.pp_create(inputs.diagonal(np.ones(n)), stream=torch.cuda.current_stream().cuda_stream,
+                           precision=prec)
+        ldv = (n + 31) // 32 * 32
+        Vd = torch.zeros((j, ldv), dtype=dt, device="cuda")
+        Vd[:, :n] = torch.tensor(Q.T, dtype=dt)
+        wd = torch.tensor(w, dtype=dt, device="cuda")
+        vd = torch.empty(n, dtype=dt, device="cuda")
+        h = pp.pp_orthogonalize(ctx, Vd.data_ptr(), ldv, j, wd.data_ptr(), vd.data_ptr())
+        out[f"{prec}_{n}_{j}"] = [h.tolist(), vd.double().cpu().numpy().tolist()]
+json.dump(out, sys.stdout)
+""" % ROOT
+
+
+def _run(no_tma: bool):
+    env = dict(os.environ)
+    env.pop("PP_NO_TMA", None)
+    if no_tma:
+        env["PP_NO_TMA"] = "1"
+    r = subprocess.run([sys.executable, "-c", CHILD], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout)
+
+
+@pytest.mark.gpu
+def test_tma_sweeps_match_plain_sweeps():
+    tma = _run(False)
+    plain = _run(True)
+    for key in tma:
+        prec = int(key.split("_")[0])
+        tol = 1e-12 if prec == 0 else 1e-5
+        h_t, v_t = (np.array(x) for x in tma[key])
+        h_p, v_p = (np.array(x) for x in plain[key])
+        assert np.abs(h_t - h_p).max() <= tol * np.abs(h_p).max(), key
+        assert np.abs(v_t - v_p).max() <= tol * max(1.0, np.abs(v_p).max()) * 10, key
