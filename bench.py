@@ -185,7 +185,7 @@ def run_ours(args, ws, rank, local):
     b = inputs.start_vector(n, seed, 0)
     v0 = inputs.start_vector(n, seed, 1)
     stream = torch.cuda.Stream(device=dev)
-    ctx = pp.pp_create(A, stream=stream.cuda_stream)
+    ctx = pp.pp_create(A, stream=stream.cuda_stream, sell_loop=args.sell_loop)
 
     def barrier():
         torch.cuda.synchronize()
@@ -271,7 +271,7 @@ def run_ours(args, ws, rank, local):
                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback"}}
 
     # the same workload with FP32 apply and basis and FP64 refinement on A
-    ctx32 = pp.pp_create(A, stream=stream.cuda_stream, precision=pp.PP_FP32)
+    ctx32 = pp.pp_create(A, stream=stream.cuda_stream, precision=pp.PP_FP32, sell_loop=args.sell_loop)
     def solve32():
         p32 = pp.pp_build_poly(ctx32, cfg["d"], b)
         return pp.pp_eigs(ctx32, p32, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=False)
@@ -289,7 +289,9 @@ def run_ours(args, ws, rank, local):
     m1.record(stream)
     barrier()
     tm = m0.elapsed_time(m1) * 1e-3
+    fmt32 = pp.pp_format_info(ctx32)
     out_mixed = {"value": round(mixed_pairs / tm, 3), "unit": UNIT, "ms_per_step": round(tm / args.steps * 1e3, 3),
+                 "format": fmt32,
                  "precision": "FP32 apply/basis, FP64 residuals and refinement on A",
                  "cycles_per_solve": mixed_cycles, "fp64_cycles": r32.stats["fp64_cycles"], "max_resid": mixed_res,
                  # eigenvalue condition numbers here reach 1e17: the residual bound is the accuracy statement
@@ -302,7 +304,7 @@ def run_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
         "config": {"workload": cfg["name"], "n": n, "nnz": nnz, "d": cfg["d"], "m": cfg["m"], "k": cfg["k"],
                    "nev": cfg["nev"], "rtol": cfg["rtol"],
-                   "format": f"SELL-{fmt['chunk']} ({fmt['index_bits']}-bit columns, tuned)",
+                   "format": f"SELL-{fmt['chunk']} ({fmt['index_bits']}-bit columns, tuned)", "format_info": fmt,
                    "parallelism": f"replicas x{ws}",
                    "l2": "working set (basis 51 x 8 MB + matrix 60 MB) exceeds the 129 MB L2",
                    "cycles_per_solve": cycles, "max_resid": maxres},
@@ -517,14 +519,14 @@ def run_precision3d(args, ws, rank, local):
     v0 = inputs.start_vector(A.n, seed, 1)
     stream = torch.cuda.Stream()
     out = {}
-    for name, prec in (("mixed_fp32", pp.PP_FP32), ("fp64", pp.PP_FP64)):
-        ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, max_cycles=60)
+    for name, prec in (("mixed_fp32", pp.PP_FP32), ("mixed_bf16_basis", pp.PP_FP32_BF16), ("fp64", pp.PP_FP64)):
+        ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, max_cycles=60, sell_loop=args.sell_loop)
 
         def solve():
             poly = pp.pp_build_poly2(ctx, cfg["d1"], cfg["d2"], b)
             return pp.pp_eigs(ctx, poly, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=False)
         steps = max(1, args.steps if name == "mixed_fp32" else 1)
-        for _ in range(max(1, args.warmup if name == "mixed_fp32" else 1)):
+        for _ in range(max(1, args.warmup if name == "mixed_fp32" else 1)):  # the others: one warm-up, one step
             solve()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -540,9 +542,13 @@ def run_precision3d(args, ws, rank, local):
         out[name] = {"value": round(pairs / t, 3), "ms_per_step": round(t / steps * 1e3, 1), "steps": steps,
                      "cycles": res.stats["cycles"], "fp64_cycles": res.stats["fp64_cycles"],
                      "max_resid": float(np.max(res.resid)), "lam": res.lam, "clocks": clk.summary(),
-                     "launches": res.stats["kernel_launches"]}
+                     "launches": res.stats["kernel_launches"], "format": pp.pp_format_info(ctx),
+                     "t_apply_s": round(res.stats["t_apply"], 4), "t_orth_s": round(res.stats["t_orth"], 4),
+                     "t_restart_s": round(res.stats["t_restart"], 4)}
         ctx.close()
     err = _match_errors(out["mixed_fp32"]["lam"], out["fp64"]["lam"])
+    err16 = _match_errors(out["mixed_bf16_basis"]["lam"], out["fp64"]["lam"])
+    out["mixed_bf16_basis"]["rel_err_vs_fp64_per_eigenpair"] = [float("%.3g" % e) for e in err16]
     for v in out.values():
         del v["lam"]
     m = out["mixed_fp32"]
@@ -552,7 +558,7 @@ def run_precision3d(args, ws, rank, local):
             "dtype": "f32 apply/basis, f64 refine", "data": "synthetic (seeded generator)",
             "config": {"workload": cfg["name"], "n": A.n, "nnz": A.nnz, "d1": cfg["d1"], "d2": cfg["d2"],
                        "m": cfg["m"], "k": cfg["k"], "nev": cfg["nev"], "rtol": cfg["rtol"]},
-            "mixed_fp32": m, "fp64": out["fp64"],
+            "mixed_fp32": m, "mixed_bf16_basis": out["mixed_bf16_basis"], "fp64": out["fp64"],
             "rel_err_vs_fp64_per_eigenpair": [float("%.3g" % e) for e in err],
             "gpu_launches": m["launches"], "clocks": m["clocks"]}
 
@@ -592,6 +598,8 @@ def main():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--serve-max-cycles", type=int, default=300)
     ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--sell-loop", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="SELL row loop (pp_opts.sell_loop): 0 tuner, 1 unrolled, 2 wide, 3 staged")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

@@ -49,7 +49,13 @@ typedef enum {
     PP_ENUMERIC = -5    /* NaN/Inf or a singular small dense problem */
 } pp_status;
 
-/* Storage / arithmetic precision of the hot path. */
+/* Storage / arithmetic precision of the hot path.
+ *  PP_FP64:      FP64 matrix values, vectors, basis and arithmetic.
+ *  PP_FP32:      FP32 values, vectors and Arnoldi basis with FP32 accumulation; the
+ *                convergence test, the refinement and (when needed) a continuation run
+ *                in FP64 on A (mixed precision).
+ *  PP_FP32_BF16: as PP_FP32 but the Arnoldi basis is stored in BF16 (widened to FP32
+ *                when read; pp_eigs only, not the batched or served engines). */
 enum { PP_FP64 = 0, PP_FP32 = 1, PP_FP32_BF16 = 2 };
 /* Sparse format on the device: auto (chosen by the tuner), CSR, SELL-C-sigma. */
 enum { PP_FMT_AUTO = 0, PP_FMT_CSR = 1, PP_FMT_SELL = 2 };
@@ -71,7 +77,8 @@ typedef struct {
     int sell_index;     /* SELL column indices: 0 (default) = 16-bit offsets col - row when every
                            |col - row| < 2^15, else 32-bit; 32 = always 32-bit */
     int sell_loop;      /* SELL row loop: 0 (default) = the tuner picks; 1 = unrolled by four;
-                           2 = loads of up to eight entries issued together */
+                           2 = loads of up to eight entries issued together; 3 = slice data staged
+                           in shared memory by bulk copies (SELL-32 only) */
     void *stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
 } pp_opts;
 
@@ -121,8 +128,8 @@ pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);
  * (PP_FMT_CSR or PP_FMT_SELL), the SELL chunk height (0 for CSR), the column
  * index width in bits (16 or 32), the block size of the product kernels, the
  * SELL row loop (0: unrolled by four; 1: the loads of up to eight entries
- * issued together), and the stored entries including SELL padding.  Any
- * output pointer may be NULL.
+ * issued together; 2: slice data staged by bulk copies), and the stored
+ * entries including SELL padding.  Any output pointer may be NULL.
  */
 pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bits, int *threads, int *row_loop,
                          int64_t *stored);

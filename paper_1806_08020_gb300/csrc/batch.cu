@@ -595,6 +595,10 @@ pp_status pp_batch_create(pp_batch **out, int count, const int64_t *n, const int
     b->count = count;
     pp_opts_default(&b->opts);
     if (opts) b->opts = *opts;
+    if (b->opts.precision == PP_FP32_BF16) {
+        delete b;
+        return pp_fail(PP_EINVAL, "pp_batch_create: the batched engine runs PP_FP64 or PP_FP32");
+    }
     if (b->opts.stream) {
         b->stream = (cudaStream_t)b->opts.stream;
     } else {
@@ -684,6 +688,10 @@ pp_status pp_server_create(pp_server **out, const pp_opts *opts, int64_t mem_bud
     auto *s = new pp_server();
     pp_opts_default(&s->opts);
     if (opts) s->opts = *opts;
+    if (s->opts.precision == PP_FP32_BF16) {
+        delete s;
+        return pp_fail(PP_EINVAL, "pp_server_create: the served engine runs PP_FP64 or PP_FP32");
+    }
     if (s->opts.stream) {
         s->stream = (cudaStream_t)s->opts.stream;
     } else {

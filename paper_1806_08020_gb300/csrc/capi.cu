@@ -225,7 +225,7 @@ pp_status ensure_part(pp_ctx *c, size_t doubles) {
 // CGS2 of w against V[:, 0..j) -> V[:, j] normalised, H[0..j, col] on the device.
 pp_status cgs2_step(pp_ctx *c, ppk::Prec pr, void *V, int64_t ldv, int j, void *w, double *hcol) {
     double *h1 = c->d_small, *h2 = c->d_small + 256, *scal = c->d_small + 512, *nrm = c->d_small + 513;
-    const size_t esz = pr == ppk::F64 ? 8 : 4;
+    const size_t esz = pr == ppk::F64 ? 8 : (pr == ppk::F32 ? 4 : 2);
     ppk::CgsArgs a;
     a.n = (int)c->n;
     a.V = V;
@@ -247,17 +247,22 @@ pp_status cgs2_step(pp_ctx *c, ppk::Prec pr, void *V, int64_t ldv, int j, void *
     a.out = h2;
     ppk::launch_cgs(pr, a, c->stream);
     CKS(check_launch(c));
-    // pass 3: w2 = w1 - V h2 -> V[:, j]; H column; 1/||w2||
+    // pass 3: w2 = w1 - V h2 -> V[:, j] (a BF16 basis: into w, then rounded once
+    // when scaled into V[:, j]); H column; 1/||w2||
     a.mode = 2;
     a.h = h2;
     a.h1 = h1;
-    a.wout = (char *)V + (size_t)j * ldv * esz;
+    void *vj = (char *)V + (size_t)j * ldv * esz;
+    a.wout = pr == ppk::BF16 ? w : vj;
     a.out = nrm;
     a.hcol = hcol;
     a.scal = scal;
     ppk::launch_cgs(pr, a, c->stream);
     CKS(check_launch(c));
-    ppk::launch_scale(pr, (int)c->n, (char *)V + (size_t)j * ldv * esz, scal, c->stream);
+    if (pr == ppk::BF16)
+        ppk::launch_scale_bf16((int)c->n, (const float *)w, scal, vj, c->stream);
+    else
+        ppk::launch_scale(pr, (int)c->n, vj, scal, c->stream);
     return check_launch(c);
 }
 
@@ -276,14 +281,21 @@ Timers::~Timers() {
 
 // Extend the Arnoldi decomposition from column j0 to m (Section 4): each step
 // w = Op(v_j), CGS2, v_{j+1}.  H is (m+1) x m column major on the device.
-pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, void *V, int64_t ldv, double *dH,
-                         int ldh, int j0, int m, void *W, Timers *tm, std::vector<std::pair<int, int>> *marks) {
+pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, ppk::Prec bpr, void *V, int64_t ldv,
+                         double *dH, int ldh, int j0, int m, void *W, Timers *tm,
+                         std::vector<std::pair<int, int>> *marks) {
+    const size_t besz = bpr == ppk::F64 ? 8 : (bpr == ppk::F32 ? 4 : 2);
     for (int j = j0; j < m; ++j) {
-        const void *vj = (const char *)V + (size_t)j * ldv * c->esz;
+        const void *vj = (const char *)V + (size_t)j * ldv * besz;
         cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
         if (tm) {
             e0 = tm->get();
             CK(cudaEventRecord(e0, c->stream));
+        }
+        if (bpr == ppk::BF16) {  // the operator reads FP32 vectors
+            ppk::launch_convert(ppk::BF16, ppk::F32, (int)c->n, vj, c->vec[8], c->stream);
+            CKS(check_launch(c));
+            vj = c->vec[8];
         }
         if (tau_of)
             CKS(op_tau(c, tau_of, vj, W));
@@ -293,7 +305,7 @@ pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, voi
             e1 = tm->get();
             CK(cudaEventRecord(e1, c->stream));
         }
-        CKS(cgs2_step(c, c->A.prec, V, ldv, j + 1, W, dH + (size_t)j * ldh));
+        CKS(cgs2_step(c, bpr, V, ldv, j + 1, W, dH + (size_t)j * ldh));
         if (tm) {
             e2 = tm->get();
             CK(cudaEventRecord(e2, c->stream));
@@ -391,7 +403,7 @@ pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, 
         return pp_fail(PP_ECUDA, "build: memset failed");
     }
     if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)c->n) * 130)) < 0 || (st = upload_vec(c, b, 1.0 / beta, V)) < 0 ||
-        (st = arnoldi_extend(c, nullptr, tau_of, V, ldv, dH, d + 1, 0, d, c->vec[6], nullptr,
+        (st = arnoldi_extend(c, nullptr, tau_of, c->A.prec, V, ldv, dH, d + 1, 0, d, c->vec[6], nullptr,
                              nullptr)) < 0) {
         cleanup();
         return st;
@@ -506,6 +518,22 @@ static int64_t sell_padded(int64_t n, const int64_t *rowptr, int cs) {
     return tot;
 }
 
+// Most stored entries of SELL-32 in any g consecutive slices (a staged tile).
+static int64_t tile_cap(int64_t n, const int64_t *rowptr, int g) {
+    int64_t best = 0, cur = 0;
+    const int64_t ns = (n + 31) / 32;
+    for (int64_t s0 = 0; s0 < ns; ++s0) {
+        int64_t w = 0;
+        for (int64_t i = s0 * 32; i < std::min(n, s0 * 32 + 32); ++i) w = std::max(w, rowptr[i + 1] - rowptr[i]);
+        cur += w * 32;
+        if ((s0 + 1) % g == 0 || s0 + 1 == ns) {
+            best = std::max(best, cur);
+            cur = 0;
+        }
+    }
+    return best;
+}
+
 // SELL-C of the device CSR: slice pointers on the host, fill on the device;
 // the allocations are returned in mem (the tuner frees the losers).
 static pp_status build_sell(pp_ctx *c, ppk::Prec pr, int64_t n, const int64_t *rowptr, int cs, bool off16,
@@ -588,7 +616,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     pp_ctx *c = new pp_ctx();
     pp_opts_default(&c->opts);
     if (opts) c->opts = *opts;
-    if (c->opts.precision != PP_FP64 && c->opts.precision != PP_FP32) {
+    if (c->opts.precision != PP_FP64 && c->opts.precision != PP_FP32 && c->opts.precision != PP_FP32_BF16) {
         delete c;
         return pp_fail(PP_EINVAL, "pp_create: precision %d not supported", c->opts.precision);
     }
@@ -629,6 +657,8 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     }
     ppk::Prec pr = c->opts.precision == PP_FP64 ? ppk::F64 : ppk::F32;
     c->esz = pr == ppk::F64 ? 8 : 4;
+    c->bprec = c->opts.precision == PP_FP32_BF16 ? ppk::BF16 : pr;
+    c->besz = c->bprec == ppk::BF16 ? 2 : c->esz;
     pp_status st = PP_OK;
     auto fail = [&](pp_status s) {
         pp_destroy(c);
@@ -654,8 +684,8 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     if (c->opts.sell_sigma > 1) return fail(pp_fail(PP_EINVAL, "pp_create: sell_sigma must be 0 or 1"));
     if (c->opts.sell_index != 0 && c->opts.sell_index != 32)
         return fail(pp_fail(PP_EINVAL, "pp_create: sell_index must be 0 or 32"));
-    if (c->opts.sell_loop < 0 || c->opts.sell_loop > 2)
-        return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop must be 0, 1 or 2"));
+    if (c->opts.sell_loop < 0 || c->opts.sell_loop > 3)
+        return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop must be 0, 1, 2 or 3"));
     std::vector<int> cands;
     if (c->opts.sell_c) cands.push_back(c->opts.sell_c == 16 ? 4 : 5);
     else cands = {5, 4};
@@ -689,21 +719,28 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         ppk::launch_csr_convert(pr, nnz, d_val, v32, c->stream);
         M.csr.val = v32;
     }
-    // scratch vectors (the tuner times products with them)
-    for (int i = 0; i < 8; ++i)
+    // scratch vectors (the tuner times products with them), reduction ticket and
+    // the small FP64 area holding the error word of the staged kernels
+    for (int i = 0; i < 9; ++i)
         if ((st = dmalloc(c, &c->vec[i], (size_t)c->ldv() * c->esz)) < 0) return fail(st);
-    if (cudaMemsetAsync(c->vec[0], 0, (size_t)c->ldv() * c->esz, c->stream) != cudaSuccess)
+    if ((st = dmalloc(c, (void **)&c->d_ticket, 64)) < 0 || (st = dmalloc(c, (void **)&c->d_small, 4096 * 8)) < 0)
+        return fail(st);
+    if (cudaMemsetAsync(c->vec[0], 0, (size_t)c->ldv() * c->esz, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_ticket, 0, 64, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_small, 0, 4096 * 8, c->stream) != cudaSuccess)
         return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
+    M.err = c->err();
     c->stored = nnz;
     if (fmt == PP_FMT_SELL) {
         M.fmt = 2;
         std::vector<int> threads = {256};
         if (!c->opts.sell_c) threads = {128, 256, 512};
-        std::vector<int> loops = {0, 1};
+        // row loops: 0 unrolled, 1 wide, 2 staged by bulk copies (SELL-32 only)
+        std::vector<int> loops = {0, 1, 2};
         if (c->opts.sell_loop) loops = {c->opts.sell_loop - 1};
         const bool tune = cands.size() * threads.size() * loops.size() > 1;
         double best_t = INFINITY;
-        int best_threads = 256, best_wide = 0;
+        int best_threads = 256, best_loop = 0, best_cap = 0;
         ppk::SellView best{};
         std::vector<void *> best_mem;
         for (int cs : cands) {
@@ -712,16 +749,26 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
             if ((st = build_sell(c, pr, n, rowptr, cs, off16, d_rowptr, d_col, d_val, sv, mem)) < 0) return fail(st);
             M.sell = sv;
             bool better = false;
-            for (int wide : loops)
+            for (int loop : loops)
                 for (int t : threads) {
+                    int cap = 0;
+                    if (loop == 2) {  // staged: SELL-32 and two stages within 200 KB of shared memory
+                        if (cs != 5) continue;
+                        cap = (int)tile_cap(n, rowptr, t / 32);
+                        const size_t esz_i = off16 ? 2 : 4;
+                        if (128 + (size_t)cap * (c->esz + esz_i) + 256 > 100 * 1024) continue;
+                    }
                     M.threads = t;
-                    M.wide = wide;
+                    M.wide = loop == 1;
+                    M.tma = loop == 2;
+                    M.tile_cap = cap;
                     double tt = tune ? time_product(c, M) : 0.0;
                     if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
                     if (tt < best_t) {
                         best_t = tt;
                         best_threads = t;
-                        best_wide = wide;
+                        best_loop = loop;
+                        best_cap = cap;
                         better = true;
                     }
                 }
@@ -731,9 +778,12 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
                 best_mem = mem;
             }
         }
+        if (!(best_t < INFINITY) && !tune) return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop 3 needs sell_c 0 or 32"));
         M.sell = best;
         M.threads = best_threads;
-        M.wide = best_wide;
+        M.wide = best_loop == 1;
+        M.tma = best_loop == 2;
+        M.tile_cap = best_cap;
         c->stored = sell_padded(n, rowptr, best.cshift);
     } else {
         M.fmt = 1;
@@ -745,14 +795,9 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     c->A64.fmt = 1;
     c->A64.csr = {(int)n, d_rowptr, d_col, d_val};
     if (pr == ppk::F64) c->A64 = M;
-    if ((st = dmalloc(c, (void **)&c->d_ticket, 64)) < 0 || (st = dmalloc(c, (void **)&c->d_small, 4096 * 8)) < 0)
-        return fail(st);
-    if (cudaMemsetAsync(c->d_ticket, 0, 64, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->d_small, 0, 4096 * 8, c->stream) != cudaSuccess)
-        return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
     if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)n) * 130)) < 0) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: setup kernels failed"));
-    if (pr == ppk::F32 && make_twin) {
+    if (c->bprec != ppk::F64 && make_twin) {
         // FP64 twin on the same stream: the mixed-precision solve continues in FP64
         // when the FP32 cycles cannot resolve the eigenvectors (u_32 kappa ~ 1)
         pp_opts o = c->opts;
@@ -827,7 +872,7 @@ pp_status pp_format_info(const pp_ctx *c, int *fmt, int *chunk, int *index_bits,
     if (chunk) *chunk = sell ? 1 << c->A.sell.cshift : 0;
     if (index_bits) *index_bits = (sell && c->A.sell.off) ? 16 : 32;
     if (threads) *threads = sell ? c->A.threads : 256;
-    if (row_loop) *row_loop = sell ? c->A.wide : 0;
+    if (row_loop) *row_loop = sell ? (c->A.tma ? 2 : c->A.wide) : 0;
     if (stored) *stored = c->stored;
     return PP_OK;
 }

@@ -74,9 +74,11 @@ struct pp_ctx {
     ppk::Matrix A;     // storage precision (shifted operator uses sigma)
     ppk::Matrix A64;   // FP64 copy for residuals on A (same as A in FP64 mode)
     size_t esz = 8;    // bytes per stored vector element
+    ppk::Prec bprec = ppk::F64;  // Arnoldi basis storage (BF16 for PP_FP32_BF16, else as the vectors)
+    size_t besz = 8;             // bytes per basis element
     std::vector<void *> allocs;
-    // scratch
-    void *vec[8] = {};
+    // scratch (vec[8]: FP32 copy of a BF16 basis vector)
+    void *vec[9] = {};
     double *d_part = nullptr;
     size_t part_cap = 0;
     unsigned *d_ticket = nullptr;
@@ -126,8 +128,11 @@ int64_t op_vops(const pp_poly *p);
 int64_t vops_of(const std::vector<StepCoef> &s);
 pp_status ensure_part(pp_ctx *c, size_t doubles);
 pp_status cgs2_step(pp_ctx *c, ppk::Prec pr, void *V, int64_t ldv, int j, void *w, double *hcol);
-pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, void *V, int64_t ldv, double *dH,
-                         int ldh, int j0, int m, void *W, Timers *tm, std::vector<std::pair<int, int>> *marks);
+// Arnoldi steps j0..m-1 on Op with a basis stored in precision bpr (the
+// context's vector precision, or BF16).
+pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, ppk::Prec bpr, void *V, int64_t ldv,
+                         double *dH, int ldh, int j0, int m, void *W, Timers *tm,
+                         std::vector<std::pair<int, int>> *marks);
 void accumulate_times(Timers &tm, std::vector<std::pair<int, int>> &marks, double &t_apply, double &t_orth);
 pp_status upload_vec(pp_ctx *c, const double *h, double s, void *d);
 pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vector<double> &out, ppk::Prec pr);

@@ -29,8 +29,9 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
         return pp_fail(PP_EINVAL, "pp_eigs: need 1 <= nev < k < m < n, m <= 127 and output arrays");
     if (!(rtol > 0)) return pp_fail(PP_EINVAL, "pp_eigs: rtol must be positive");
     const int64_t n = c->n, ldv = c->ldv();
-    const size_t esz = c->esz;
-    const bool mixed = c->A.prec != ppk::F64;
+    const size_t esz = c->besz;  // basis element bytes
+    const ppk::Prec bpr = c->bprec;
+    const bool mixed = bpr != ppk::F64;
     const double target = p ? 1.0 : 0.0;
     pp_stats S{};
     const int64_t launches0 = c->launches, twin0 = c->twin ? c->twin->launches : 0;
@@ -49,7 +50,13 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
     for (double x : v0h) nv += x * x;
     nv = std::sqrt(nv);
     if (!(nv > 0) || !std::isfinite(nv)) return pp_fail(PP_EINVAL, "pp_eigs: start vector is zero or not finite");
-    CKS(upload_vec(c, v0h.data(), 1.0 / nv, V));
+    if (bpr == ppk::BF16) {  // through the FP32 scratch
+        CKS(upload_vec(c, v0h.data(), 1.0 / nv, c->vec[8]));
+        ppk::launch_convert(ppk::F32, ppk::BF16, (int)n, c->vec[8], V, c->stream);
+        CKS(check_launch(c));
+    } else {
+        CKS(upload_vec(c, v0h.data(), 1.0 / nv, V));
+    }
     CK(cudaMemsetAsync(dH, 0, (size_t)ldh * m * 8, c->stream));
     S.dots += 1;
     S.vops += 2;
@@ -65,7 +72,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
     int j0 = 0;
     for (int64_t cycle = 1; cycle <= c->opts.max_cycles; ++cycle) {
         S.cycles = cycle;
-        CKS(arnoldi_extend(c, p, nullptr, V, ldv, dH, ldh, j0, m, W, &tm, &marks));
+        CKS(arnoldi_extend(c, p, nullptr, bpr, V, ldv, dH, ldh, j0, m, W, &tm, &marks));
         S.mvps += opm * (m - j0);
         for (int j = j0; j < m; ++j) {
             S.dots += 2 * (j + 1) + 1;
@@ -77,9 +84,10 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
         CKS(check_sweeps(c));
         accumulate_times(tm, marks, S.t_apply, S.t_orth);
         CKS(wanted_set(H, ldh, m, nev, target, cy));
-        CKS(D.ritz_test(V, c->A.prec, m, cy.Sw, cy.sl, rtol, R, S));
+        CKS(D.ritz_test(V, bpr, m, cy.Sw, cy.sl, rtol, R, S));
         S.nconv = R.nconv;
-        trace_cycle("eigs", c, cycle, mixed ? 32 : 64, R, R.all ? "converged" : nullptr);
+        trace_cycle("eigs", c, cycle, bpr == ppk::F64 ? 64 : (bpr == ppk::F32 ? 32 : 16), R,
+                    R.all ? "converged" : nullptr);
         if (R.all) {
             converged = true;
             S.t_restart += now() - th0;
@@ -131,7 +139,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
         std::vector<double> Q, Hn;
         int kk = restart_basis(cy, H, ldh, k, Q, Hn);
         CK(cudaMemcpyAsync(D.dQ, Q.data(), Q.size() * 8, cudaMemcpyHostToDevice, c->stream));
-        ppk::launch_rotate(c->A.prec, (int)n, V, ldv, m, D.dQ, kk, V2, ldv, c->stream);
+        ppk::launch_rotate(bpr, (int)n, V, ldv, m, D.dQ, kk, V2, ldv, c->stream);
         CKS(check_launch(c));
         CK(cudaMemcpyAsync((char *)V2 + (size_t)kk * ldv * esz, (char *)V + (size_t)m * ldv * esz, n * esz,
                            cudaMemcpyDeviceToDevice, c->stream));

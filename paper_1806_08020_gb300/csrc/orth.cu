@@ -202,17 +202,18 @@ __device__ __forceinline__ void dot2_term(float x, float y, float &s, float &c) 
     c = __fadd_rn(c, __fadd_rn(q, e));
 }
 
-// The sweep over an FP32 basis.  The first projection h1 = V^T w and both
-// updates w - V h run in FP32 (FP32 FMAs are many times faster than FP64 ones
-// on this part); the reorthogonalising projection h2 = V^T w1 uses Dot2, so
-// the second Gram-Schmidt pass is accurate to about twice FP32 precision.
-// Squared norms accumulate in FP64.
-template <int CPW>
+// The sweep over an FP32 or BF16 basis (BF16 elements widened to FP32 on
+// load; w is FP32).  The first projection h1 = V^T w and both updates w - V h
+// run in FP32 (FP32 FMAs are many times faster than FP64 ones on this part);
+// the reorthogonalising projection h2 = V^T w1 uses Dot2, so the second
+// Gram-Schmidt pass is accurate to about twice FP32 precision.  Squared norms
+// accumulate in FP64.
+template <typename TV, int CPW>
 __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
-    const float *V = (const float *)a.V;
+    const TV *V = (const TV *)a.V;
     const float *w = (const float *)a.w;
-    float *wout = (float *)a.wout;
+    float *wout = (float *)a.wout;  // FP32 always (a BF16 basis column is written by the scaling kernel)
     const int j = a.j, n = a.n;
     __shared__ float red[kWarps][kRows];
     __shared__ float wsh[kRows];
@@ -234,7 +235,7 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
                 int row = r0 + lane + 32 * q;
-                vv[cc][q] = (c < j && row < n) ? __ldg(V + (size_t)c * a.ldv + row) : 0.f;
+                vv[cc][q] = (c < j && row < n) ? ld_f32(V + (size_t)c * a.ldv + row) : 0.f;
             }
         }
         if (a.mode == 0) {
@@ -295,7 +296,7 @@ __device__ __forceinline__ void cgs_body(const CgsArgs &a, int bid, int nblk) {
     if constexpr (sizeof(T) == 8)
         cgs_body_f64<CPW>(a, bid, nblk);
     else
-        cgs_body_f32<CPW>(a, bid, nblk);
+        cgs_body_f32<T, CPW>(a, bid, nblk);
 }
 
 template <typename T, int CPW>
@@ -317,41 +318,6 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
 // so the grid reduction completes, and the host reports PP_ETIMEOUT.
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 4;
-constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls; a healthy tile needs a few
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    for (long long it = 0; it < kWaitLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
 
 template <typename T>
 struct CgsArith;
@@ -395,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs_tma(CgsArgs a, int stages, int
         for (int c = tid; c < j; c += kThreads) hs[c] = (Acc)a.h[c];
     if (tid == 0) {
         for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_fence_init();
     }
     __syncthreads();
     // local tile k -> stage k % stages (issued by warp 0)
@@ -570,6 +536,34 @@ __global__ void k_scale(int n, T *x, const double *scal) {
 // arithmetic: FP64 for FP64 bases; FP32 for FP32 bases, whose columns are
 // rounded to FP32 on store anyway (an FP64 FMA costs many FP32 ones here).
 // ---------------------------------------------------------------------------
+template <typename Acc, typename T>
+__device__ __forceinline__ Acc load_acc(const T *p) {
+    return (Acc)__ldg(p);
+}
+template <>
+__device__ __forceinline__ float load_acc<float, __nv_bfloat16>(const __nv_bfloat16 *p) {
+    return ld_f32(p);
+}
+template <>
+__device__ __forceinline__ double load_acc<double, __nv_bfloat16>(const __nv_bfloat16 *p) {
+    return (double)ld_f32(p);
+}
+template <typename TO, typename Acc>
+__device__ __forceinline__ TO store_as(Acc v) {
+    return (TO)v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, float>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+// A BF16 basis column: out = bf16(w * scal) (w is the FP32 orthogonalised vector).
+__global__ void k_scale_bf16(int n, const float *w, const double *scal, __nv_bfloat16 *out) {
+    const float sc = (float)*scal;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(w[i] * sc);
+}
+
 template <typename T, typename TO, typename Acc>
 __global__ void __launch_bounds__(kThreads) k_rotate(int n, const T *V, int64_t ldv, int m, const double *Q,
                                                      int kk, TO *out, int64_t ldo) {
@@ -582,13 +576,13 @@ __global__ void __launch_bounds__(kThreads) k_rotate(int n, const T *V, int64_t 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int row = tile * 32 + lane;
         __syncthreads();
-        for (int r = warp; r < m; r += kWarps) Vs[r * 32 + lane] = row < n ? (Acc)__ldg(V + (size_t)r * ldv + row) : (Acc)0;
+        for (int r = warp; r < m; r += kWarps) Vs[r * 32 + lane] = row < n ? load_acc<Acc>(V + (size_t)r * ldv + row) : (Acc)0;
         __syncthreads();
         for (int c = warp; c < kk; c += kWarps) {
             Acc acc = 0;
             const Acc *qc = Qs + (size_t)c * m;
             for (int r = 0; r < m; ++r) acc = fma(Vs[r * 32 + lane], qc[r], acc);
-            if (row < n) out[(size_t)c * ldo + row] = (TO)acc;
+            if (row < n) out[(size_t)c * ldo + row] = store_as<TO>(acc);
         }
     }
 }
@@ -690,10 +684,12 @@ static int resident_grid(int n, int cap) {
 
 // TMA-staged sweeps need 16-byte aligned column starts and w, a context's
 // error word, and at least one full tile; PP_NO_TMA in the environment turns
-// them off (the plain sweeps compute the same values).
+// them off (the plain sweeps compute the same values).  FP64 bases keep the
+// plain sweeps: they are bound by FP64 arithmetic, which staging does not
+// relieve, and the staged form measured slower there (block barriers).
 static bool tma_usable(const CgsArgs &a, size_t esz) {
     static const bool off = std::getenv("PP_NO_TMA") != nullptr;
-    return !off && a.err && a.n >= kRows && ((uintptr_t)a.V % 16) == 0 && ((uintptr_t)a.w % 16) == 0 &&
+    return !off && esz == 4 && a.err && a.n >= kRows && ((uintptr_t)a.V % 16) == 0 && ((uintptr_t)a.w % 16) == 0 &&
            (a.ldv * (int64_t)esz) % 16 == 0 && a.j >= 1 && a.j <= 128;
 }
 
@@ -721,7 +717,8 @@ static void cgs_tma_launch(const CgsArgs &a, int cap, cudaStream_t st) {
 
 template <typename T>
 static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
-    if (tma_usable(a, sizeof(T))) {
+    if constexpr (sizeof(T) == 4) {
+        if (tma_usable(a, sizeof(T))) {
         int cpw = (a.j + kWarps - 1) / kWarps;
         if (cpw <= 2)
             cgs_tma_launch<T, 2>(a, cap, st);
@@ -732,6 +729,7 @@ static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
         else
             cgs_tma_launch<T, 16>(a, cap, st);
         return;
+        }
     }
     int cpw = (a.j + kWarps - 1) / kWarps;
     if (cpw <= 2)
@@ -747,8 +745,14 @@ static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
 void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st) {
     if (p == F64)
         cgs_dispatch<double>(a, 0, st);
-    else
+    else if (p == F32)
         cgs_dispatch<float>(a, 0, st);
+    else
+        cgs_dispatch<__nv_bfloat16>(a, 0, st);
+}
+
+void launch_scale_bf16(int n, const float *w, const double *scal, void *out, cudaStream_t st) {
+    k_scale_bf16<<<num_sms() * 4, kThreads, 0, st>>>(n, w, scal, (__nv_bfloat16 *)out);
 }
 
 void launch_cgs_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int mode,
@@ -781,8 +785,10 @@ int cgs_batch_blocks(int n) {
 void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st) {
     if (p == F64)
         cgs_dispatch<double>(a, grid_cap, st);
-    else
+    else if (p == F32)
         cgs_dispatch<float>(a, grid_cap, st);
+    else
+        cgs_dispatch<__nv_bfloat16>(a, grid_cap, st);
 }
 
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st) {
@@ -804,10 +810,14 @@ void launch_rotate(Prec p, int n, const void *V, int64_t ldv, int m, const doubl
         cudaFuncSetAttribute(k_rotate<double, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rotate<double, double, double><<<g, kThreads, smem, st>>>(n, (const double *)V, ldv, m, Q, kk,
                                                                     (double *)out, ldo);
-    } else {
+    } else if (p == F32) {
         cudaFuncSetAttribute(k_rotate<float, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rotate<float, float, float><<<g, kThreads, smem, st>>>(n, (const float *)V, ldv, m, Q, kk, (float *)out,
                                                                  ldo);
+    } else {
+        using B = __nv_bfloat16;
+        cudaFuncSetAttribute(k_rotate<B, B, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rotate<B, B, float><<<g, kThreads, smem, st>>>(n, (const B *)V, ldv, m, Q, kk, (B *)out, ldo);
     }
 }
 
@@ -819,9 +829,13 @@ void launch_rotate64(Prec p, int n, const void *V, int64_t ldv, int m, const dou
     if (tiles < g) g = tiles;
     if (p == F64) {
         launch_rotate(p, n, V, ldv, m, Q, kk, out, ldo, st);
-    } else {
+    } else if (p == F32) {
         cudaFuncSetAttribute(k_rotate<float, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_rotate<float, double, double><<<g, kThreads, smem, st>>>(n, (const float *)V, ldv, m, Q, kk, out, ldo);
+    } else {
+        using B = __nv_bfloat16;
+        cudaFuncSetAttribute(k_rotate<B, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_rotate<B, double, double><<<g, kThreads, smem, st>>>(n, (const B *)V, ldv, m, Q, kk, out, ldo);
     }
 }
 

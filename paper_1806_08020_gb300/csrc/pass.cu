@@ -155,6 +155,116 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass(SellView S, CsrView R,
     }
 }
 
+// The fused pass with the slice data staged by the bulk-copy (TMA) engine.
+// A tile is G = blockDim/32 consecutive SELL-32 slices (one warp per slice);
+// its values and column indices are contiguous, so per tile one thread issues
+// two bulk copies into a pipeline stage (with the tile's slice offsets in a
+// small header) and arms the stage's mbarrier with their bytes.  Each block
+// walks its tiles bid, bid + nblk, ... with up to `stages` tiles in flight;
+// only the x gathers and the epilogue's row reads stay direct loads, so a
+// row waits for one memory round trip instead of three (slice pointer,
+// index, x).  A warp releases a stage through the stage's "empty" mbarrier;
+// thread 0 refills it once all warps have.  Every wait is bounded: on expiry
+// the thread records it in *err and leaves (the issuing thread first drains
+// its copies), and the next host synchronisation reports PP_ETIMEOUT.  The
+// row sums run in the entry order of the other formats, so the results are
+// bit-identical to theirs.
+constexpr int kTmaMaxSlices = kPassMaxThreads / 32;
+constexpr int kTmaMaxStages = 4;
+constexpr int kTmaHeader = 128;  // bytes: slice offsets of the tile (<= 17 ints)
+
+template <typename T, typename I, int KIND, bool SIGMA>
+__global__ void __launch_bounds__(kPassMaxThreads) k_pass_tma(SellView A, StepArgs s, int stages,
+                                                              unsigned stage_bytes, unsigned idx_at, int *err) {
+    extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ unsigned long long full[kTmaMaxStages], empty[kTmaMaxStages];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = blockDim.x >> 5;
+    const int ntiles = (A.nslices + G - 1) / G;
+    const int bid = blockIdx.x, nblk = gridDim.x;
+    const int mine = bid < ntiles ? (ntiles - 1 - bid) / nblk + 1 : 0;
+    const T *val = (const T *)A.val;
+    const I *idx = (const I *)(sizeof(I) == 2 ? (const void *)A.off : (const void *)A.col);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < stages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], G);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // thread 0: stage local tile k (its slice offsets, values and indices)
+    auto issue = [&](int k) {
+        const int st = k % stages;
+        unsigned char *stage = tsm + (size_t)st * stage_bytes;
+        const int s0 = (bid + k * nblk) * G, s1 = min(s0 + G, A.nslices);
+        const int beg = __ldg(A.slice_ptr + s0), end = __ldg(A.slice_ptr + s1);
+        int *hdr = (int *)stage;
+        for (int q = 0; q <= s1 - s0; ++q) hdr[q] = __ldg(A.slice_ptr + s0 + q) - beg;
+        const unsigned ne = (unsigned)(end - beg);
+        mbar_arrive_expect(&full[st], ne * (unsigned)(sizeof(T) + sizeof(I)));
+        if (ne) {
+            bulk_copy_g2s(stage + kTmaHeader, val + beg, ne * (unsigned)sizeof(T), &full[st]);
+            bulk_copy_g2s(stage + idx_at, idx + beg, ne * (unsigned)sizeof(I), &full[st]);
+        }
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < stages && k < mine; ++k) issue(k);
+    const T *x = (const T *)s.x;
+    T *y = (T *)s.y;
+    for (int k = 0; k < mine; ++k) {
+        const int st = k % stages;
+        const unsigned par = (unsigned)(k / stages) & 1u;
+        if (!mbar_wait_bounded(&full[st], par)) {
+            atomicExch(err, 1);
+            if (threadIdx.x == 0)  // drain this block's copies still in flight
+                for (int kk = k; kk < mine && kk < k + stages; ++kk)
+                    mbar_wait_bounded(&full[kk % stages], (unsigned)(kk / stages) & 1u);
+            return;
+        }
+        const unsigned char *stage = tsm + (size_t)st * stage_bytes;
+        const int *hdr = (const int *)stage;
+        const int s0 = (bid + k * nblk) * G;
+        const int sl = s0 + warp;
+        const int row = sl * 32 + lane;
+        if (sl < A.nslices && row < A.n) {
+            const int rb = hdr[warp], len = (hdr[warp + 1] - rb) >> 5;
+            const T *vs = (const T *)(stage + kTmaHeader) + rb + lane;
+            const I *is = (const I *)(stage + idx_at) + rb + lane;
+            T u = 0;
+            if (sizeof(I) == 2) {
+                const T *xr = x + row;
+#pragma unroll 4
+                for (int q = 0; q < len; ++q) u = fma(vs[32 * q], __ldg(xr + (int)is[32 * q]), u);
+            } else {
+#pragma unroll 4
+                for (int q = 0; q < len; ++q) u = fma(vs[32 * q], __ldg(x + (int)is[32 * q]), u);
+            }
+            if (SIGMA) u = fma(-(T)s.sigma, x[row], u);
+            if (KIND == 0) {
+                y[row] = u;
+            } else if (KIND == 1) {
+                y[row] = fma(-(T)s.a2, u, x[row]);
+            } else {
+                T v = fma(-(T)s.a1, x[row], ((const T *)s.aux)[row]);
+                y[row] = fma(-(T)s.a2, u, v);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        if (threadIdx.x == 0 && k + stages < mine) {
+            // refill this stage once every warp has released it
+            if (!mbar_wait_bounded(&empty[st], par)) {
+                atomicExch(err, 1);
+                for (int kk = k + 1; kk < mine && kk < k + stages; ++kk)
+                    mbar_wait_bounded(&full[kk % stages], (unsigned)(kk / stages) & 1u);
+                return;
+            }
+            issue(k + stages);
+        }
+    }
+}
+
 // General pass (running sum, optional output, outer epilogue): see StepArgs.
 template <typename T, typename V, typename Acc, int FMT>
 __global__ void __launch_bounds__(kPassMaxThreads) k_step(SellView S, CsrView R, StepArgs s) {
@@ -222,6 +332,14 @@ __global__ void k_convert_vals(int64_t nnz, const double *val, V *out) {
         out[i] = (V)val[i];
 }
 
+__global__ void k_bf16_to_f32(int n, const __nv_bfloat16 *x, float *y) {
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) y[i] = ld_f32(x + i);
+}
+
+__global__ void k_f32_to_bf16(int n, const float *x, __nv_bfloat16 *y) {
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) y[i] = __float2bfloat16_rn(x[i]);
+}
+
 template <typename A, typename B>
 __global__ void k_convert(int n, const A *x, B *y) {
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) y[i] = (B)x[i];
@@ -254,8 +372,53 @@ static void pass_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
 #undef PP_PASS
 }
 
+template <typename T, typename I, int KIND, bool SIGMA>
+static void tma_pass_launch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    static int attr = 0;  // one per instantiation
+    if (!attr) {
+        cudaFuncSetAttribute(k_pass_tma<T, I, KIND, SIGMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = 1;
+    }
+    const unsigned vbytes = (unsigned)(((size_t)A.tile_cap * sizeof(T) + 127) / 128 * 128);
+    const unsigned ibytes = (unsigned)(((size_t)A.tile_cap * sizeof(I) + 127) / 128 * 128);
+    const unsigned idx_at = kTmaHeader + vbytes, stage = idx_at + ibytes;
+    int stages = (int)((64u * 1024u) / stage);
+    stages = stages < 2 ? 2 : (stages > kTmaMaxStages ? kTmaMaxStages : stages);
+    const size_t smem = (size_t)stages * stage;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_tma<T, I, KIND, SIGMA>, A.threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int G = A.threads / 32;
+    const int ntiles = (A.sell.nslices + G - 1) / G;
+    int grid = per_sm * num_sms();
+    if (grid > ntiles) grid = ntiles;
+    k_pass_tma<T, I, KIND, SIGMA><<<grid, A.threads, smem, st>>>(A.sell, s, stages, stage, idx_at, A.err);
+}
+
+template <typename T, typename I>
+static bool tma_pass_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    const bool general = s.r || s.oy || !s.y;
+    if (general || (!s.plain && !s.aux && s.a1 != 0.0)) return false;
+    const bool sig = s.sigma != 0.0;
+    const int kind = s.plain ? 0 : (s.aux ? 2 : 1);
+#define PP_TPASS(K, S) tma_pass_launch<T, I, K, S>(A, s, st)
+    if (kind == 0) {
+        if (sig) PP_TPASS(0, true); else PP_TPASS(0, false);
+    } else if (kind == 1) {
+        if (sig) PP_TPASS(1, true); else PP_TPASS(1, false);
+    } else {
+        if (sig) PP_TPASS(2, true); else PP_TPASS(2, false);
+    }
+#undef PP_TPASS
+    return true;
+}
+
 template <typename T>
 static void pass_format(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    if (A.fmt == 2 && A.tma && A.err) {
+        const bool done = A.sell.off ? tma_pass_dispatch<T, short>(A, s, st) : tma_pass_dispatch<T, int>(A, s, st);
+        if (done) return;
+    }
     if (A.fmt != 2)
         pass_dispatch<T, 0>(A, s, st);
     else if (A.sell.off)
@@ -302,7 +465,11 @@ void launch_csr_convert(Prec p, int64_t nnz, const double *val, void *out, cudaS
 
 void launch_convert(Prec from, Prec to, int n, const void *x, void *y, cudaStream_t st) {
     int g = num_sms() * 4;
-    if (from == F64 && to == F32)
+    if (from == BF16 && to == F32)
+        k_bf16_to_f32<<<g, kThreads, 0, st>>>(n, (const __nv_bfloat16 *)x, (float *)y);
+    else if (from == F32 && to == BF16)
+        k_f32_to_bf16<<<g, kThreads, 0, st>>>(n, (const float *)x, (__nv_bfloat16 *)y);
+    else if (from == F64 && to == F32)
         k_convert<double, float><<<g, kThreads, 0, st>>>(n, (const double *)x, (float *)y);
     else if (from == F32 && to == F64)
         k_convert<float, double><<<g, kThreads, 0, st>>>(n, (const float *)x, (double *)y);

@@ -31,8 +31,8 @@ typedef struct CUstream_st *cudaStream_t;
 
 namespace ppk {
 
-// Storage precisions of device vectors / matrix values.
-enum Prec { F64 = 0, F32 = 1 };
+// Storage precisions of device vectors / matrix values (BF16: basis only).
+enum Prec { F64 = 0, F32 = 1, BF16 = 2 };
 
 // SELL-C matrix (sigma = 1: rows keep their order) with chunk height
 // C = 1 << cshift (16 or 32): slice s holds rows [C s, C s + C); its entries
@@ -83,6 +83,9 @@ struct Matrix {
     int fmt = 2;  // 1 CSR, 2 SELL
     int threads = 256;  // block size of the SELL pass kernels (64..512, chosen by the tuner)
     int wide = 0;       // SELL row loop: 0 unrolled by four, 1 chunks of eight loads (tuner)
+    int tma = 0;        // SELL-32 slice data staged by bulk copies (tuner); needs tile_cap and err
+    int tile_cap = 0;   // most stored entries in threads/32 consecutive slices
+    int *err = nullptr; // the context's error word (bounded waits of the staged kernels)
     Prec prec = F64;
     SellView sell{};
     CsrView csr{};
@@ -117,6 +120,8 @@ void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st);
 // as launch_cgs with at most grid_cap blocks (the partial sums need grid_cap * (j+1) doubles)
 void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st);
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st);
+// out (BF16, n) = w * scal (w FP32): the new column of a BF16 basis
+void launch_scale_bf16(int n, const float *w, const double *scal, void *out, cudaStream_t st);
 
 // Batched Arnoldi steps (many instances advance together, one launch per pass).
 // Per-instance CGS2 state: the basis V (ldv), the operator output W, the

@@ -205,8 +205,9 @@ def _wide_band_matrix():
 @pytest.mark.parametrize("precision", [0, 1])
 def test_sell_formats_bit_identical(kind, precision):
     """Every device format gives the same pi(A) x bit for bit: CSR, SELL with
-    chunk height 16 or 32, 16- or 32-bit column indices, either row loop, and
-    whatever chunk height, block size and row loop the tuner picks.  Each row sums its entries in CSR
+    chunk height 16 or 32, 16- or 32-bit column indices, any row loop (plain,
+    wide, or slice data staged by bulk copies), and whatever chunk height,
+    block size and row loop the tuner picks.  Each row sums its entries in CSR
     order in every format (SELL padding adds 0 * x = 0 exactly)."""
     from paper_1806_08020_gb300 import pp
     A = {"cd": lambda: inputs.convection_diffusion_2d(150, 50.0),
@@ -220,6 +221,8 @@ def test_sell_formats_bit_identical(kind, precision):
                 "c32_i32": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=1),
                 "c16_wide": dict(format=pp.PP_FMT_SELL, sell_c=16, sell_loop=2),
                 "c32_i32_wide": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=2),
+                "c32_staged": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_loop=3),
+                "c32_i32_staged": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=3),
                 "tuned": dict(format=pp.PP_FMT_SELL)}
     out, info = {}, {}
     for name, o in variants.items():
@@ -232,5 +235,6 @@ def test_sell_formats_bit_identical(kind, precision):
     assert info["c32"]["index_bits"] == (32 if kind == "wide" else 16)
     assert info["tuned"]["chunk"] in (16, 32) and info["tuned"]["threads"] in (128, 256, 512)
     assert info["c16_wide"]["row_loop"] == 1 and info["c32"]["row_loop"] == 0
+    assert info["c32_staged"]["row_loop"] == 2 and info["c32_i32_staged"]["index_bits"] == 32
     for name in variants:
         assert np.array_equal(out[name], out["csr"]), name

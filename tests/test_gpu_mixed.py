@@ -54,8 +54,11 @@ def test_fp32_apply_matches_oracle(case):
     assert np.abs(y - ref).max() <= _bound32(A, sigma, P.roots, x)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
 @pytest.mark.parametrize("case", ["single", "double", "banded"])
-def test_mixed_eigs_match_fp64_oracle(case):
+def test_mixed_eigs_match_fp64_oracle(case, precision):
+    """FP32 or BF16 basis (FP32 apply), FP64 test, refinement and continuation:
+    converged pairs meet the FP64 residual bound and match the oracle's."""
     from paper_1806_08020_gb300 import pp
     if case == "single":
         Acsr, d, d2, nev, m, k = inputs.convection_diffusion_2d(60, 20.0), 10, None, 8, 30, 13
@@ -64,7 +67,7 @@ def test_mixed_eigs_match_fp64_oracle(case):
     else:
         Acsr, d, d2, nev, m, k = inputs.banded_random(2000, 4, 2), 5, None, 6, 30, 11
     A, P, R = oracle_solve(Acsr, d, nev, m, k, 41, d2=d2)
-    ctx = pp.pp_create(Acsr, precision=pp.PP_FP32)
+    ctx = pp.pp_create(Acsr, precision=pp.PP_FP32 if precision == "fp32" else pp.PP_FP32_BF16)
     b = inputs.start_vector(Acsr.n, 41, 0)
     v0 = inputs.start_vector(Acsr.n, 41, 1)
     poly = pp.pp_build_poly2(ctx, d, d2, b) if d2 else pp.pp_build_poly(ctx, d, b)
@@ -81,3 +84,12 @@ def test_mixed_eigs_match_fp64_oracle(case):
         kj = kap[np.argmin(np.abs(w - lam))]
         bound = 10 * kj * (res.resid[i] + R.resid[j]) * nA
         assert dist[i] <= bound + 1e-12 * abs(lam), (j, lam, res.lam[i], bound)
+
+
+def test_bf16_basis_rejected_by_batched_engines():
+    from paper_1806_08020_gb300 import pp
+    A = inputs.convection_diffusion_2d(20, 5.0)
+    with pytest.raises(pp.PPError):
+        pp.pp_batch_create([A], precision=pp.PP_FP32_BF16)
+    with pytest.raises(pp.PPError):
+        pp.pp_server_create(precision=pp.PP_FP32_BF16)
