@@ -78,7 +78,7 @@ typedef struct {
                            |col - row| < 2^15, else 32-bit; 32 = always 32-bit */
     int sell_loop;      /* SELL row loop: 0 (default) = the tuner picks; 1 = unrolled by four;
                            2 = loads of up to eight entries issued together; 3 = slice data staged
-                           in shared memory by bulk copies (SELL-32 only) */
+                           in shared memory by bulk copies (SELL-32 only); 4 = two rows per thread */
     void *stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
 } pp_opts;
 
@@ -117,6 +117,16 @@ pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_
                     const double *vals, const pp_opts *opts);
 void pp_destroy(pp_ctx *ctx);
 
+/*
+ * pp_debug_stall_sweeps — test support for the failure path of the staged
+ * CGS2 sweeps: the next `count` CGS2 steps on this context issue no bulk
+ * copies, so every wait for a staged tile runs out its bounded limit; the
+ * next host synchronisation of the call returns PP_ETIMEOUT and the context
+ * stays usable.  Applies to FP32 contexts whose sweeps are staged (a step
+ * that takes the plain sweeps is unaffected).  Not for production use.
+ */
+pp_status pp_debug_stall_sweeps(pp_ctx *ctx, int count);
+
 /* Number of library kernels launched on this context since pp_create. */
 int64_t pp_launch_count(const pp_ctx *ctx);
 
@@ -128,8 +138,9 @@ pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);
  * (PP_FMT_CSR or PP_FMT_SELL), the SELL chunk height (0 for CSR), the column
  * index width in bits (16 or 32), the block size of the product kernels, the
  * SELL row loop (0: unrolled by four; 1: the loads of up to eight entries
- * issued together; 2: slice data staged by bulk copies), and the stored
- * entries including SELL padding.  Any output pointer may be NULL.
+ * issued together; 2: slice data staged by bulk copies; 3: two rows per
+ * thread), and the stored entries including SELL padding.  Any output
+ * pointer may be NULL.
  */
 pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bits, int *threads, int *row_loop,
                          int64_t *stored);

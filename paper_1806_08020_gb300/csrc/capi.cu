@@ -234,6 +234,10 @@ pp_status cgs2_step(pp_ctx *c, ppk::Prec pr, void *V, int64_t ldv, int j, void *
     a.part = c->d_part;
     a.ticket = c->d_ticket;
     a.err = c->err();
+    if (c->stall_sweeps > 0) {
+        a.stall = 1;
+        c->stall_sweeps--;
+    }
     // pass 1: h1 = V^T w
     a.mode = 0;
     a.w = w;
@@ -570,35 +574,51 @@ static pp_status build_sell(pp_ctx *c, ppk::Prec pr, int64_t n, const int64_t *r
     return PP_OK;
 }
 
-// Seconds per product y = A x with this format and block size: the fastest of
-// five launches after two warm-up ones, CUDA events on the context's stream.
+// Tuner cost of a format: the time of a specialised root pass (y = x - A x/theta,
+// the single polynomial's pass) plus a general pass with the running sum (the
+// double polynomial's inner pass), each the fastest of eight launches after
+// two warm-up ones, CUDA events on the context's stream.  Negative on a
+// launch error.
 static double time_product(pp_ctx *c, const ppk::Matrix &M) {
-    ppk::StepArgs a;
+    ppk::StepArgs a, g;
     a.x = c->vec[0];
     a.y = c->vec[1];
-    a.plain = 1;
+    a.a2 = 1e-3;
+    g.x = c->vec[0];
+    g.y = c->vec[2];
+    g.r = c->vec[3];
+    g.r_init = 1;
+    g.a2 = 1e-3;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return -1;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return -1;
     }
-    double best = INFINITY;
-    for (int it = 0; it < 7; ++it) {
-        cudaEventRecord(e0, c->stream);
-        ppk::launch_step(M, a, c->stream);
-        cudaEventRecord(e1, c->stream);
-        float ms = 0;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            best = -1;
+    double total = 0;
+    for (const ppk::StepArgs *s : {&a, &g}) {
+        double best = INFINITY;
+        for (int it = 0; it < 10; ++it) {
+            cudaEventRecord(e0, c->stream);
+            ppk::launch_step(M, *s, c->stream);
+            cudaEventRecord(e1, c->stream);
+            float ms = 0;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                best = -1;
+                break;
+            }
+            if (it >= 2) best = std::min(best, (double)ms * 1e-3);
+        }
+        if (best < 0) {
+            total = -1;
             break;
         }
-        if (it >= 2) best = std::min(best, (double)ms * 1e-3);
+        total += best;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) return -1;
-    return best;
+    return total;
 }
 
 pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind,
@@ -684,8 +704,8 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     if (c->opts.sell_sigma > 1) return fail(pp_fail(PP_EINVAL, "pp_create: sell_sigma must be 0 or 1"));
     if (c->opts.sell_index != 0 && c->opts.sell_index != 32)
         return fail(pp_fail(PP_EINVAL, "pp_create: sell_index must be 0 or 32"));
-    if (c->opts.sell_loop < 0 || c->opts.sell_loop > 3)
-        return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop must be 0, 1, 2 or 3"));
+    if (c->opts.sell_loop < 0 || c->opts.sell_loop > 4)
+        return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop must be 0 to 4"));
     std::vector<int> cands;
     if (c->opts.sell_c) cands.push_back(c->opts.sell_c == 16 ? 4 : 5);
     else cands = {5, 4};
@@ -726,6 +746,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     if ((st = dmalloc(c, (void **)&c->d_ticket, 64)) < 0 || (st = dmalloc(c, (void **)&c->d_small, 4096 * 8)) < 0)
         return fail(st);
     if (cudaMemsetAsync(c->vec[0], 0, (size_t)c->ldv() * c->esz, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->vec[3], 0, (size_t)c->ldv() * c->esz, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->d_ticket, 0, 64, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->d_small, 0, 4096 * 8, c->stream) != cudaSuccess)
         return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
@@ -735,8 +756,8 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         M.fmt = 2;
         std::vector<int> threads = {256};
         if (!c->opts.sell_c) threads = {128, 256, 512};
-        // row loops: 0 unrolled, 1 wide, 2 staged by bulk copies (SELL-32 only)
-        std::vector<int> loops = {0, 1, 2};
+        // row loops: 0 unrolled, 1 wide, 2 staged by bulk copies (SELL-32 only), 3 two rows per thread
+        std::vector<int> loops = {0, 1, 2, 3};
         if (c->opts.sell_loop) loops = {c->opts.sell_loop - 1};
         const bool tune = cands.size() * threads.size() * loops.size() > 1;
         double best_t = INFINITY;
@@ -759,7 +780,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
                         if (128 + (size_t)cap * (c->esz + esz_i) + 256 > 100 * 1024) continue;
                     }
                     M.threads = t;
-                    M.wide = loop == 1;
+                    M.wide = loop == 1 ? 1 : (loop == 3 ? 2 : 0);
                     M.tma = loop == 2;
                     M.tile_cap = cap;
                     double tt = tune ? time_product(c, M) : 0.0;
@@ -781,7 +802,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         if (!(best_t < INFINITY) && !tune) return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop 3 needs sell_c 0 or 32"));
         M.sell = best;
         M.threads = best_threads;
-        M.wide = best_loop == 1;
+        M.wide = best_loop == 1 ? 1 : (best_loop == 3 ? 2 : 0);
         M.tma = best_loop == 2;
         M.tile_cap = best_cap;
         c->stored = sell_padded(n, rowptr, best.cshift);
@@ -830,6 +851,10 @@ pp_status pp_orthogonalize(pp_ctx *c, const void *V, int64_t ldv, int j, void *w
     a.part = c->d_part;
     a.ticket = c->d_ticket;
     a.err = c->err();
+    if (c->stall_sweeps > 0) {
+        a.stall = 1;
+        c->stall_sweeps--;
+    }
     a.mode = 0;
     a.w = w;
     a.out = h1;
@@ -864,6 +889,12 @@ pp_status pp_matrix_info(const pp_ctx *c, double *norm1, double *sigma) {
     return PP_OK;
 }
 
+pp_status pp_debug_stall_sweeps(pp_ctx *c, int count) {
+    if (!c || count < 0) return pp_fail(PP_EINVAL, "pp_debug_stall_sweeps: bad arguments");
+    c->stall_sweeps = count;
+    return PP_OK;
+}
+
 pp_status pp_format_info(const pp_ctx *c, int *fmt, int *chunk, int *index_bits, int *threads, int *row_loop,
                          int64_t *stored) {
     if (!c) return pp_fail(PP_EINVAL, "pp_format_info: null context");
@@ -872,7 +903,7 @@ pp_status pp_format_info(const pp_ctx *c, int *fmt, int *chunk, int *index_bits,
     if (chunk) *chunk = sell ? 1 << c->A.sell.cshift : 0;
     if (index_bits) *index_bits = (sell && c->A.sell.off) ? 16 : 32;
     if (threads) *threads = sell ? c->A.threads : 256;
-    if (row_loop) *row_loop = sell ? (c->A.tma ? 2 : c->A.wide) : 0;
+    if (row_loop) *row_loop = sell ? (c->A.tma ? 2 : (c->A.wide == 2 ? 3 : c->A.wide)) : 0;
     if (stored) *stored = c->stored;
     return PP_OK;
 }

@@ -86,6 +86,7 @@ struct pp_ctx {
     int64_t launches = 0;
     pp_ctx *twin = nullptr;  // FP64 copy of an FP32 context (mixed-precision fallback)
     int64_t stored = 0;      // matrix entries held on the device (with SELL padding)
+    int stall_sweeps = 0;    // test hook: staged CGS2 sweeps left to run without copies
     int64_t ldv() const { return (n + 31) / 32 * 32; }
     // device error word of the TMA-staged sweeps (set when a bounded wait expired)
     int *err() const { return (int *)(d_small + 4000); }

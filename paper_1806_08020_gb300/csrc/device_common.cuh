@@ -27,9 +27,10 @@ inline int num_sms() {
 
 // ---------------------------------------------------------------------------
 // Bulk-copy (TMA) staging: mbarrier and cp.async.bulk wrappers (inline PTX).
-// Every wait is bounded by kWaitLimit polls; callers treat expiry as an error.
+// Every wait is bounded (one second, and kWaitLimit polls); callers treat expiry as an error.
 // ---------------------------------------------------------------------------
-constexpr long long kWaitLimit = 1LL << 22;  // try_wait polls; a healthy stage needs a few
+constexpr long long kWaitLimit = 1LL << 26;        // try_wait polls (backstop)
+constexpr unsigned long long kWaitNs = 1000000000ULL;  // and at most one second of waiting
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -67,9 +68,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with this parity; false after one second (or kWaitLimit polls).
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    for (long long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 1; it < kWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 

@@ -158,9 +158,10 @@ struct Driver {
 
     // FP64 refinement on A (mixed precision): Rayleigh-Ritz of A itself on a
     // search space built in FP64 from the wanted Ritz vectors Y.  With an FP64
-    // copy of the operator the space is span{pi(A) Y}: the polynomial keeps
-    // the wanted part of Y and damps the FP32 rounding noise in the unwanted
-    // part of the spectrum (one step of subspace iteration on pi(A)).  Without
+    // copy of the operator the space is span{pi(A) Y} (pi_1(A) Y for a double
+    // polynomial): the polynomial keeps the wanted part of Y and damps the FP32
+    // rounding noise in the unwanted part of the spectrum (one step of subspace
+    // iteration).  Without
     // one it is the block Krylov space span{Y, A Y, ..., A^s Y}.  The Ritz
     // pairs nearest the current estimates replace them, for up to `rounds`
     // rounds; a round that does not lower the largest residual is undone and
@@ -172,6 +173,10 @@ struct Driver {
         if (!dG) CKS(alloc((void **)&dG, (size_t)(kZcap + 1) * kZcap * 8));
         if (!Yb) CKS(alloc((void **)&Yb, (size_t)ldv * (wcap + 1) * 8));
         pp_ctx *tw = (p && c->twin) ? c->twin : nullptr;
+        // the filter: pi itself, or for a double polynomial its inner factor pi_1
+        // (degree d1 instead of d1 d2: it damps the same unwanted part, less
+        // sharply, at a d2-th of the FP64 passes)
+        const pp_poly *pf = (p && p->inner) ? p->inner : p;
         steps = std::max(1, std::min(steps, kZcap / (nev + 1) - 1));
         const int ldg = kZcap + 1;
         double *W = AY64 + (size_t)(nev + 1) * ldv;  // spare FP64 column (context vectors are FP32 here)
@@ -211,13 +216,13 @@ struct Driver {
             CK(cudaMemsetAsync(dG, 0, (size_t)ldg * kZcap * 8, c->stream));
             if (tw) {
                 for (int s = 0; s < nw; ++s) {
-                    CKS(op_apply(tw, p, Y64 + (size_t)s * ldv, W));
+                    CKS(op_apply(tw, pf, Y64 + (size_t)s * ldv, W));
                     CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, c->d_small + 2048));
                     S.dots += 2 * nz + 1;
                     S.vops += 4 * nz + 2;
                     nz++;
                 }
-                S.mvps += op_mvps(p) * nw;
+                S.mvps += op_mvps(pf) * nw;
                 for (int col = 0; col < nz; ++col) CKS(project(col, nz));
             } else {
                 for (int s = 0; s < nw; ++s) {

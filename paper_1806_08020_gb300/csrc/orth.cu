@@ -421,12 +421,13 @@ __global__ void __launch_bounds__(kThreads) k_cgs_tma(CgsArgs a, int stages, int
                     for (int q = 0; q < kQ; ++q) acc[cc].add_second(V(warp + kWarps * cc, lane + 32 * q), wsh[lane + 32 * q]);
         }
     };
-    if (warp == 0)
+    const bool feed = !a.stall;  // the failure-path test withholds the copies
+    if (warp == 0 && feed)
         for (int k = 0; k < stages - 1 && k < mine; ++k) issue(k);
     int k = 0;
     bool bad = false;
     for (; k < mine; ++k) {
-        if (warp == 0 && k + stages - 1 < mine) issue(k + stages - 1);
+        if (warp == 0 && feed && k + stages - 1 < mine) issue(k + stages - 1);
         const bool ok = mbar_wait_bounded(&full[k % stages], (unsigned)(k / stages) & 1u);
         if (__syncthreads_or(!ok)) {
             bad = true;
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs_tma(CgsArgs a, int stages, int
     if (bad) {
         // record, drain this block's copies still in flight (bounded), drop its partials
         if (tid == 0) atomicExch(err, 1);
-        for (int kk = k; kk < mine && kk < k + stages; ++kk)
+        for (int kk = k; feed && kk < mine && kk < k + stages; ++kk)
             mbar_wait_bounded(&full[kk % stages], (unsigned)(kk / stages) & 1u);
         __syncthreads();
 #pragma unroll

@@ -112,11 +112,45 @@ __device__ __forceinline__ Acc sell_row_wide(const SellView &A, const T *__restr
     return acc;
 }
 
+// Two rows per thread (row0 and row0 + blockDim), their entries interleaved
+// in one loop: twice the independent loads in flight per thread at the same
+// register budget per row.  Each row still sums in CSR order.
+template <typename T, typename V, typename Acc, bool OFF16>
+__device__ __forceinline__ void sell_row2(const SellView &A, const T *__restrict__ x, int r0, int r1, bool has1,
+                                          Acc &u0, Acc &u1) {
+    const int cs = A.cshift, mask = (1 << cs) - 1;
+    const int b0 = __ldg(A.slice_ptr + (r0 >> cs));
+    const int l0 = (__ldg(A.slice_ptr + (r0 >> cs) + 1) - b0) >> cs;
+    int b1 = b0, l1 = 0;
+    if (has1) {
+        b1 = __ldg(A.slice_ptr + (r1 >> cs));
+        l1 = (__ldg(A.slice_ptr + (r1 >> cs) + 1) - b1) >> cs;
+    }
+    const V *v0 = (const V *)A.val + b0 + (r0 & mask), *v1 = (const V *)A.val + b1 + (r1 & mask);
+    const short *o0 = A.off + b0 + (r0 & mask), *o1 = A.off + b1 + (r1 & mask);
+    const int *c0 = A.col + b0 + (r0 & mask), *c1 = A.col + b1 + (r1 & mask);
+    u0 = 0;
+    u1 = 0;
+    const int L = l0 > l1 ? l0 : l1;
+#pragma unroll 4
+    for (int k = 0; k < L; ++k) {
+        const int e = k << cs;
+        if (k < l0) {
+            const int c = OFF16 ? r0 + __ldg(o0 + e) : __ldg(c0 + e);
+            u0 = fma((Acc)__ldg(v0 + e), (Acc)__ldg(x + c), u0);
+        }
+        if (k < l1) {
+            const int c = OFF16 ? r1 + __ldg(o1 + e) : __ldg(c1 + e);
+            u1 = fma((Acc)__ldg(v1 + e), (Acc)__ldg(x + c), u1);
+        }
+    }
+}
+
 constexpr int kPassMaxThreads = 512;
 
 // Row sum of the matrix in format FMT: 0 CSR; SELL with 1 32-bit columns,
-// 2 16-bit offsets, 3 / 4 the same with the wide row loop.  All sum a row's
-// entries in CSR order.
+// 2 16-bit offsets, 3 / 4 the same with the wide row loop (5 / 6: two rows per
+// thread, handled by the kernels).  All sum a row's entries in CSR order.
 template <typename T, typename V, typename Acc, int FMT>
 __device__ __forceinline__ Acc row_sum(const SellView &S, const CsrView &R, const T *__restrict__ x, int row) {
     if constexpr (FMT == 0) {
@@ -139,19 +173,30 @@ __device__ __forceinline__ Acc row_sum(const SellView &S, const CsrView &R, cons
 // with u = A x - sigma x when SIGMA.
 template <typename T, typename V, typename Acc, int KIND, bool SIGMA, int FMT>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass(SellView S, CsrView R, StepArgs s) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= (FMT == 0 ? R.n : S.n)) return;
     const T *x = (const T *)s.x;
-    Acc u = row_sum<T, V, Acc, FMT>(S, R, x, row);
-    if (SIGMA) u = fma(-(Acc)s.sigma, (Acc)x[row], u);
     T *y = (T *)s.y;
-    if (KIND == 0) {
-        y[row] = (T)u;
-    } else if (KIND == 1) {
-        y[row] = (T)fma(-(Acc)s.a2, u, (Acc)x[row]);
+    auto finish = [&](int row, Acc u) {
+        if (SIGMA) u = fma(-(Acc)s.sigma, (Acc)x[row], u);
+        if (KIND == 0) {
+            y[row] = (T)u;
+        } else if (KIND == 1) {
+            y[row] = (T)fma(-(Acc)s.a2, u, (Acc)x[row]);
+        } else {
+            Acc v = fma(-(Acc)s.a1, (Acc)x[row], (Acc)((const T *)s.aux)[row]);
+            y[row] = (T)fma(-(Acc)s.a2, u, v);
+        }
+    };
+    if constexpr (FMT >= 5) {  // two rows per thread
+        const int r0 = blockIdx.x * 2 * blockDim.x + threadIdx.x, r1 = r0 + blockDim.x;
+        if (r0 >= S.n) return;
+        Acc u0, u1;
+        sell_row2<T, V, Acc, FMT == 6>(S, x, r0, r1, r1 < S.n, u0, u1);
+        finish(r0, u0);
+        if (r1 < S.n) finish(r1, u1);
     } else {
-        Acc v = fma(-(Acc)s.a1, (Acc)x[row], (Acc)((const T *)s.aux)[row]);
-        y[row] = (T)fma(-(Acc)s.a2, u, v);
+        const int row = blockIdx.x * blockDim.x + threadIdx.x;
+        if (row >= (FMT == 0 ? R.n : S.n)) return;
+        finish(row, row_sum<T, V, Acc, FMT>(S, R, x, row));
     }
 }
 
@@ -268,10 +313,19 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_tma(SellView A, StepAr
 // General pass (running sum, optional output, outer epilogue): see StepArgs.
 template <typename T, typename V, typename Acc, int FMT>
 __global__ void __launch_bounds__(kPassMaxThreads) k_step(SellView S, CsrView R, StepArgs s) {
-    int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= (FMT == 0 ? R.n : S.n)) return;
-    Acc acc = row_sum<T, V, Acc, FMT>(S, R, (const T *)s.x, row);
-    step_epilogue<T, Acc>(row, acc, s);
+    if constexpr (FMT >= 5) {  // two rows per thread
+        const int r0 = blockIdx.x * 2 * blockDim.x + threadIdx.x, r1 = r0 + blockDim.x;
+        if (r0 >= S.n) return;
+        Acc u0, u1;
+        sell_row2<T, V, Acc, FMT == 6>(S, (const T *)s.x, r0, r1, r1 < S.n, u0, u1);
+        step_epilogue<T, Acc>(r0, u0, s);
+        if (r1 < S.n) step_epilogue<T, Acc>(r1, u1, s);
+    } else {
+        int row = blockIdx.x * blockDim.x + threadIdx.x;
+        if (row >= (FMT == 0 ? R.n : S.n)) return;
+        Acc acc = row_sum<T, V, Acc, FMT>(S, R, (const T *)s.x, row);
+        step_epilogue<T, Acc>(row, acc, s);
+    }
 }
 
 // One polynomial pass for every active instance: warp = 32 consecutive rows
@@ -353,7 +407,8 @@ __global__ void k_convert(int n, const A *x, B *y) {
 template <typename T, int FMT>
 static void pass_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
     const int threads = A.threads;
-    const int blocks = (A.n + threads - 1) / threads;
+    const int rows_per_block = FMT >= 5 ? 2 * threads : threads;
+    const int blocks = (A.n + rows_per_block - 1) / rows_per_block;
     const bool general = s.r || s.oy || !s.y;
     const bool sig = s.sigma != 0.0;
     if (general || (!s.plain && !s.aux && s.a1 != 0.0)) {  // not one of the specialised forms
@@ -422,9 +477,11 @@ static void pass_format(const Matrix &A, const StepArgs &s, cudaStream_t st) {
     if (A.fmt != 2)
         pass_dispatch<T, 0>(A, s, st);
     else if (A.sell.off)
-        A.wide ? pass_dispatch<T, 4>(A, s, st) : pass_dispatch<T, 2>(A, s, st);
+        A.wide == 2 ? pass_dispatch<T, 6>(A, s, st)
+                    : (A.wide ? pass_dispatch<T, 4>(A, s, st) : pass_dispatch<T, 2>(A, s, st));
     else
-        A.wide ? pass_dispatch<T, 3>(A, s, st) : pass_dispatch<T, 1>(A, s, st);
+        A.wide == 2 ? pass_dispatch<T, 5>(A, s, st)
+                    : (A.wide ? pass_dispatch<T, 3>(A, s, st) : pass_dispatch<T, 1>(A, s, st));
 }
 
 void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st) {

@@ -82,7 +82,7 @@ struct Matrix {
     int n = 0;
     int fmt = 2;  // 1 CSR, 2 SELL
     int threads = 256;  // block size of the SELL pass kernels (64..512, chosen by the tuner)
-    int wide = 0;       // SELL row loop: 0 unrolled by four, 1 chunks of eight loads (tuner)
+    int wide = 0;       // SELL row loop: 0 unrolled by four, 1 chunks of eight loads, 2 two rows per thread (tuner)
     int tma = 0;        // SELL-32 slice data staged by bulk copies (tuner); needs tile_cap and err
     int tile_cap = 0;   // most stored entries in threads/32 consecutive slices
     int *err = nullptr; // the context's error word (bounded waits of the staged kernels)
@@ -114,6 +114,7 @@ struct CgsArgs {
     double *part = nullptr;
     unsigned *ticket = nullptr;
     int *err = nullptr;  // set to 1 by a TMA-staged sweep whose bounded wait expired (null: plain sweeps only)
+    int stall = 0;       // test hook: a staged sweep issues no copies, so its waits expire
 };
 int cgs_grid(int n);
 void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st);

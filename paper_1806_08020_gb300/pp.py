@@ -57,6 +57,7 @@ _SIGS = {
     "pp_create": (C.c_int, [C.POINTER(_P), C.c_int64, _I64, C.POINTER(C.c_int32), _D, C.POINTER(pp_opts)]),
     "pp_destroy": (None, [_P]),
     "pp_matrix_info": (C.c_int, [_P, _D, _D]),
+    "pp_debug_stall_sweeps": (C.c_int, [_P, C.c_int]),
     "pp_format_info": (C.c_int, [_P, _I, _I, _I, _I, _I, _I64]),
     "pp_launch_count": (C.c_int64, [_P]),
     "pp_build_poly": (C.c_int, [_P, C.c_int, _D, C.POINTER(_P)]),
@@ -205,6 +206,11 @@ def pp_format_info(ctx: Context) -> dict:
                               C.byref(st)))
     return {"fmt": f.value, "chunk": c.value, "index_bits": ib.value, "threads": t.value, "row_loop": w.value,
             "stored": st.value}
+
+
+def pp_debug_stall_sweeps(ctx: Context, count: int) -> None:
+    """Test support: the next `count` staged CGS2 steps issue no copies (their waits run out)."""
+    _check(LIB.pp_debug_stall_sweeps(ctx.handle, int(count)))
 
 
 def pp_launch_count(ctx: Context) -> int:

@@ -222,6 +222,8 @@ def test_sell_formats_bit_identical(kind, precision):
                 "c16_wide": dict(format=pp.PP_FMT_SELL, sell_c=16, sell_loop=2),
                 "c32_i32_wide": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=2),
                 "c32_staged": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_loop=3),
+                "c16_two_rows": dict(format=pp.PP_FMT_SELL, sell_c=16, sell_loop=4),
+                "c32_i32_two_rows": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=4),
                 "c32_i32_staged": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=3),
                 "tuned": dict(format=pp.PP_FMT_SELL)}
     out, info = {}, {}
@@ -236,5 +238,6 @@ def test_sell_formats_bit_identical(kind, precision):
     assert info["tuned"]["chunk"] in (16, 32) and info["tuned"]["threads"] in (128, 256, 512)
     assert info["c16_wide"]["row_loop"] == 1 and info["c32"]["row_loop"] == 0
     assert info["c32_staged"]["row_loop"] == 2 and info["c32_i32_staged"]["index_bits"] == 32
+    assert info["c16_two_rows"]["row_loop"] == 3
     for name in variants:
         assert np.array_equal(out[name], out["csr"]), name

@@ -60,3 +60,38 @@ def test_tma_sweeps_match_plain_sweeps():
         h_p, v_p = (np.array(x) for x in plain[key])
         assert np.abs(h_t - h_p).max() <= tol * np.abs(h_p).max(), key
         assert np.abs(v_t - v_p).max() <= tol * max(1.0, np.abs(v_p).max()) * 10, key
+
+
+@pytest.mark.gpu
+def test_staged_sweep_wait_expiry_is_reported_and_recoverable():
+    """Failure path of the staged sweeps without a GPU fault: with the copies
+    withheld (a barrier that nothing arms) every bounded wait runs out, the
+    call returns PP_ETIMEOUT, and the same context then computes correctly."""
+    import time
+
+    import torch
+
+    import oracle as O
+    from paper_1806_08020_gb300 import inputs, pp
+    n, j = 100003, 21
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, j)))
+    Q = Q.astype(np.float32).astype(np.float64)
+    w = (rng.standard_normal(n) + Q @ rng.standard_normal(j)).astype(np.float32).astype(np.float64)
+    ctx = pp.pp_create(inputs.diagonal(np.ones(n)), stream=torch.cuda.current_stream().cuda_stream,
+                       precision=pp.PP_FP32)
+    ldv = (n + 31) // 32 * 32
+    Vd = torch.zeros((j, ldv), dtype=torch.float32, device="cuda")
+    Vd[:, :n] = torch.tensor(Q.T, dtype=torch.float32)
+    vd = torch.empty(n, dtype=torch.float32, device="cuda")
+    pp.pp_debug_stall_sweeps(ctx, 1)
+    wd = torch.tensor(w, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_orthogonalize(ctx, Vd.data_ptr(), ldv, j, wd.data_ptr(), vd.data_ptr())
+    assert e.value.status == pp.PP_ETIMEOUT
+    assert time.perf_counter() - t0 < 60
+    wd = torch.tensor(w, dtype=torch.float32, device="cuda")
+    h = pp.pp_orthogonalize(ctx, Vd.data_ptr(), ldv, j, wd.data_ptr(), vd.data_ptr())
+    _, href = O.cgs2(Q, w, O.Counters())
+    assert np.abs(h[:j] - href).max() <= 16 * 2.0**-24 * np.linalg.norm(w)
