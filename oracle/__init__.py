@@ -19,10 +19,13 @@ from .ppa import (  # noqa: F401
     build_double_poly,
     build_poly,
     cgs2,
+    damped_poly,
     eigs,
+    first_cycle_rayleigh,
     gershgorin_shift,
     gmres_arnoldi,
     harmonic_ritz,
+    ideal_order,
     modified_leja,
     norm1,
     pof_log10,

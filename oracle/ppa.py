@@ -13,7 +13,7 @@ Citations name the paper's section, equation or algorithm box:
   reorthogonalisation, convergence test on A with Rayleigh quotients.
 * "Section 7 box": pof and added roots.
 * "Section 8": double polynomial preconditioning.
-* "Section 6.3 box": damping heuristic (not part of this oracle).
+* "Section 6.3 box": heuristic for damping b and adjusting d.
 """
 from __future__ import annotations
 
@@ -518,3 +518,79 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
         j0 = kk
     srt = _target_sort(lam, target)
     return EigResult(lam[srt], X[:, srt], res[srt], False, max_cycles, c, nu[want][srt], hist)
+
+
+# ----------------------------------------------------------------------------
+# Damped polynomials (Section 6; the heuristic of the Section 6.3 box)
+# ----------------------------------------------------------------------------
+
+def ideal_order(mu: np.ndarray, nev: int, k: int) -> bool:
+    """Ideal Order Condition (Section 6.3 box, step 4) on Rayleigh quotients mu_1..mu_k
+    listed in the Ritz order: |mu_1| <= ... <= |mu_nev| < min_{nev < j <= k} |mu_j|."""
+    a = np.abs(np.asarray(mu)[:k])
+    nondecreasing = all(a[i] <= a[i + 1] for i in range(nev - 1))
+    return bool(nondecreasing and a[nev - 1] < a[nev:k].min())
+
+
+def first_cycle_rayleigh(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], b: np.ndarray, m: int,
+                         k: int, c: Counters, sigma: float = 0.0) -> np.ndarray:
+    """Steps 1-3 of the Section 6.3 box: one Arnoldi(m, k) cycle on op = pi(A) from b
+    (CGS2 as in Section 4), Ritz values of H_m ordered by |1 - nu|, and the Rayleigh
+    quotients mu_j = y_j^* A y_j of the unit Ritz vectors for the first k of them,
+    returned for the shifted operator (mu_j - sigma)."""
+    n = b.size
+    V = np.zeros((n, m + 1))
+    H = np.zeros((m + 1, m))
+    V[:, 0] = b / np.linalg.norm(b)
+    for j in range(m):
+        w, h = cgs2(V[:, : j + 1], op(V[:, j]), c)
+        H[: j + 1, j] = h
+        hn = np.linalg.norm(w)
+        H[j + 1, j] = hn
+        V[:, j + 1] = w / hn
+    nu, S = np.linalg.eig(H[:m, :m])
+    order = ritz_order(nu, 1.0)
+    mu = np.zeros(k, dtype=complex)
+    for t, i in enumerate(order[:k]):
+        y = V[:, :m] @ S[:, i]
+        y = y / np.linalg.norm(y)
+        mu[t] = np.vdot(y, A @ y) - sigma
+    return mu
+
+
+@dataclass
+class DampResult:
+    poly: Poly
+    degree: int  # degree finally used (before added roots)
+    damped: bool  # the GMRES start vector was replaced by A b
+    ideal: bool  # the Ideal Order Condition holds for the returned polynomial
+    trials: list  # (degree, damped, condition) per attempt
+
+
+def damped_poly(A: sp.csr_matrix, sigma: float, b: np.ndarray, d: int, m: int, k: int, nev: int,
+                c: Counters, add_roots: bool = True) -> DampResult:
+    """Heuristic for damping b and adjusting d (Section 6.3 box).
+
+    1-3. GMRES(d) polynomial from b; one Arnoldi(m, k) cycle on pi(A) from b; Rayleigh
+         quotients for A of the k Ritz vectors nearest 1.
+    4.   Ideal Order Condition.
+    5.   If it fails: a fresh polynomial from A b (one power step damps the components
+         of b along the small eigenvalues, Section 6.1); if that fails too, halve d
+         (keeping A b) until it holds or d = 1.
+    Readings: the Arnoldi cycle always starts from the original b; with a shift
+    (smallest-real-part targets on A - sigma I) the polynomial, the damping product and
+    the magnitudes all refer to the shifted operator.
+    """
+    op = Operator(A, sigma, c)
+    start, damped, trials = b, False, []
+    while True:
+        P = build_poly(op, start, d, c, add_roots=add_roots)
+        mu = first_cycle_rayleigh(A, make_operator(op, P, c), b, m, k, c, sigma)
+        ok = ideal_order(mu, nev, k)
+        trials.append((d, damped, ok))
+        if ok or (damped and d == 1):
+            return DampResult(P, d, damped, ok, trials)
+        if not damped:
+            start, damped = op(b), True
+        else:
+            d = max(1, d // 2)

@@ -168,3 +168,49 @@ def _eigs_without_coupling(A, op, nev, m, k, v0, cycles=6):
         y /= np.linalg.norm(y)
         out.append(np.vdot(y, A @ y).real)
     return np.array(out)
+
+
+# ---- damping heuristic (Section 6.3 box) ----
+
+def _ideal_strict_first(mu, nev, k):  # "<" instead of "<=" among the first nev
+    a = np.abs(np.asarray(mu)[:k])
+    return bool(all(a[i] < a[i + 1] for i in range(nev - 1)) and a[nev - 1] < a[nev:k].min())
+
+
+def _ideal_no_boundary(mu, nev, k):  # forgets the comparison with the last k - nev
+    a = np.abs(np.asarray(mu)[:k])
+    return bool(all(a[i] <= a[i + 1] for i in range(nev - 1)))
+
+
+def _ideal_real_part(mu, nev, k):  # compares real parts instead of magnitudes
+    a = np.real(np.asarray(mu)[:k])
+    return bool(all(a[i] <= a[i + 1] for i in range(nev - 1)) and a[nev - 1] < a[nev:k].min())
+
+
+@pytest.mark.parametrize("mutant", [_ideal_strict_first, _ideal_no_boundary, _ideal_real_part])
+def test_ideal_order_mutants_caught(mutant, monkeypatch):
+    import test_oracle_damping as T
+    monkeypatch.setattr(O, "ideal_order", mutant)
+    failures = 0
+    for t in (T.test_paper_sequence_fails_ideal_order, T.test_ideal_order_boundaries):
+        try:
+            t()
+        except AssertionError:
+            failures += 1
+    assert failures > 0
+
+
+def test_damping_without_power_step_caught(monkeypatch):
+    """A heuristic that 'damps' by rebuilding from b itself (no A b) never passes at d = 50."""
+    import test_oracle_damping as T
+    real_build = ppa.build_poly
+    calls = []
+
+    def build_no_damp(op, b, d, c, add_roots=True):
+        calls.append(d)
+        return real_build(op, T_b[0], d, c, add_roots)
+    A = O.to_scipy(inputs.diagonal(inputs.example6_diag()))
+    T_b = [inputs.start_vector(A.shape[0], 2, 0)]
+    monkeypatch.setattr(ppa, "build_poly", build_no_damp)
+    with pytest.raises(AssertionError):
+        T.test_example6_d50_damping(A, 2)
