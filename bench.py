@@ -603,8 +603,8 @@ def main():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--serve-max-cycles", type=int, default=300)
     ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--sell-loop", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="SELL row loop (pp_opts.sell_loop): 0 tuner, 1 unrolled, 2 wide, 3 staged")
+    ap.add_argument("--sell-loop", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="SELL row loop (pp_opts.sell_loop): 0 tuner, 1 unrolled, 2 wide, 3 staged, 4 two rows")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

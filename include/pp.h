@@ -157,6 +157,22 @@ pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bit
 pp_status pp_build_poly(pp_ctx *ctx, int d, const double *b, pp_poly **out);
 
 /*
+ * pp_build_poly_damped — the heuristic for damping b and adjusting d (Section
+ * 6.3 box): build pi from b (as pp_build_poly), run one Arnoldi(m, k) cycle on
+ * pi(A) from b, and check the Ideal Order Condition on the Rayleigh quotients
+ * for A of the k Ritz vectors nearest 1 (|mu_1| <= ... <= |mu_nev| < the other
+ * k - nev).  If it fails, rebuild from A b (damping, Section 6.1); if that
+ * fails too, halve d until it holds or d = 1.  With a shift (smallest real
+ * part targets) A stands for A - sigma I throughout.  b: host, n doubles.
+ * Outputs: the polynomial, the degree finally used (before added roots),
+ * damped (1 when built from A b) and ideal (1 when the condition holds for
+ * it; 0 only when d reached 1 without it).  Requires 1 <= nev < k <= m <= 127,
+ * m < n.  Returns PP_OK, or PP_EBREAKDOWN when the final build broke down.
+ */
+pp_status pp_build_poly_damped(pp_ctx *ctx, int d, const double *b, int m, int k, int nev, pp_poly **out,
+                               int *degree, int *damped, int *ideal);
+
+/*
  * pp_build_poly2 — double polynomial (Section 8): pi_1 of degree d1 from b,
  * tau(z) = 1 - pi_1(z) applied as the running sum of pi_1's factors, pi_2 of
  * degree d2 = GMRES polynomial of tau(A) from the same b.  Arnoldi then runs

@@ -18,6 +18,7 @@ from .ppa import (  # noqa: F401
     apply_poly,
     build_double_poly,
     build_poly,
+    build_poly_two,
     cgs2,
     damped_poly,
     eigs,

@@ -13,6 +13,7 @@ Citations name the paper's section, equation or algorithm box:
   reorthogonalisation, convergence test on A with Rayleigh quotients.
 * "Section 7 box": pof and added roots.
 * "Section 8": double polynomial preconditioning.
+* "Section 5 box": polynomial determined by two starting vectors.
 * "Section 6.3 box": heuristic for damping b and adjusting d.
 """
 from __future__ import annotations
@@ -309,6 +310,20 @@ def build_poly(op: Callable[[np.ndarray], np.ndarray], b: np.ndarray, d: int, c:
     if add_roots:
         ordered, added = add_stability_roots(ordered)
     return Poly(roots=ordered, degree=steps, added=added, breakdown=brk, H=H)
+
+
+def build_poly_two(op: Callable[[np.ndarray], np.ndarray], b1: np.ndarray, b2: np.ndarray, d: int, c: Counters,
+                   add_roots: bool = True) -> Poly:
+    """Polynomial determined by two starting vectors (Section 5 box): one GMRES(d)
+    cycle on blockdiag(A, A) from [b1; b2] with ||b1|| = ||b2|| = 1/sqrt(2), then
+    the roots as in the Section 2 box (and the Section 7 box)."""
+    n = b1.size
+    bhat = np.concatenate([b1 / (np.sqrt(2.0) * np.linalg.norm(b1)), b2 / (np.sqrt(2.0) * np.linalg.norm(b2))])
+
+    def op2(x: np.ndarray) -> np.ndarray:
+        return np.concatenate([op(x[:n]), op(x[n:])])
+
+    return build_poly(op2, bhat, d, c, add_roots=add_roots)
 
 
 def apply_poly(op: Callable[[np.ndarray], np.ndarray], roots: np.ndarray, x: np.ndarray,

@@ -785,6 +785,9 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
                     M.tile_cap = cap;
                     double tt = tune ? time_product(c, M) : 0.0;
                     if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
+                    // the plain candidate (SELL-32, unrolled, 256 threads) wins ties within 3 %:
+                    // a variant must be clearly faster to be chosen over timing noise
+                    if (tune && cs == 5 && loop == 0 && t == 256) tt *= 0.97;
                     if (tt < best_t) {
                         best_t = tt;
                         best_threads = t;

@@ -62,6 +62,7 @@ _SIGS = {
     "pp_launch_count": (C.c_int64, [_P]),
     "pp_build_poly": (C.c_int, [_P, C.c_int, _D, C.POINTER(_P)]),
     "pp_build_poly2": (C.c_int, [_P, C.c_int, C.c_int, _D, C.POINTER(_P)]),
+    "pp_build_poly_damped": (C.c_int, [_P, C.c_int, _D, C.c_int, C.c_int, C.c_int, C.POINTER(_P), _I, _I, _I]),
     "pp_poly_from_roots": (C.c_int, [_P, C.c_int, _D, _D, C.POINTER(_P)]),
     "pp_poly_roots": (C.c_int, [_P, _D, _D, C.c_int, _I]),
     "pp_poly_inner_roots": (C.c_int, [_P, _D, _D, C.c_int, _I]),
@@ -222,6 +223,16 @@ def pp_build_poly(ctx: Context, d: int, b) -> Poly:
     h = C.c_void_p()
     st = _check(LIB.pp_build_poly(ctx.handle, int(d), _dp(b), C.byref(h)), allow=(PP_OK, PP_EBREAKDOWN))
     return Poly(h.value, ctx, st)
+
+
+def pp_build_poly_damped(ctx: Context, d: int, b, m: int, k: int, nev: int) -> tuple[Poly, dict]:
+    """Damping heuristic (Section 6.3 box); returns the polynomial and degree / damped / ideal."""
+    b = _f64(b)
+    h = C.c_void_p()
+    deg, dmp, ide = C.c_int(), C.c_int(), C.c_int()
+    st = _check(LIB.pp_build_poly_damped(ctx.handle, int(d), _dp(b), int(m), int(k), int(nev), C.byref(h),
+                                         C.byref(deg), C.byref(dmp), C.byref(ide)), allow=(PP_OK, PP_EBREAKDOWN))
+    return Poly(h.value, ctx, st), {"degree": deg.value, "damped": bool(dmp.value), "ideal": bool(ide.value)}
 
 
 def pp_build_poly2(ctx: Context, d1: int, d2: int, b) -> Poly:
