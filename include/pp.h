@@ -157,6 +157,15 @@ pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bit
 pp_status pp_build_poly(pp_ctx *ctx, int d, const double *b, pp_poly **out);
 
 /*
+ * pp_build_poly_two — the polynomial determined by two starting vectors
+ * (Section 5 box): one GMRES(d) cycle on blockdiag(A, A) (A - sigma I with a
+ * shift) from [b1; b2], each half scaled to norm 1/sqrt(2), then roots as in
+ * pp_build_poly.  b1, b2: host, n doubles each.  Guards against a skewed
+ * start vector.  Requires 1 <= d <= 127.  Returns PP_OK or PP_EBREAKDOWN.
+ */
+pp_status pp_build_poly_two(pp_ctx *ctx, int d, const double *b1, const double *b2, pp_poly **out);
+
+/*
  * pp_build_poly_damped — the heuristic for damping b and adjusting d (Section
  * 6.3 box): build pi from b (as pp_build_poly), run one Arnoldi(m, k) cycle on
  * pi(A) from b, and check the Ideal Order Condition on the Rayleigh quotients

@@ -610,7 +610,10 @@ pp_status pp_batch_create(pp_batch **out, int count, const int64_t *n, const int
     }
     pp_opts o = b->opts;
     o.stream = b->stream;
-    o.format = PP_FMT_SELL;  // the batched pass kernel reads SELL-32
+    o.format = PP_FMT_SELL;  // the batched pass kernel reads SELL
+    // the batched kernels have their own block-shape tuner; no per-matrix tuning
+    if (!o.sell_c) o.sell_c = 32;
+    if (!o.sell_loop) o.sell_loop = 1;
     b->ctx.assign(count, nullptr);
     for (int i = 0; i < count; ++i) {
         pp_status st = pp_create(&b->ctx[i], n[i], rowptr[i], colind[i], vals[i], &o);
@@ -766,6 +769,8 @@ pp_status pp_server_step(pp_server *s, int *active, int *queued) {
         pp_opts o = s->opts;
         o.stream = s->stream;
         o.format = PP_FMT_SELL;
+        if (!o.sell_c) o.sell_c = 32;  // the batched kernels tune their own block shape
+        if (!o.sell_loop) o.sell_loop = 1;
         pp_status st = pp_create_internal(&r->c, r->n, r->rowptr.data(), r->colind.data(), r->vals.data(), &o,
                                           o.precision != PP_FP64);
         r->own_ctx = st >= 0;

@@ -129,6 +129,10 @@ int64_t op_vops(const pp_poly *p);
 int64_t vops_of(const std::vector<StepCoef> &s);
 pp_status ensure_part(pp_ctx *c, size_t doubles);
 pp_status cgs2_step(pp_ctx *c, ppk::Prec pr, void *V, int64_t ldv, int j, void *w, double *hcol);
+// the same over vectors of length n (a block system's basis)
+pp_status cgs2_step_n(pp_ctx *c, ppk::Prec pr, int64_t n, void *V, int64_t ldv, int j, void *w, double *hcol);
+pp_status roots_from_hessenberg(pp_ctx *c, int d, const std::vector<double> &H, int64_t mvps_per_step,
+                                int64_t vops_per_step, pp_poly *out);
 // Arnoldi steps j0..m-1 on Op with a basis stored in precision bpr (the
 // context's vector precision, or BF16).
 pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, ppk::Prec bpr, void *V, int64_t ldv,

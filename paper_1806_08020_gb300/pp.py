@@ -62,6 +62,7 @@ _SIGS = {
     "pp_launch_count": (C.c_int64, [_P]),
     "pp_build_poly": (C.c_int, [_P, C.c_int, _D, C.POINTER(_P)]),
     "pp_build_poly2": (C.c_int, [_P, C.c_int, C.c_int, _D, C.POINTER(_P)]),
+    "pp_build_poly_two": (C.c_int, [_P, C.c_int, _D, _D, C.POINTER(_P)]),
     "pp_build_poly_damped": (C.c_int, [_P, C.c_int, _D, C.c_int, C.c_int, C.c_int, C.POINTER(_P), _I, _I, _I]),
     "pp_poly_from_roots": (C.c_int, [_P, C.c_int, _D, _D, C.POINTER(_P)]),
     "pp_poly_roots": (C.c_int, [_P, _D, _D, C.c_int, _I]),
@@ -222,6 +223,15 @@ def pp_build_poly(ctx: Context, d: int, b) -> Poly:
     b = _f64(b)
     h = C.c_void_p()
     st = _check(LIB.pp_build_poly(ctx.handle, int(d), _dp(b), C.byref(h)), allow=(PP_OK, PP_EBREAKDOWN))
+    return Poly(h.value, ctx, st)
+
+
+def pp_build_poly_two(ctx: Context, d: int, b1, b2) -> Poly:
+    """Polynomial from two starting vectors (Section 5 box)."""
+    b1, b2 = _f64(b1), _f64(b2)
+    h = C.c_void_p()
+    st = _check(LIB.pp_build_poly_two(ctx.handle, int(d), _dp(b1), _dp(b2), C.byref(h)),
+                allow=(PP_OK, PP_EBREAKDOWN))
     return Poly(h.value, ctx, st)
 
 
