@@ -144,6 +144,16 @@ def _profile_traffic(name: str) -> float | None:
         return None
 
 
+def _format_name(f: dict) -> str:
+    loops = {0: "unrolled", 1: "wide", 2: "staged (bulk copies)", 3: "two rows per thread"}
+    if f["fmt"] == 3:
+        return f"k_pass_dia (DIA, {f['stored']} stored values, {f['threads']} threads/block)"
+    if f["fmt"] == 1:
+        return "k_pass (CSR)"
+    return (f"k_pass (SELL-{f['chunk']}, {f['index_bits']}-bit columns, {f['threads']} threads/block, "
+            f"{loops.get(f['row_loop'], '?')} row loop)")
+
+
 def _step_bytes(n: int, nnz_padded: int, nslices: int, roots: np.ndarray, vbytes: int = 8,
                 ibytes: int = 4) -> tuple[int, int]:
     """Algorithmic bytes and launches of one pi(A) apply with SELL-C.
@@ -244,7 +254,7 @@ def run_ours(args, ws, rank, local):
     # roofline of the dominant kernel (fused SELL root step), event-timed over the region
     roots = pp.pp_poly_roots(poly)
     fmt = pp.pp_format_info(ctx)
-    nslices = (n + fmt["chunk"] - 1) // fmt["chunk"]
+    nslices = (n + fmt["chunk"] - 1) // fmt["chunk"] if fmt["chunk"] else 0  # DIA: no slices
     bytes_apply, launches_apply = _step_bytes(n, fmt["stored"], nslices, roots, 8, fmt["index_bits"] // 8)
     # number of applies per solve: m + (cycles - 1) (m - k); t_apply covers all of them
     applies_total = sum(cfg["m"] + (c - 1) * (cfg["m"] - cfg["k"]) for c in cycles)
@@ -261,9 +271,7 @@ def run_ours(args, ws, rank, local):
     roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                 "frac": round(achieved_tflops / fp64_peak, 4), "traffic": traffic,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x %.0f MHz (FP64 non-tensor)" % sm_mhz,
-                "kernel": f"k_pass<double> (fused root step, SELL-{fmt['chunk']}, {fmt['index_bits']}-bit columns, "
-                          f"{fmt['threads']} threads/block, {'wide' if fmt['row_loop'] else 'unrolled'} row loop; "
-                          "real and pair passes)",
+                "kernel": _format_name(fmt) + " (fused root step; real and pair passes)",
                 "bytes_per_launch": round(bytes_apply / launches_apply),
                 "flops_per_launch": round(flops_apply / launches_apply),
                 "launches_timed": applies_total * launches_apply,
@@ -306,7 +314,7 @@ def run_ours(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
         "config": {"workload": cfg["name"], "n": n, "nnz": nnz, "d": cfg["d"], "m": cfg["m"], "k": cfg["k"],
                    "nev": cfg["nev"], "rtol": cfg["rtol"],
-                   "format": f"SELL-{fmt['chunk']} ({fmt['index_bits']}-bit columns, tuned)", "format_info": fmt,
+                   "format": _format_name(fmt), "format_info": fmt,
                    "parallelism": f"replicas x{ws}",
                    "l2": "working set (basis 51 x 8 MB + matrix 60 MB) exceeds the 129 MB L2",
                    "cycles_per_solve": cycles, "max_resid": maxres,

@@ -57,8 +57,10 @@ typedef enum {
  *  PP_FP32_BF16: as PP_FP32 but the Arnoldi basis is stored in BF16 (widened to FP32
  *                when read; pp_eigs only, not the batched or served engines). */
 enum { PP_FP64 = 0, PP_FP32 = 1, PP_FP32_BF16 = 2 };
-/* Sparse format on the device: auto (chosen by the tuner), CSR, SELL-C-sigma. */
-enum { PP_FMT_AUTO = 0, PP_FMT_CSR = 1, PP_FMT_SELL = 2 };
+/* Sparse format on the device: auto (chosen by the tuner), CSR, SELL-C-sigma, DIA
+ * (diagonal storage: stencil and banded matrices with at most 64 distinct diagonals,
+ * sorted columns and at most 30 % padding; no column indices are stored). */
+enum { PP_FMT_AUTO = 0, PP_FMT_CSR = 1, PP_FMT_SELL = 2, PP_FMT_DIA = 3 };
 /* Which eigenvalues: smallest magnitude (Section 2) or smallest real part
  * (run on A - sigma I with sigma the leftmost Gershgorin point, Section 2 footnote 1). */
 enum { PP_TARGET_SM = 0, PP_TARGET_SR = 1 };
@@ -135,12 +137,12 @@ pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);
 
 /*
  * pp_format_info — the device format of A chosen at pp_create: fmt
- * (PP_FMT_CSR or PP_FMT_SELL), the SELL chunk height (0 for CSR), the column
- * index width in bits (16 or 32), the block size of the product kernels, the
+ * (PP_FMT_CSR, PP_FMT_SELL or PP_FMT_DIA), the SELL chunk height (0 otherwise),
+ * the column index width in bits (16 or 32; 0 for DIA), the block size of the product kernels, the
  * SELL row loop (0: unrolled by four; 1: the loads of up to eight entries
  * issued together; 2: slice data staged by bulk copies; 3: two rows per
- * thread), and the stored entries including SELL padding.  Any output
- * pointer may be NULL.
+ * thread), and the stored entries including padding.  Any output pointer
+ * may be NULL.
  */
 pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bits, int *threads, int *row_loop,
                          int64_t *stored);

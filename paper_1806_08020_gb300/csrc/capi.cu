@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <set>
 #include <vector>
 
 
@@ -534,6 +535,20 @@ static int64_t sell_padded(int64_t n, const int64_t *rowptr, int cs) {
     return tot;
 }
 
+// The distinct diagonals col - row of a CSR matrix in increasing order, when the
+// columns of every row increase strictly and there are at most kDiaMax of them.
+static bool dia_offsets(int64_t n, const int64_t *rowptr, const int32_t *colind, std::vector<int> &off) {
+    std::set<int> seen;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            if (k > rowptr[i] && colind[k] <= colind[k - 1]) return false;
+            seen.insert((int)(colind[k] - i));
+            if ((int)seen.size() > ppk::kDiaMax) return false;
+        }
+    off.assign(seen.begin(), seen.end());
+    return true;
+}
+
 // Most stored entries of SELL-32 in any g consecutive slices (a staged tile).
 static int64_t tile_cap(int64_t n, const int64_t *rowptr, int g) {
     int64_t best = 0, cur = 0;
@@ -759,6 +774,9 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
     M.err = c->err();
     c->stored = nnz;
+    double sell_t = INFINITY;  // the tuner's time of the chosen SELL format
+    std::vector<void *> sell_mem;
+    if (fmt == PP_FMT_DIA) fmt = PP_FMT_SELL;  // DIA replaces SELL below when the matrix allows it
     if (fmt == PP_FMT_SELL) {
         M.fmt = 2;
         std::vector<int> threads = {256};
@@ -816,8 +834,56 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         M.tma = best_loop == 2;
         M.tile_cap = best_cap;
         c->stored = sell_padded(n, rowptr, best.cshift);
+        sell_t = best_t;
+        sell_mem = best_mem;
     } else {
         M.fmt = 1;
+    }
+    // DIA for stencil and banded matrices (no column indices): when asked for,
+    // or in auto mode when it times faster than the SELL choice
+    std::vector<int> doff;
+    const bool dia_fits = dia_offsets(n, rowptr, colind, doff) &&
+                          (int64_t)doff.size() * n <= (int64_t)(1.3 * (double)nnz) + 32 * 8;
+    if (c->opts.format == PP_FMT_DIA && !dia_fits)
+        return fail(pp_fail(PP_EINVAL, "pp_create: DIA needs sorted columns, at most %d diagonals and <= 30 %% padding",
+                            ppk::kDiaMax));
+    const bool auto_tuned = c->opts.format == PP_FMT_AUTO && !c->opts.sell_c && !c->opts.sell_loop && M.fmt == 2;
+    if (dia_fits && (c->opts.format == PP_FMT_DIA || auto_tuned)) {
+        const int nd = (int)doff.size();
+        const int64_t ld = c->ldv();
+        int *d_off = nullptr;
+        void *d_dval = nullptr;
+        if ((st = dmalloc(c, (void **)&d_off, nd * 4)) < 0 || (st = dmalloc(c, &d_dval, (size_t)nd * ld * c->esz)) < 0)
+            return fail(st);
+        if (cudaMemcpyAsync(d_off, doff.data(), nd * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return fail(pp_fail(PP_ECUDA, "pp_create: upload failed"));
+        ppk::launch_dia_fill(pr, (int)n, d_rowptr, d_col, d_val, d_off, nd, ld, d_dval, c->stream);
+        if (cudaGetLastError() != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: DIA fill failed"));
+        ppk::Matrix D = M;
+        D.fmt = 3;
+        D.wide = 0;
+        D.tma = 0;
+        D.dia = {(int)n, nd, ld, d_off, d_dval};
+        double dia_t = INFINITY;
+        int dia_threads = 256;
+        for (int t : {128, 256, 512}) {
+            D.threads = t;
+            double tt = time_product(c, D);
+            if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
+            if (tt < dia_t) {
+                dia_t = tt;
+                dia_threads = t;
+            }
+        }
+        if (c->opts.format == PP_FMT_DIA || dia_t < sell_t) {
+            for (void *q : sell_mem) dfree(c, q);
+            D.threads = dia_threads;
+            M = D;
+            c->stored = (int64_t)nd * n;
+        } else {
+            dfree(c, d_off);
+            dfree(c, d_dval);
+        }
     }
     c->A = M;
     // FP64 operator for residuals on A (Section 4 tests convergence on A itself)
@@ -909,10 +975,10 @@ pp_status pp_format_info(const pp_ctx *c, int *fmt, int *chunk, int *index_bits,
                          int64_t *stored) {
     if (!c) return pp_fail(PP_EINVAL, "pp_format_info: null context");
     const bool sell = c->A.fmt == 2;
-    if (fmt) *fmt = sell ? PP_FMT_SELL : PP_FMT_CSR;
+    if (fmt) *fmt = sell ? PP_FMT_SELL : (c->A.fmt == 3 ? PP_FMT_DIA : PP_FMT_CSR);
     if (chunk) *chunk = sell ? 1 << c->A.sell.cshift : 0;
-    if (index_bits) *index_bits = (sell && c->A.sell.off) ? 16 : 32;
-    if (threads) *threads = sell ? c->A.threads : 256;
+    if (index_bits) *index_bits = c->A.fmt == 3 ? 0 : ((sell && c->A.sell.off) ? 16 : 32);
+    if (threads) *threads = c->A.fmt != 1 ? c->A.threads : 256;
     if (row_loop) *row_loop = sell ? (c->A.tma ? 2 : (c->A.wide == 2 ? 3 : c->A.wide)) : 0;
     if (stored) *stored = c->stored;
     return PP_OK;

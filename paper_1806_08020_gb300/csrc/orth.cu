@@ -306,160 +306,148 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
 
 // ---------------------------------------------------------------------------
 // CGS2 sweeps with the basis staged in shared memory by the bulk-copy (TMA)
-// engine.  Each block owns the 64-row tiles bid, bid + nblk, ...; for every
-// full tile one warp issues j + 1 bulk copies (the tile's rows of V[:, c] for
-// c < j, and of w) into a pipeline stage whose mbarrier counts the bytes;
-// `stages` tiles are in flight while the block computes on the oldest.  The
-// arithmetic is that of cgs_body_f64 / cgs_body_f32 on the same rows in the
-// same order, so both paths give bit-identical sweeps.  A ragged last tile
-// (n not a multiple of 64) is read with plain loads.  Every wait on an
-// mbarrier is bounded: on expiry the block records the failure in *err,
-// waits (bounded) for its copies still in flight, contributes zero partials
-// so the grid reduction completes, and the host reports PP_ETIMEOUT.
+// engine (FP32 bases).  A tile is RT = 256 consecutive rows (128 when the
+// basis is too wide for two 256-row stages); block bid owns the full tiles
+// bid, bid + nblk, ...  Warp 0 stages a tile with j + 1 bulk copies (the
+// tile's segment of each basis column and of w) into a pipeline stage whose
+// "full" mbarrier is armed with their bytes; warps release a stage through its
+// "empty" mbarrier and warp 0 refills it, so up to `stages` tiles are in
+// flight while the block computes on the oldest.  Work per tile:
+//  mode 0   column-owned projections (warp w: columns w, w + 8, ...);
+//  mode 1   row-owned update w1 = w - V h1 (one thread per row over all j
+//           columns), one block barrier, then column-owned Dot2 projections
+//           of w1 (double-buffered row vector, so one barrier per tile);
+//  mode 2   row-owned update only.
+// One vote per tile (a block barrier) makes a bounded wait that expired end
+// the sweep in every thread together; the issuing warp then drains its copies
+// (bounded), the block contributes zero partials so the grid reduction
+// completes, and the host reports PP_ETIMEOUT.  A ragged last tile is read
+// with plain loads.  The row sums run over the columns in a different order
+// than the plain sweeps, so the two agree to rounding.
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 4;
+constexpr int kTmaRows = 256;
 
-template <typename T>
-struct CgsArith;
-template <>
-struct CgsArith<double> {  // FP64 throughout
-    using A = double;
-    struct Dot {
-        double s = 0;
-        __device__ void add_first(double x, double y) { s = fma(x, y, s); }
-        __device__ void add_second(double x, double y) { s = fma(x, y, s); }
-        __device__ double value() const { return s; }
-    };
-};
-template <>
-struct CgsArith<float> {  // FP32 first pass and updates, Dot2 second pass
-    using A = float;
-    struct Dot {
-        float s = 0.f, c = 0.f;
-        __device__ void add_first(float x, float y) { s = fmaf(x, y, s); }
-        __device__ void add_second(float x, float y) { dot2_term(x, y, s, c); }
-        __device__ double value() const { return (double)s + (double)c; }
-    };
-};
-
-template <typename T, int CPW>
+template <typename T, int CPW, int RT>
 __global__ void __launch_bounds__(kThreads) k_cgs_tma(CgsArgs a, int stages, int *err) {
-    using Acc = typename CgsArith<T>::A;
-    using Dot = typename CgsArith<T>::Dot;
+    using Acc = float;  // FP32 bases only
     extern __shared__ __align__(128) unsigned char tma_smem[];
-    __shared__ unsigned long long full[kMaxStages];
-    __shared__ Acc red[kWarps][kRows];
-    __shared__ Acc wsh[kRows];
+    __shared__ unsigned long long full[kMaxStages], empty[kMaxStages];
+    __shared__ Acc wsh[2][RT];
     __shared__ Acc hs[8 * CPW];
+    __shared__ int stop;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const int j = a.j, n = a.n, bid = blockIdx.x, nblk = gridDim.x;
-    const size_t stage_elems = (size_t)(j + 1) * kRows;  // V tile columns, then the w tile
+    const size_t stage_elems = (size_t)(j + 1) * RT;  // basis columns, then w
     T *const stage0 = (T *)tma_smem;
-    const int nfull = n / kRows;
-    const int mine = bid < nfull ? (nfull - 1 - bid) / nblk + 1 : 0;  // this block's full tiles
+    const int nfull = n / RT;
+    const int mine = bid < nfull ? (nfull - 1 - bid) / nblk + 1 : 0;
     if (a.mode != 0)
         for (int c = tid; c < j; c += kThreads) hs[c] = (Acc)a.h[c];
     if (tid == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
+        for (int q = 0; q < stages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kWarps);
+        }
         mbar_fence_init();
+        stop = 0;
     }
     __syncthreads();
-    // local tile k -> stage k % stages (issued by warp 0)
-    auto issue = [&](int k) {
-        const int s = k % stages;
-        const size_t r0 = (size_t)(bid + (size_t)k * nblk) * kRows;
-        T *dst = stage0 + (size_t)s * stage_elems;
-        if (lane == 0) mbar_arrive_expect(&full[s], (unsigned)(stage_elems * sizeof(T)));
+    const bool feed = !a.stall;  // the failure-path test withholds the copies
+    int issued = 0;              // tiles issued (warp 0)
+    auto issue = [&](int k) {   // warp 0
+        const int q = k % stages;
+        const size_t r0 = (size_t)(bid + (size_t)k * nblk) * RT;
+        T *dst = stage0 + (size_t)q * stage_elems;
+        if (lane == 0) mbar_arrive_expect(&full[q], (unsigned)(stage_elems * sizeof(T)));
         __syncwarp();
         for (int c = lane; c <= j; c += 32) {
             const T *src = c < j ? (const T *)a.V + (size_t)c * a.ldv + r0 : (const T *)a.w + r0;
-            bulk_copy_g2s(dst + (size_t)c * kRows, src, kRows * sizeof(T), &full[s]);
+            bulk_copy_g2s(dst + (size_t)c * RT, src, (unsigned)(RT * sizeof(T)), &full[q]);
         }
+        issued = k + 1;
     };
-    Dot acc[CPW];
+    float hi[CPW], lo[CPW];
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) hi[cc] = lo[cc] = 0.f;
     double nrm = 0;
-    // one tile: V(c, i) and W(i) give rows r0 + i of V[:, c] and w (zero past n)
-    auto tile = [&](int r0, auto V, auto W) {
+    // One tile of `rows` rows starting at r0: V(c, i), W(i) give its basis and w entries.
+    auto tile = [&](int r0, int rows, int buf, auto V, auto W) {
         if (a.mode == 0) {
 #pragma unroll
-            for (int cc = 0; cc < CPW; ++cc)
-                if (warp + kWarps * cc < j)
-#pragma unroll
-                    for (int q = 0; q < kQ; ++q) acc[cc].add_first(V(warp + kWarps * cc, lane + 32 * q), W(lane + 32 * q));
+            for (int cc = 0; cc < CPW; ++cc) {
+                const int c = warp + kWarps * cc;
+                if (c < j)
+                    for (int i = lane; i < rows; i += 32) hi[cc] = fmaf(V(c, i), W(i), hi[cc]);
+            }
             return;
         }
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) {
+        for (int i = tid; i < rows; i += kThreads) {  // row-owned update
             Acc s = 0;
+            for (int c = 0; c < j; ++c) s = fmaf(V(c, i), hs[c], s);
+            const Acc v = W(i) - s;
+            ((float *)a.wout)[r0 + i] = v;
+            nrm = fma((double)v, (double)v, nrm);
+            wsh[buf][i] = v;
+        }
+        if (a.mode == 1) {
+            __syncthreads();
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc) {
-                int c = warp + kWarps * cc;
-                if (c < j) s = fma(V(c, lane + 32 * q), hs[c], s);
+                const int c = warp + kWarps * cc;
+                if (c < j)
+                    for (int i = lane; i < rows; i += 32) dot2_term(V(c, i), wsh[buf][i], hi[cc], lo[cc]);
             }
-            red[warp][lane + 32 * q] = s;
-        }
-        __syncthreads();
-        if (tid < kRows) {
-            int row = r0 + tid;
-            Acc v = 0;
-            if (row < n) {
-                Acc s = 0;
-#pragma unroll
-                for (int ww = 0; ww < kWarps; ++ww) s += red[ww][tid];
-                v = W(tid) - s;
-                ((T *)a.wout)[row] = (T)v;
-                nrm = fma((double)v, (double)v, nrm);
-            }
-            wsh[tid] = v;
-        }
-        __syncthreads();
-        if (a.mode == 1) {
-#pragma unroll
-            for (int cc = 0; cc < CPW; ++cc)
-                if (warp + kWarps * cc < j)
-#pragma unroll
-                    for (int q = 0; q < kQ; ++q) acc[cc].add_second(V(warp + kWarps * cc, lane + 32 * q), wsh[lane + 32 * q]);
         }
     };
-    const bool feed = !a.stall;  // the failure-path test withholds the copies
     if (warp == 0 && feed)
-        for (int k = 0; k < stages - 1 && k < mine; ++k) issue(k);
-    int k = 0;
+        for (int k = 0; k < stages && k < mine; ++k) issue(k);
     bool bad = false;
+    int k = 0;
     for (; k < mine; ++k) {
-        if (warp == 0 && feed && k + stages - 1 < mine) issue(k + stages - 1);
-        const bool ok = mbar_wait_bounded(&full[k % stages], (unsigned)(k / stages) & 1u);
-        if (__syncthreads_or(!ok)) {
+        const int q = k % stages;
+        const unsigned par = (unsigned)(k / stages) & 1u;
+        const bool ok = mbar_wait_bounded(&full[q], par);
+        if (__syncthreads_or(!ok || stop)) {
             bad = true;
             break;
         }
-        const T *Vs = stage0 + (size_t)(k % stages) * stage_elems;
-        const T *Ws = Vs + (size_t)j * kRows;
-        tile((bid + k * nblk) * kRows, [&](int c, int i) { return (Acc)Vs[(size_t)c * kRows + i]; },
-             [&](int i) { return (Acc)Ws[i]; });
-        __syncthreads();  // the stage is free for the copy issued next iteration
+        const T *Vs = stage0 + (size_t)q * stage_elems;
+        const T *Ws = Vs + (size_t)j * RT;
+        tile((bid + k * nblk) * RT, RT, k & 1, [&](int c, int i) { return ld_f32(Vs + (size_t)c * RT + i); },
+             [&](int i) { return ld_f32(Ws + i); });
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[q]);
+        if (warp == 0 && feed && k + stages < mine) {
+            bool ok2 = true;
+            if (lane == 0) ok2 = mbar_wait_bounded(&empty[q], par);  // every warp released the stage
+            ok2 = __shfl_sync(0xffffffffu, ok2 ? 1 : 0, 0) != 0;
+            if (ok2)
+                issue(k + stages);
+            else if (lane == 0)
+                stop = 1;
+        }
     }
     if (bad) {
-        // record, drain this block's copies still in flight (bounded), drop its partials
         if (tid == 0) atomicExch(err, 1);
-        for (int kk = k; feed && kk < mine && kk < k + stages; ++kk)
-            mbar_wait_bounded(&full[kk % stages], (unsigned)(kk / stages) & 1u);
+        if (warp == 0 && lane == 0)  // drain this block's copies still in flight (bounded)
+            for (int kk = k; kk < issued; ++kk) mbar_wait_bounded(&full[kk % stages], (unsigned)(kk / stages) & 1u);
         __syncthreads();
 #pragma unroll
-        for (int cc = 0; cc < CPW; ++cc) acc[cc] = Dot();
+        for (int cc = 0; cc < CPW; ++cc) hi[cc] = lo[cc] = 0.f;
         nrm = 0;
-    } else if (n % kRows != 0 && (nfull % nblk) == bid) {
+    } else if (n % RT != 0 && (nfull % nblk) == bid) {
         // ragged last tile: plain loads
-        const int r0 = nfull * kRows;
+        __syncthreads();  // wsh of the last full tile may still be read (mode 1)
+        const int r0 = nfull * RT, rows = n - r0;
         const T *V = (const T *)a.V;
         const T *w = (const T *)a.w;
-        tile(r0,
-             [&](int c, int i) { return r0 + i < n ? (Acc)__ldg(V + (size_t)c * a.ldv + r0 + i) : (Acc)0; },
-             [&](int i) { return r0 + i < n ? (Acc)__ldg(w + r0 + i) : (Acc)0; });
+        tile(r0, rows, mine & 1, [&](int c, int i) { return ld_f32(V + (size_t)c * a.ldv + r0 + i); },
+             [&](int i) { return ld_f32(w + r0 + i); });
     }
     double accd[CPW];
 #pragma unroll
-    for (int cc = 0; cc < CPW; ++cc) accd[cc] = acc[cc].value();
+    for (int cc = 0; cc < CPW; ++cc) accd[cc] = (double)hi[cc] + (double)lo[cc];
     cgs_finish<CPW>(a, bid, nblk, accd, nrm);
 }
 
@@ -690,30 +678,39 @@ static int resident_grid(int n, int cap) {
 // relieve, and the staged form measured slower there (block barriers).
 static bool tma_usable(const CgsArgs &a, size_t esz) {
     static const bool off = std::getenv("PP_NO_TMA") != nullptr;
-    return !off && esz == 4 && a.err && a.n >= kRows && ((uintptr_t)a.V % 16) == 0 && ((uintptr_t)a.w % 16) == 0 &&
+    return !off && esz == 4 && a.err && a.n >= kTmaRows && ((uintptr_t)a.V % 16) == 0 && ((uintptr_t)a.w % 16) == 0 &&
            (a.ldv * (int64_t)esz) % 16 == 0 && a.j >= 1 && a.j <= 128;
 }
 
-template <typename T, int CPW>
-static void cgs_tma_launch(const CgsArgs &a, int cap, cudaStream_t st) {
+template <typename T, int CPW, int RT>
+static void cgs_tma_launch_rt(const CgsArgs &a, int cap, cudaStream_t st) {
     static bool attr = false;  // one per instantiation
     if (!attr) {
-        cudaFuncSetAttribute(k_cgs_tma<T, CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_cgs_tma<T, CPW, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    const size_t stage = (size_t)(a.j + 1) * kRows * sizeof(T);
+    const size_t stage = (size_t)(a.j + 1) * RT * sizeof(T);
     int stages = (int)(96 * 1024 / stage);
     stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
     const size_t smem = stage * stages;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_tma<T, CPW>, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_tma<T, CPW, RT>, kThreads, smem);
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 4) per_sm = 4;
-    const int tiles = (a.n + kRows - 1) / kRows;
+    const int tiles = (a.n + RT - 1) / RT;
     int g = per_sm * num_sms();
     if (cap > 0 && g > cap) g = cap;
     if (g > tiles) g = tiles;
-    k_cgs_tma<T, CPW><<<g, kThreads, smem, st>>>(a, stages, a.err);
+    k_cgs_tma<T, CPW, RT><<<g, kThreads, smem, st>>>(a, stages, a.err);
+}
+
+// 256-row tiles while two stages fit in 200 KB, else 128-row tiles.
+template <typename T, int CPW>
+static void cgs_tma_launch(const CgsArgs &a, int cap, cudaStream_t st) {
+    if ((size_t)(a.j + 1) * kTmaRows * sizeof(T) * 2 <= 200 * 1024)
+        cgs_tma_launch_rt<T, CPW, kTmaRows>(a, cap, st);
+    else
+        cgs_tma_launch_rt<T, CPW, kTmaRows / 2>(a, cap, st);
 }
 
 template <typename T>

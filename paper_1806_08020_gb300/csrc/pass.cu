@@ -171,6 +171,53 @@ __device__ __forceinline__ Acc row_sum(const SellView &S, const CsrView &R, cons
 //   KIND 1 real:   y = x - a2 u                (a2 = 1/theta)
 //   KIND 2 pair 2: y = aux - a1 x - a2 u        (x = t, aux = p, a1 = c1, a2 = -c2)
 // with u = A x - sigma x when SIGMA.
+// Row sum over the diagonals (DIA): no index loads; the offsets are in shared
+// memory.  Diagonals run in increasing offset, i.e. the row's CSR order; where
+// the matrix has no entry the stored value is 0 and adds 0 * x exactly.
+template <typename T, typename V, typename Acc>
+__device__ __forceinline__ Acc dia_row(const DiaView &D, const int *off_s, const T *__restrict__ x, int row) {
+    const V *val = (const V *)D.val + row;
+    Acc acc = 0;
+#pragma unroll 8
+    for (int d = 0; d < D.ndiag; ++d) {
+        const int c = row + off_s[d];
+        const Acc xv = (c >= 0 && c < D.n) ? (Acc)__ldg(x + c) : (Acc)0;
+        acc = fma((Acc)__ldg(val + (size_t)d * D.ld), xv, acc);
+    }
+    return acc;
+}
+
+template <typename T, typename V, typename Acc, int KIND, bool SIGMA>
+__global__ void __launch_bounds__(kPassMaxThreads) k_pass_dia(DiaView D, StepArgs s) {
+    __shared__ int off_s[kDiaMax];
+    for (int d = threadIdx.x; d < D.ndiag; d += blockDim.x) off_s[d] = D.off[d];
+    __syncthreads();
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= D.n) return;
+    const T *x = (const T *)s.x;
+    T *y = (T *)s.y;
+    Acc u = dia_row<T, V, Acc>(D, off_s, x, row);
+    if (SIGMA) u = fma(-(Acc)s.sigma, (Acc)x[row], u);
+    if (KIND == 0) {
+        y[row] = (T)u;
+    } else if (KIND == 1) {
+        y[row] = (T)fma(-(Acc)s.a2, u, (Acc)x[row]);
+    } else {
+        Acc v = fma(-(Acc)s.a1, (Acc)x[row], (Acc)((const T *)s.aux)[row]);
+        y[row] = (T)fma(-(Acc)s.a2, u, v);
+    }
+}
+
+template <typename T, typename V, typename Acc>
+__global__ void __launch_bounds__(kPassMaxThreads) k_step_dia(DiaView D, StepArgs s) {
+    __shared__ int off_s[kDiaMax];
+    for (int d = threadIdx.x; d < D.ndiag; d += blockDim.x) off_s[d] = D.off[d];
+    __syncthreads();
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= D.n) return;
+    step_epilogue<T, Acc>(row, dia_row<T, V, Acc>(D, off_s, (const T *)s.x, row), s);
+}
+
 template <typename T, typename V, typename Acc, int KIND, bool SIGMA, int FMT>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass(SellView S, CsrView R, StepArgs s) {
     const T *x = (const T *)s.x;
@@ -381,6 +428,22 @@ __global__ void k_sell_fill(int n, int nslices, int cshift, const int *rowptr, c
 }
 
 template <typename V>
+__global__ void k_dia_fill(int n, const int *rowptr, const int *col, const double *val, const int *off, int ndiag,
+                           int64_t ld, V *dval) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    int k = rowptr[row];
+    const int end = rowptr[row + 1];
+    for (int d = 0; d < ndiag; ++d) {  // columns sorted: walk the row and the offsets together
+        const int c = row + off[d];
+        double v = 0.0;
+        while (k < end && col[k] < c) ++k;
+        if (k < end && col[k] == c) v = val[k];
+        dval[(size_t)d * ld + row] = (V)v;
+    }
+}
+
+template <typename V>
 __global__ void k_convert_vals(int64_t nnz, const double *val, V *out) {
     for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * kThreads)
         out[i] = (V)val[i];
@@ -469,7 +532,33 @@ static bool tma_pass_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t s
 }
 
 template <typename T>
+static void dia_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    const int threads = A.threads;
+    const int blocks = (A.n + threads - 1) / threads;
+    const bool general = s.r || s.oy || !s.y;
+    const bool sig = s.sigma != 0.0;
+    if (general || (!s.plain && !s.aux && s.a1 != 0.0)) {
+        k_step_dia<T, T, T><<<blocks, threads, 0, st>>>(A.dia, s);
+        return;
+    }
+    const int kind = s.plain ? 0 : (s.aux ? 2 : 1);
+#define PP_DPASS(K, S) k_pass_dia<T, T, T, K, S><<<blocks, threads, 0, st>>>(A.dia, s)
+    if (kind == 0) {
+        if (sig) PP_DPASS(0, true); else PP_DPASS(0, false);
+    } else if (kind == 1) {
+        if (sig) PP_DPASS(1, true); else PP_DPASS(1, false);
+    } else {
+        if (sig) PP_DPASS(2, true); else PP_DPASS(2, false);
+    }
+#undef PP_DPASS
+}
+
+template <typename T>
 static void pass_format(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    if (A.fmt == 3) {
+        dia_dispatch<T>(A, s, st);
+        return;
+    }
     if (A.fmt == 2 && A.tma && A.err) {
         const bool done = A.sell.off ? tma_pass_dispatch<T, short>(A, s, st) : tma_pass_dispatch<T, int>(A, s, st);
         if (done) return;
@@ -513,6 +602,15 @@ void launch_sell_fill(Prec p, int n, int nslices, int cshift, const int *rowptr,
     else
         k_sell_fill<float><<<blocks, kThreads, 0, st>>>(n, nslices, cshift, rowptr, col, val, slice_ptr, scol, soff,
                                                         (float *)sval);
+}
+
+void launch_dia_fill(Prec p, int n, const int *rowptr, const int *col, const double *val, const int *off, int ndiag,
+                     int64_t ld, void *dval, cudaStream_t st) {
+    const int blocks = (n + kThreads - 1) / kThreads;
+    if (p == F64)
+        k_dia_fill<double><<<blocks, kThreads, 0, st>>>(n, rowptr, col, val, off, ndiag, ld, (double *)dval);
+    else
+        k_dia_fill<float><<<blocks, kThreads, 0, st>>>(n, rowptr, col, val, off, ndiag, ld, (float *)dval);
 }
 
 void launch_csr_convert(Prec p, int64_t nnz, const double *val, void *out, cudaStream_t st) {

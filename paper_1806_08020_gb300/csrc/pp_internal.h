@@ -57,6 +57,18 @@ struct CsrView {
     const void *val;
 };
 
+// Diagonal storage (for stencil and banded matrices): ndiag offsets off[d]
+// (increasing), values val[d * ld + row] = A(row, row + off[d]) or 0 where the
+// matrix has no entry or row + off[d] lies outside [0, n).  No column indices.
+struct DiaView {
+    int n;
+    int ndiag;
+    int64_t ld;
+    const int *off;
+    const void *val;
+};
+constexpr int kDiaMax = 64;  // most diagonals the DIA kernels take
+
 // One fused pass of the factored polynomial (Eq. (2.1)):
 //   u = (A - sigma I) x
 //   plain:  y = u
@@ -80,7 +92,7 @@ struct StepArgs {
 
 struct Matrix {
     int n = 0;
-    int fmt = 2;  // 1 CSR, 2 SELL
+    int fmt = 2;  // 1 CSR, 2 SELL, 3 DIA
     int threads = 256;  // block size of the SELL pass kernels (64..512, chosen by the tuner)
     int wide = 0;       // SELL row loop: 0 unrolled by four, 1 chunks of eight loads, 2 two rows per thread (tuner)
     int tma = 0;        // SELL-32 slice data staged by bulk copies (tuner); needs tile_cap and err
@@ -89,6 +101,7 @@ struct Matrix {
     Prec prec = F64;
     SellView sell{};
     CsrView csr{};
+    DiaView dia{};
 };
 
 void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st);
@@ -201,6 +214,9 @@ void launch_coldots(Prec p, const ColDotArgs &a, cudaStream_t st);
 void launch_sell_fill(Prec p, int n, int nslices, int cshift, const int *rowptr, const int *col, const double *val,
                       const int *slice_ptr, int *scol, short *soff, void *sval, cudaStream_t st);
 void launch_csr_convert(Prec p, int64_t nnz, const double *val, void *out, cudaStream_t st);
+// DIA fill from a device CSR with sorted columns (off: ndiag device offsets, increasing)
+void launch_dia_fill(Prec p, int n, const int *rowptr, const int *col, const double *val, const int *off, int ndiag,
+                     int64_t ld, void *dval, cudaStream_t st);
 // y = x converted between storage precisions
 void launch_convert(Prec from, Prec to, int n, const void *x, void *y, cudaStream_t st);
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpp.so")
 PP_OK, PP_ENOTCONV, PP_EBREAKDOWN, PP_EAGAIN = 0, 1, 2, 3
 PP_EINVAL, PP_ENOMEM, PP_ECUDA, PP_ETIMEOUT, PP_ENUMERIC = -1, -2, -3, -4, -5
 PP_FP64, PP_FP32, PP_FP32_BF16 = 0, 1, 2
-PP_FMT_AUTO, PP_FMT_CSR, PP_FMT_SELL = 0, 1, 2
+PP_FMT_AUTO, PP_FMT_CSR, PP_FMT_SELL, PP_FMT_DIA = 0, 1, 2, 3
 PP_TARGET_SM, PP_TARGET_SR = 0, 1
 
 

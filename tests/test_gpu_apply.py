@@ -225,7 +225,9 @@ def test_sell_formats_bit_identical(kind, precision):
                 "c16_two_rows": dict(format=pp.PP_FMT_SELL, sell_c=16, sell_loop=4),
                 "c32_i32_two_rows": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=4),
                 "c32_i32_staged": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=3),
-                "tuned": dict(format=pp.PP_FMT_SELL)}
+                "dia": dict(format=pp.PP_FMT_DIA),
+                "tuned": dict(format=pp.PP_FMT_SELL),
+                "auto": dict()}
     out, info = {}, {}
     for name, o in variants.items():
         ctx = pp.pp_create(A, precision=precision, **o)
@@ -239,5 +241,6 @@ def test_sell_formats_bit_identical(kind, precision):
     assert info["c16_wide"]["row_loop"] == 1 and info["c32"]["row_loop"] == 0
     assert info["c32_staged"]["row_loop"] == 2 and info["c32_i32_staged"]["index_bits"] == 32
     assert info["c16_two_rows"]["row_loop"] == 3
+    assert info["dia"]["fmt"] == pp.PP_FMT_DIA and info["dia"]["index_bits"] == 0
     for name in variants:
         assert np.array_equal(out[name], out["csr"]), name
