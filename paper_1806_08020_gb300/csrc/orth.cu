@@ -414,8 +414,9 @@ __global__ void __launch_bounds__(kThreads) k_cgs_tma(CgsArgs a, int stages, int
         }
         const T *Vs = stage0 + (size_t)q * stage_elems;
         const T *Ws = Vs + (size_t)j * RT;
-        tile((bid + k * nblk) * RT, RT, k & 1, [&](int c, int i) { return ld_f32(Vs + (size_t)c * RT + i); },
-             [&](int i) { return ld_f32(Ws + i); });
+        // shared-memory stage: plain loads (the __ldg path is for global memory only)
+        tile((bid + k * nblk) * RT, RT, k & 1, [&](int c, int i) { return (Acc)Vs[(size_t)c * RT + i]; },
+             [&](int i) { return (Acc)Ws[i]; });
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[q]);
         if (warp == 0 && feed && k + stages < mine) {
