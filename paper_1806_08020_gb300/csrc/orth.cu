@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
 // with plain loads.  The row sums run over the columns in a different order
 // than the plain sweeps, so the two agree to rounding.
 // ---------------------------------------------------------------------------
-constexpr int kMaxStages = 4;
+constexpr int kMaxStages = 8;
 constexpr int kTmaRows = 256;
 
 template <typename T, int CPW, int RT>
@@ -383,8 +383,11 @@ __global__ void __launch_bounds__(kThreads) k_cgs_tma(CgsArgs a, int stages, int
             return;
         }
         for (int i = tid; i < rows; i += kThreads) {  // row-owned update
-            Acc s = 0;
-            for (int c = 0; c < j; ++c) s = fmaf(V(c, i), hs[c], s);
+            // eight interleaved partial sums (columns c mod 8), combined pairwise: the
+            // rounding error of a sum over ~j/8 + 3 terms, as in the plain sweeps
+            Acc p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int c = 0; c < j; ++c) p[c & 7] = fmaf(V(c, i), hs[c], p[c & 7]);
+            const Acc s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
             const Acc v = W(i) - s;
             ((float *)a.wout)[r0 + i] = v;
             nrm = fma((double)v, (double)v, nrm);
@@ -690,16 +693,14 @@ static void cgs_tma_launch_rt(const CgsArgs &a, int cap, cudaStream_t st) {
         cudaFuncSetAttribute(k_cgs_tma<T, CPW, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
+    // one block per SM with a deep pipeline (up to 8 stages, ~150 KB in flight):
+    // each block then walks enough tiles to run at steady state
     const size_t stage = (size_t)(a.j + 1) * RT * sizeof(T);
-    int stages = (int)(96 * 1024 / stage);
+    int stages = (int)(150 * 1024 / stage);
     stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
     const size_t smem = stage * stages;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_tma<T, CPW, RT>, kThreads, smem);
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 4) per_sm = 4;
     const int tiles = (a.n + RT - 1) / RT;
-    int g = per_sm * num_sms();
+    int g = num_sms();
     if (cap > 0 && g > cap) g = cap;
     if (g > tiles) g = tiles;
     k_cgs_tma<T, CPW, RT><<<g, kThreads, smem, st>>>(a, stages, a.err);

@@ -2,9 +2,11 @@
 polynomial pass for all instances, one CUDA graph per Arnoldi step).
 
 * Each batched result equals the solo GPU solve of the same instance on the
-  same inputs (same method, same precision): eigenvalues within 1e-10
-  relative, and the same number of cycles (FP64).  The batched CGS2 uses a
-  different block count, so sums differ by rounding only.
+  same inputs (same method, same precision): in FP64 eigenvalues within
+  1e-10 relative and the same number of cycles (the batched CGS2 uses a
+  different block count, so sums differ by rounding only); in FP32 within the
+  kappa-gated bound (the solo sweeps are staged and sum rows in another
+  order).
 * Every returned pair meets ||A x - lam x|| <= 1e-8 ||A||_1, recomputed on the
   CPU from the returned vectors; eigenvalues match the oracle's within the
   kappa-gated first-order bound.
@@ -52,9 +54,17 @@ def test_batch_equals_solo(precision):
         rc = cpu_residuals(O.to_scipy(A), rb.lam, rb.X)
         assert np.all(rc <= 1.01e-8)
         assert rb.lam.size == solo.lam.size
-        assert np.max(np.abs(rb.lam - solo.lam) / np.abs(solo.lam)) <= 1e-10
         if precision == "fp64":
+            assert np.max(np.abs(rb.lam - solo.lam) / np.abs(solo.lam)) <= 1e-10
             assert rb.stats["cycles"] == solo.stats["cycles"]
+        else:
+            # FP32 solo sweeps are staged (row sums in another order): the two runs take
+            # different rounding paths, so they agree within each eigenvalue's conditioning
+            w, kap = eig_condition(A.to_dense())
+            nA = O.norm1(O.to_scipy(A))
+            for lb, ls, rsb, rss in zip(rb.lam, solo.lam, rb.resid, solo.resid):
+                kj = kap[np.argmin(np.abs(w - ls))]
+                assert abs(lb - ls) <= 10 * kj * (rsb + rss) * nA + 1e-12 * abs(ls)
 
 
 def test_batch_matches_oracle():
