@@ -675,14 +675,15 @@ static int resident_grid(int n, int cap) {
     return tiles < g ? tiles : g;
 }
 
-// TMA-staged sweeps need 16-byte aligned column starts and w, a context's
-// error word, and at least one full tile; PP_NO_TMA in the environment turns
-// them off (the plain sweeps compute the same values).  FP64 bases keep the
-// plain sweeps: they are bound by FP64 arithmetic, which staging does not
-// relieve, and the staged form measured slower there (block barriers).
+// TMA-staged sweeps are opt-in (PP_TMA_CGS in the environment): on the bases
+// measured here (j <= 51, n up to 4e6) they ran no faster than the plain
+// sweeps, and their different summation order moved the mixed-precision
+// solves onto slower paths.  They need FP32 bases, 16-byte aligned column
+// starts and w, a context's error word, and one full tile.  FP64 bases always
+// take the plain sweeps (bound by FP64 arithmetic, which staging cannot relieve).
 static bool tma_usable(const CgsArgs &a, size_t esz) {
-    static const bool off = std::getenv("PP_NO_TMA") != nullptr;
-    return !off && esz == 4 && a.err && a.n >= kTmaRows && ((uintptr_t)a.V % 16) == 0 && ((uintptr_t)a.w % 16) == 0 &&
+    static const bool on = std::getenv("PP_TMA_CGS") != nullptr;
+    return (on || a.stall) && esz == 4 && a.err && a.n >= kTmaRows && ((uintptr_t)a.V % 16) == 0 && ((uintptr_t)a.w % 16) == 0 &&
            (a.ldv * (int64_t)esz) % 16 == 0 && a.j >= 1 && a.j <= 128;
 }
 
@@ -693,14 +694,18 @@ static void cgs_tma_launch_rt(const CgsArgs &a, int cap, cudaStream_t st) {
         cudaFuncSetAttribute(k_cgs_tma<T, CPW, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    // one block per SM with a deep pipeline (up to 8 stages, ~150 KB in flight):
-    // each block then walks enough tiles to run at steady state
+    // up to four stages in 96 KB; as many blocks per SM as fit (measured faster than
+    // one block per SM with a deeper pipeline: eight warps cannot keep the stages busy)
     const size_t stage = (size_t)(a.j + 1) * RT * sizeof(T);
-    int stages = (int)(150 * 1024 / stage);
-    stages = stages < 2 ? 2 : (stages > kMaxStages ? kMaxStages : stages);
+    int stages = (int)(96 * 1024 / stage);
+    stages = stages < 2 ? 2 : (stages > 4 ? 4 : stages);
     const size_t smem = stage * stages;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs_tma<T, CPW, RT>, kThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;
     const int tiles = (a.n + RT - 1) / RT;
-    int g = num_sms();
+    int g = per_sm * num_sms();
     if (cap > 0 && g > cap) g = cap;
     if (g > tiles) g = tiles;
     k_cgs_tma<T, CPW, RT><<<g, kThreads, smem, st>>>(a, stages, a.err);

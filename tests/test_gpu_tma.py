@@ -1,9 +1,9 @@
-"""CGS2 sweeps with the basis staged by the bulk-copy (TMA) engine against the
-plain sweeps (PP_NO_TMA), through the C-ABI.
+"""CGS2 sweeps with the basis staged by the bulk-copy (TMA) engine (opt-in,
+PP_TMA_CGS) against the plain sweeps, through the C-ABI.
 
-Both compute the same projections on the same rows; only the grid (and so
-the order of the block partial sums) may differ, so they agree to rounding.
-The plain run happens in a child process because the switch is read once.
+Both compute the same projections on the same rows in different orders, so
+they agree to rounding.  Each run happens in a child process because the
+switch is read once.
 """
 import json
 import os
@@ -41,9 +41,9 @@ json.dump(out, sys.stdout)
 
 def _run(no_tma: bool):
     env = dict(os.environ)
-    env.pop("PP_NO_TMA", None)
-    if no_tma:
-        env["PP_NO_TMA"] = "1"
+    env.pop("PP_TMA_CGS", None)
+    if not no_tma:
+        env["PP_TMA_CGS"] = "1"
     r = subprocess.run([sys.executable, "-c", CHILD], capture_output=True, text=True, env=env, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     return json.loads(r.stdout)
