@@ -224,6 +224,7 @@ def run_ours(args, ws, rank, local):
             t_apply += st["t_apply"]
             cycles.append(st["cycles"])
             counters = {k: int(st[k]) for k in ("mvps", "dots", "vops")}
+            phases = {k: round(st[k] * 1e3, 3) for k in ("t_total", "t_apply", "t_orth", "t_restart")}
             counters.update({"build_" + k: v for k, v in pp.pp_poly_counts(poly).items()})
             maxres = max(maxres, float(np.max(res.resid)))
         ev1.record(stream)
@@ -320,7 +321,10 @@ def run_ours(args, ws, rank, local):
                    "cycles_per_solve": cycles, "max_resid": maxres,
                    # Section 4's counters for one solve (eigensolve, and the GMRES build), as in the
                    # paper's tables: mvps = products with A, dots = inner products, vops = vector ops
-                   "counters_per_solve": counters},
+                   "counters_per_solve": counters,
+                   # one solve's phases in ms (apply and CGS2 event-timed on the device; restart and
+                   # convergence test include host work); the polynomial build is the remainder
+                   "phases_ms": phases},
         "e2e": {"value": round(e2e_pairs / te, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "steps": e2e_steps},
         "gpu_launches": int(launches),

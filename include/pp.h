@@ -113,6 +113,10 @@ const char *pp_last_error(void);
  * the device formats (Section 2: the method needs only products with A).
  * rowptr: n+1 int64; colind: nnz int32 in [0, n); vals: nnz doubles.
  * opts may be NULL (defaults).  On success *out receives a context.
+ * In auto mode the tuner's choice (format, chunk, row loop, block size) is kept
+ * for the life of the process under a signature of the matrix (n, nnz, element
+ * size, index width, sampled row pointers and columns); a later context for a
+ * matrix with the same signature reuses it without timing.
  * Errors: PP_EINVAL (n <= 0, bad indices), PP_ENOMEM, PP_ECUDA.
  */
 pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind,

@@ -19,6 +19,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
 #include <set>
 #include <vector>
 
@@ -642,6 +644,39 @@ static double time_product(pp_ctx *c, const ppk::Matrix &M) {
     return best;
 }
 
+// Tuner decisions cached per process, keyed by a signature of the matrix (size,
+// precision, index width and sampled row pointers and columns): contexts for the
+// same matrix skip the timing runs and build only the chosen format.
+struct TuneChoice {
+    int cs = 5, threads = 256, loop = 0, cap = 0;
+    bool dia = false;
+    int dia_threads = 256;
+};
+static std::mutex g_tune_mu;
+static std::map<uint64_t, TuneChoice> g_tune_cache;
+
+static uint64_t matrix_signature(int64_t n, const int64_t *rowptr, const int32_t *colind, size_t esz, bool off16) {
+    uint64_t h = 1469598103934665603ULL;
+    auto mix = [&](uint64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (v >> (8 * b)) & 0xff;
+            h *= 1099511628211ULL;
+        }
+    };
+    mix((uint64_t)n);
+    mix((uint64_t)rowptr[n]);
+    mix(esz);
+    mix(off16 ? 1 : 0);
+    const int64_t nnz = rowptr[n];
+    for (int t = 0; t < 192; ++t) {
+        const int64_t i = t < 64 ? std::min<int64_t>(t, n - 1)
+                                 : (t < 128 ? std::max<int64_t>(0, n - 128 + t) : (n - 1) * (t - 128) / 63);
+        mix((uint64_t)rowptr[i]);
+        if (nnz > 0) mix((uint64_t)(uint32_t)colind[std::min<int64_t>(nnz - 1, (nnz - 1) * t / 191)]);
+    }
+    return h;
+}
+
 pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind,
                              const double *vals, const pp_opts *opts, int make_twin) {
     if (!out || n <= 0 || !rowptr || !colind || !vals) return pp_fail(PP_EINVAL, "pp_create: bad arguments");
@@ -777,6 +812,18 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     double sell_t = INFINITY;  // the tuner's time of the chosen SELL format
     std::vector<void *> sell_mem;
     if (fmt == PP_FMT_DIA) fmt = PP_FMT_SELL;  // DIA replaces SELL below when the matrix allows it
+    const bool cacheable = c->opts.format == PP_FMT_AUTO && !c->opts.sell_c && !c->opts.sell_loop && fmt == PP_FMT_SELL;
+    const uint64_t sig = cacheable ? matrix_signature(n, rowptr, colind, c->esz, off16) : 0;
+    bool cached = false;
+    TuneChoice choice;
+    if (cacheable) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(sig);
+        if (it != g_tune_cache.end()) {
+            choice = it->second;
+            cached = true;
+        }
+    }
     if (fmt == PP_FMT_SELL) {
         M.fmt = 2;
         std::vector<int> threads = {256};
@@ -784,6 +831,11 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         // row loops: 0 unrolled, 1 wide, 2 staged by bulk copies (SELL-32 only), 3 two rows per thread
         std::vector<int> loops = {0, 1, 2, 3};
         if (c->opts.sell_loop) loops = {c->opts.sell_loop - 1};
+        if (cached) {  // the decision of an earlier context for this matrix
+            cands = {choice.cs};
+            threads = {choice.threads};
+            loops = {choice.loop};
+        }
         const bool tune = cands.size() * threads.size() * loops.size() > 1;
         double best_t = INFINITY;
         int best_threads = 256, best_loop = 0, best_cap = 0;
@@ -836,6 +888,10 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         c->stored = sell_padded(n, rowptr, best.cshift);
         sell_t = best_t;
         sell_mem = best_mem;
+        choice.cs = best.cshift;
+        choice.threads = best_threads;
+        choice.loop = best_loop;
+        choice.cap = best_cap;
     } else {
         M.fmt = 1;
     }
@@ -848,7 +904,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         return fail(pp_fail(PP_EINVAL, "pp_create: DIA needs sorted columns, at most %d diagonals and <= 30 %% padding",
                             ppk::kDiaMax));
     const bool auto_tuned = c->opts.format == PP_FMT_AUTO && !c->opts.sell_c && !c->opts.sell_loop && M.fmt == 2;
-    if (dia_fits && (c->opts.format == PP_FMT_DIA || auto_tuned)) {
+    if (dia_fits && (c->opts.format == PP_FMT_DIA || (auto_tuned && (!cached || choice.dia)))) {
         const int nd = (int)doff.size();
         const int64_t ld = c->ldv();
         int *d_off = nullptr;
@@ -865,17 +921,20 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         D.tma = 0;
         D.dia = {(int)n, nd, ld, d_off, d_dval};
         double dia_t = INFINITY;
-        int dia_threads = 256;
-        for (int t : {128, 256, 512}) {
-            D.threads = t;
-            double tt = time_product(c, D);
-            if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
-            if (tt < dia_t) {
-                dia_t = tt;
-                dia_threads = t;
+        int dia_threads = cached ? choice.dia_threads : 256;
+        if (!cached)
+            for (int t : {128, 256, 512}) {
+                D.threads = t;
+                double tt = time_product(c, D);
+                if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
+                if (tt < dia_t) {
+                    dia_t = tt;
+                    dia_threads = t;
+                }
             }
-        }
-        if (c->opts.format == PP_FMT_DIA || dia_t < sell_t) {
+        choice.dia = cached ? choice.dia : dia_t < sell_t;
+        choice.dia_threads = dia_threads;
+        if (c->opts.format == PP_FMT_DIA || choice.dia) {
             for (void *q : sell_mem) dfree(c, q);
             D.threads = dia_threads;
             M = D;
@@ -884,6 +943,10 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
             dfree(c, d_off);
             dfree(c, d_dval);
         }
+    }
+    if (cacheable && !cached) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[sig] = choice;
     }
     c->A = M;
     // FP64 operator for residuals on A (Section 4 tests convergence on A itself)

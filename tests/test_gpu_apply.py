@@ -242,5 +242,7 @@ def test_sell_formats_bit_identical(kind, precision):
     assert info["c32_staged"]["row_loop"] == 2 and info["c32_i32_staged"]["index_bits"] == 32
     assert info["c16_two_rows"]["row_loop"] == 3
     assert info["dia"]["fmt"] == pp.PP_FMT_DIA and info["dia"]["index_bits"] == 0
+    # the second auto context on this matrix takes the first one's cached choice
+    assert info["auto"] == pp.pp_format_info(ref_ctx)
     for name in variants:
         assert np.array_equal(out[name], out["csr"]), name
