@@ -78,9 +78,10 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
             S.dots += 2 * (j + 1) + 1;
             S.vops += 4 * (j + 1) + 2 + opv;
         }
-        double th0 = now();
         CK(cudaMemcpyAsync(H.data(), dH, H.size() * 8, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        // the restart clock starts once the cycle's Arnoldi steps have run
+        double th0 = now();
         CKS(check_sweeps(c));
         accumulate_times(tm, marks, S.t_apply, S.t_orth);
         CKS(wanted_set(H, ldh, m, nev, target, cy));

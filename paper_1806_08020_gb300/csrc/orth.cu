@@ -12,6 +12,7 @@
 
 #include <cstdint>
 #include <cstdlib>
+#include <type_traits>
 
 namespace ppk {
 
@@ -720,6 +721,31 @@ static void cgs_tma_launch(const CgsArgs &a, int cap, cudaStream_t st) {
         cgs_tma_launch_rt<T, CPW, kTmaRows / 2>(a, cap, st);
 }
 
+// Calls f(std::integral_constant<int, C>) with C the smallest instantiated
+// columns-per-warp count >= cpw.  Every count up to 8 (bases of up to 64
+// columns) has its own instantiation: a warp's column slots past j are skipped
+// by a warp-uniform test that the compiler may turn into predicated FMAs, which
+// still occupy the FP64 pipe, so the slots are kept within 7 of j.
+template <typename F>
+static void with_cpw(int cpw, F &&f) {
+    switch (cpw) {
+        case 0:
+        case 1: f(std::integral_constant<int, 1>{}); break;
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 3: f(std::integral_constant<int, 3>{}); break;
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        case 5: f(std::integral_constant<int, 5>{}); break;
+        case 6: f(std::integral_constant<int, 6>{}); break;
+        case 7: f(std::integral_constant<int, 7>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        case 9:
+        case 10:
+        case 11:
+        case 12: f(std::integral_constant<int, 12>{}); break;
+        default: f(std::integral_constant<int, 16>{}); break;
+    }
+}
+
 template <typename T>
 static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
@@ -736,15 +762,9 @@ static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
         return;
         }
     }
-    int cpw = (a.j + kWarps - 1) / kWarps;
-    if (cpw <= 2)
-        k_cgs<T, 2><<<resident_grid<T, 2>(a.n, cap), kThreads, 0, st>>>(a);
-    else if (cpw <= 4)
-        k_cgs<T, 4><<<resident_grid<T, 4>(a.n, cap), kThreads, 0, st>>>(a);
-    else if (cpw <= 8)
-        k_cgs<T, 8><<<resident_grid<T, 8>(a.n, cap), kThreads, 0, st>>>(a);
-    else
-        k_cgs<T, 16><<<resident_grid<T, 16>(a.n, cap), kThreads, 0, st>>>(a);
+    with_cpw((a.j + kWarps - 1) / kWarps, [&](auto C) {
+        k_cgs<T, C.value><<<resident_grid<T, C.value>(a.n, cap), kThreads, 0, st>>>(a);
+    });
 }
 
 void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st) {
@@ -762,14 +782,12 @@ void launch_scale_bf16(int n, const float *w, const double *scal, void *out, cud
 
 void launch_cgs_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int mode,
                       int jj, cudaStream_t st) {
-    int cpw = (jj + 1 + kWarps - 1) / kWarps;
-#define PP_CB(T, C) k_cgs_batch<T, C><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj)
-    if (p == F64) {
-        if (cpw <= 2) PP_CB(double, 2); else if (cpw <= 4) PP_CB(double, 4); else if (cpw <= 8) PP_CB(double, 8); else PP_CB(double, 16);
-    } else {
-        if (cpw <= 2) PP_CB(float, 2); else if (cpw <= 4) PP_CB(float, 4); else if (cpw <= 8) PP_CB(float, 8); else PP_CB(float, 16);
-    }
-#undef PP_CB
+    with_cpw((jj + 1 + kWarps - 1) / kWarps, [&](auto C) {
+        if (p == F64)
+            k_cgs_batch<double, C.value><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj);
+        else
+            k_cgs_batch<float, C.value><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj);
+    });
 }
 
 void launch_scale_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int jj,
