@@ -195,7 +195,7 @@ def run_ours(args, ws, rank, local):
     b = inputs.start_vector(n, seed, 0)
     v0 = inputs.start_vector(n, seed, 1)
     stream = torch.cuda.Stream(device=dev)
-    ctx = pp.pp_create(A, stream=stream.cuda_stream, sell_loop=args.sell_loop)
+    ctx = pp.pp_create(A, stream=stream.cuda_stream, sell_loop=args.sell_loop, sell_c=args.sell_c)
 
     def barrier():
         torch.cuda.synchronize()
@@ -287,7 +287,8 @@ def run_ours(args, ws, rank, local):
                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback"}}
 
     # the same workload with FP32 apply and basis and FP64 refinement on A
-    ctx32 = pp.pp_create(A, stream=stream.cuda_stream, precision=pp.PP_FP32, sell_loop=args.sell_loop)
+    ctx32 = pp.pp_create(A, stream=stream.cuda_stream, precision=pp.PP_FP32, sell_loop=args.sell_loop,
+                         sell_c=args.sell_c)
     def solve32():
         p32 = pp.pp_build_poly(ctx32, cfg["d"], b)
         return pp.pp_eigs(ctx32, p32, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=False)
@@ -542,7 +543,8 @@ def run_precision3d(args, ws, rank, local):
     stream = torch.cuda.Stream()
     out = {}
     for name, prec in (("mixed_fp32", pp.PP_FP32), ("mixed_bf16_basis", pp.PP_FP32_BF16), ("fp64", pp.PP_FP64)):
-        ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, max_cycles=60, sell_loop=args.sell_loop)
+        ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, max_cycles=60, sell_loop=args.sell_loop,
+                           sell_c=args.sell_c)
 
         def solve():
             poly = pp.pp_build_poly2(ctx, cfg["d1"], cfg["d2"], b)
@@ -666,6 +668,8 @@ def main():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--serve-max-cycles", type=int, default=300)
     ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--sell-c", type=int, default=0, choices=[0, 16, 32],
+                    help="SELL chunk height (pp_opts.sell_c): 0 tuner; 16 or 32 fixes it and the block size (256)")
     ap.add_argument("--sell-loop", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="SELL row loop (pp_opts.sell_loop): 0 tuner, 1 unrolled, 2 wide, 3 staged, 4 two rows")
     args = ap.parse_args()

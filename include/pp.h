@@ -124,6 +124,16 @@ pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_
 void pp_destroy(pp_ctx *ctx);
 
 /*
+ * pp_trim — free the device workspace a context keeps between calls.
+ * pp_build_poly* and pp_eigs hand their per-call buffers (Krylov bases, the
+ * FP64 test and refinement buffers) back to the context, which reuses them for
+ * later calls of the same sizes instead of allocating again; the memory stays
+ * held until pp_trim or pp_destroy.  Synchronises the context's stream.
+ * Errors: PP_EINVAL (null context).
+ */
+pp_status pp_trim(pp_ctx *ctx);
+
+/*
  * pp_debug_stall_sweeps — test support for the failure path of the staged
  * CGS2 sweeps: the next `count` CGS2 steps on this context issue no bulk
  * copies, so every wait for a staged tile runs out its bounded limit; the

@@ -56,6 +56,41 @@ void dfree(pp_ctx *c, void *p) {
     c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), p), c->allocs.end());
 }
 
+pp_status ws_get(pp_ctx *c, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    int best = -1;
+    for (size_t i = 0; i < c->ws_spare.size(); ++i) {
+        const size_t s = c->ws_spare[i].second;
+        if (s >= bytes && s - bytes <= bytes / 4 && (best < 0 || s < c->ws_spare[best].second)) best = (int)i;
+    }
+    if (best >= 0) {
+        *p = c->ws_spare[best].first;
+        c->ws_live.push_back(c->ws_spare[best]);
+        c->ws_spare.erase(c->ws_spare.begin() + best);
+        return PP_OK;
+    }
+    CKS(dmalloc(c, p, bytes));
+    c->ws_live.push_back({*p, bytes});
+    return PP_OK;
+}
+
+void ws_put(pp_ctx *c, void *p) {
+    for (size_t i = 0; i < c->ws_live.size(); ++i)
+        if (c->ws_live[i].first == p) {
+            c->ws_spare.push_back(c->ws_live[i]);
+            c->ws_live.erase(c->ws_live.begin() + i);
+            return;
+        }
+    dfree(c, p);
+}
+
+void ws_trim(pp_ctx *c) {
+    if (c->ws_spare.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto &b : c->ws_spare) dfree(c, b.first);
+    c->ws_spare.clear();
+}
+
 pp_status check_launch(pp_ctx *c) {
     c->launches++;
     cudaError_t e = cudaGetLastError();
@@ -388,14 +423,11 @@ pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, 
     pp_status st = PP_OK;
     std::vector<void *> mine;
     auto cleanup = [&]() {
-        for (void *q : mine) {
-            cudaFree(q);
-            c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), q), c->allocs.end());
-        }
+        for (void *q : mine) ws_put(c, q);
     };
-    if ((st = dmalloc(c, &V, (size_t)ldv * (d + 1) * c->esz)) < 0) return st;
+    if ((st = ws_get(c, &V, (size_t)ldv * (d + 1) * c->esz)) < 0) return st;
     mine.push_back(V);
-    if ((st = dmalloc(c, (void **)&dH, (size_t)(d + 1) * d * 8)) < 0) {
+    if ((st = ws_get(c, (void **)&dH, (size_t)(d + 1) * d * 8)) < 0) {
         cleanup();
         return st;
     }
@@ -507,6 +539,13 @@ void pp_opts_default(pp_opts *o) {
     o->sell_c = 0;
     o->sell_sigma = 0;
     o->stream = nullptr;
+}
+
+pp_status pp_trim(pp_ctx *c) {
+    if (!c) return pp_fail(PP_EINVAL, "pp_trim: null context");
+    ws_trim(c);
+    if (c->twin) ws_trim(c->twin);
+    return PP_OK;
 }
 
 void pp_destroy(pp_ctx *c) {
@@ -1086,19 +1125,19 @@ static pp_status build_roots_two(pp_ctx *c, int d, const double *b1, const doubl
     const size_t esz = c->esz;
     std::vector<void *> mine;
     auto cleanup = [&]() {
-        for (void *q : mine) dfree(c, q);
+        for (void *q : mine) ws_put(c, q);
     };
     void *V = nullptr, *W = nullptr;
     double *dH = nullptr;
     pp_status st;
-    if ((st = dmalloc(c, &V, (size_t)ldv * (d + 1) * esz)) < 0) return st;
+    if ((st = ws_get(c, &V, (size_t)ldv * (d + 1) * esz)) < 0) return st;
     mine.push_back(V);
-    if ((st = dmalloc(c, &W, (size_t)ldv * esz)) < 0) {
+    if ((st = ws_get(c, &W, (size_t)ldv * esz)) < 0) {
         cleanup();
         return st;
     }
     mine.push_back(W);
-    if ((st = dmalloc(c, (void **)&dH, (size_t)(d + 1) * d * 8)) < 0) {
+    if ((st = ws_get(c, (void **)&dH, (size_t)(d + 1) * d * 8)) < 0) {
         cleanup();
         return st;
     }

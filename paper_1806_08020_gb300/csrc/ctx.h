@@ -87,6 +87,9 @@ struct pp_ctx {
     pp_ctx *twin = nullptr;  // FP64 copy of an FP32 context (mixed-precision fallback)
     int64_t stored = 0;      // matrix entries held on the device (with SELL padding)
     int stall_sweeps = 0;    // test hook: staged CGS2 sweeps left to run without copies
+    // per-call device workspace (bases, test buffers) kept for the next call:
+    // blocks in use and their sizes, and blocks free for reuse
+    std::vector<std::pair<void *, size_t>> ws_live, ws_spare;
     int64_t ldv() const { return (n + 31) / 32 * 32; }
     // device error word of the TMA-staged sweeps (set when a bounded wait expired)
     int *err() const { return (int *)(d_small + 4000); }
@@ -120,6 +123,13 @@ struct Timers {
 
 pp_status dmalloc(pp_ctx *c, void **p, size_t bytes);
 void dfree(pp_ctx *c, void *p);
+// Workspace of one call: a spare block of the context that fits (at most a
+// quarter larger), else a new allocation; ws_put hands it back for reuse on
+// the context's stream (work queued on it is ordered before any reuse).
+pp_status ws_get(pp_ctx *c, void **p, size_t bytes);
+void ws_put(pp_ctx *c, void *p);
+// Free the spare blocks (pp_trim).
+void ws_trim(pp_ctx *c);
 pp_status check_launch(pp_ctx *c);
 pp_status step(pp_ctx *c, const ppk::StepArgs &s);
 pp_status op_apply(pp_ctx *c, const pp_poly *p, const void *x, void *y);

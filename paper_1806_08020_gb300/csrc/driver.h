@@ -43,10 +43,10 @@ struct Driver {
 
     ~Driver() {
         cudaStreamSynchronize(c->stream);
-        for (void *q : mine) dfree(c, q);
+        for (void *q : mine) ws_put(c, q);
     }
     pp_status alloc(void **p, size_t bytes) {
-        pp_status st = dmalloc(c, p, bytes);
+        pp_status st = ws_get(c, p, bytes);
         if (st >= 0) mine.push_back(*p);
         return st;
     }

@@ -56,6 +56,7 @@ _SIGS = {
     "pp_last_error": (C.c_char_p, []),
     "pp_create": (C.c_int, [C.POINTER(_P), C.c_int64, _I64, C.POINTER(C.c_int32), _D, C.POINTER(pp_opts)]),
     "pp_destroy": (None, [_P]),
+    "pp_trim": (C.c_int, [_P]),
     "pp_matrix_info": (C.c_int, [_P, _D, _D]),
     "pp_debug_stall_sweeps": (C.c_int, [_P, C.c_int]),
     "pp_format_info": (C.c_int, [_P, _I, _I, _I, _I, _I, _I64]),
@@ -213,6 +214,11 @@ def pp_format_info(ctx: Context) -> dict:
 def pp_debug_stall_sweeps(ctx: Context, count: int) -> None:
     """Test support: the next `count` staged CGS2 steps issue no copies (their waits run out)."""
     _check(LIB.pp_debug_stall_sweeps(ctx.handle, int(count)))
+
+
+def pp_trim(ctx: Context) -> None:
+    """Free the device workspace the context keeps between calls."""
+    _check(LIB.pp_trim(ctx.handle))
 
 
 def pp_launch_count(ctx: Context) -> int:

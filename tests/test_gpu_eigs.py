@@ -238,3 +238,29 @@ def test_build_poly_on_dirty_device_memory():
         assert got.size == ref.roots.size
         for z in ref.roots:
             assert np.min(np.abs(got - z)) <= 1e-8 * abs(z)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_repeated_solves_reuse_workspace(precision):
+    """Solves repeated on one context (its workspace reused from the previous
+    call, a workspace of another size in between, and after pp_trim) give the
+    same bits as the first."""
+    from paper_1806_08020_gb300 import pp
+    cfg = inputs.plain_small()
+    A = cfg["A"]
+    ctx = pp.pp_create(A, precision=precision)
+    b, v0 = inputs.start_vector(A.n, 5, 0), inputs.start_vector(A.n, 5, 1)
+
+    def solve(m, k):
+        poly = pp.pp_build_poly(ctx, 10, b)
+        return pp.pp_poly_roots(poly), pp.pp_eigs(ctx, poly, 8, m, k, 1e-8, v0)
+
+    r0, e0 = solve(30, 15)
+    runs = [solve(30, 15), solve(40, 20), solve(30, 15)]
+    pp.pp_trim(ctx)
+    runs.append(solve(30, 15))
+    for i, (r, e) in enumerate(runs):
+        if i == 1:
+            assert e.status == 0
+            continue
+        assert np.array_equal(r, r0) and np.array_equal(e.lam, e0.lam) and np.array_equal(e.resid, e0.resid), i
