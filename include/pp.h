@@ -163,7 +163,8 @@ pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bit
 
 /*
  * pp_build_poly — GMRES polynomial of degree d (Section 2 box, step 1):
- * one GMRES(d) cycle on A - sigma I from b (host, n doubles), harmonic Ritz
+ * one GMRES(d) cycle on A - sigma I from b (n doubles, host or device memory:
+ * a device vector is normalised on the device, with no copy), harmonic Ritz
  * values as roots (step 1(b)), modified Leja order (step 1(c)), then extra
  * copies of roots with large pof when opts.add_roots (Section 7 box).
  * The Arnoldi process runs on the GPU (SpMV + CGS2); the d x d dense steps run
@@ -176,7 +177,7 @@ pp_status pp_build_poly(pp_ctx *ctx, int d, const double *b, pp_poly **out);
  * pp_build_poly_two — the polynomial determined by two starting vectors
  * (Section 5 box): one GMRES(d) cycle on blockdiag(A, A) (A - sigma I with a
  * shift) from [b1; b2], each half scaled to norm 1/sqrt(2), then roots as in
- * pp_build_poly.  b1, b2: host, n doubles each.  Guards against a skewed
+ * pp_build_poly.  b1, b2: n doubles each, host or device.  Guards against a skewed
  * start vector.  Requires 1 <= d <= 127.  Returns PP_OK or PP_EBREAKDOWN.
  */
 pp_status pp_build_poly_two(pp_ctx *ctx, int d, const double *b1, const double *b2, pp_poly **out);
@@ -188,7 +189,7 @@ pp_status pp_build_poly_two(pp_ctx *ctx, int d, const double *b1, const double *
  * for A of the k Ritz vectors nearest 1 (|mu_1| <= ... <= |mu_nev| < the other
  * k - nev).  If it fails, rebuild from A b (damping, Section 6.1); if that
  * fails too, halve d until it holds or d = 1.  With a shift (smallest real
- * part targets) A stands for A - sigma I throughout.  b: host, n doubles.
+ * part targets) A stands for A - sigma I throughout.  b: n doubles, host or device.
  * Outputs: the polynomial, the degree finally used (before added roots),
  * damped (1 when built from A b) and ideal (1 when the condition holds for
  * it; 0 only when d reached 1 without it).  Requires 1 <= nev < k <= m <= 127,
@@ -251,7 +252,8 @@ pp_status pp_apply_host(const pp_poly *p, const double *x, double *y);
  * cycle on A itself: ||A y_j - mu_j y_j|| <= rtol * ||A||_1 with mu_j the
  * Rayleigh quotient of the unit Ritz vector y_j.
  * p == NULL runs plain Arnoldi(m, k) on A - sigma I.
- * v0: host start vector (n doubles), NULL = e_1 + ... (deterministic ones).
+ * v0: start vector (n doubles, host or device memory; a device vector is
+ * normalised on the device), NULL = e_1 + ... (deterministic ones).
  * Outputs (capacity nev + 1 slots; a conjugate pair takes two slots and the
  * wanted set grows by one when nev would split a pair):
  *   lam_re, lam_im: eigenvalue estimates, sorted by the target;

@@ -388,6 +388,46 @@ pp_status upload_vec(pp_ctx *c, const double *h, double s, void *d) {
     return PP_OK;
 }
 
+bool on_device(const void *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+pp_status load_unit(pp_ctx *c, const double *x, ppk::Prec pr, void *dst, double *beta, const char *what) {
+    const int64_t n = c->n;
+    double nb = 0;
+    if (!on_device(x)) {
+        for (int64_t i = 0; i < n; ++i) nb += x[i] * x[i];
+        nb = std::sqrt(nb);
+        if (!(nb > 0) || !std::isfinite(nb)) return pp_fail(PP_EINVAL, "%s: start vector is zero or not finite", what);
+        if (pr == ppk::BF16) {  // through the FP32 scratch
+            CKS(upload_vec(c, x, 1.0 / nb, c->vec[8]));
+            ppk::launch_convert(ppk::F32, ppk::BF16, (int)n, c->vec[8], dst, c->stream);
+            CKS(check_launch(c));
+        } else {
+            CKS(upload_vec(c, x, 1.0 / nb, dst));
+        }
+        *beta = nb;
+        return PP_OK;
+    }
+    double *nrm2 = c->d_small + 3968;
+    ppk::launch_norm2((int)n, x, c->d_part, c->d_ticket, nrm2, c->stream);
+    CKS(check_launch(c));
+    double h = 0;
+    CK(cudaMemcpyAsync(&h, nrm2, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    nb = std::sqrt(h);
+    if (!(nb > 0) || !std::isfinite(nb)) return pp_fail(PP_EINVAL, "%s: start vector is zero or not finite", what);
+    ppk::launch_unit_into(pr, (int)n, x, nrm2, dst, c->stream);
+    CKS(check_launch(c));
+    *beta = nb;
+    return PP_OK;
+}
+
 pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vector<double> &out, ppk::Prec pr) {
     out.resize((size_t)c->n * cols);
     if (pr == ppk::F64) {
@@ -433,19 +473,14 @@ pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, 
     }
     mine.push_back(dH);
     double beta = 0;
-    for (int64_t i = 0; i < c->n; ++i) beta += b[i] * b[i];
-    beta = std::sqrt(beta);
-    if (!(beta > 0) || !std::isfinite(beta)) {
-        cleanup();
-        return pp_fail(PP_EINVAL, "start vector is zero or not finite");
-    }
     std::vector<double> H((size_t)(d + 1) * d, 0.0);
     // CGS2 writes rows 0..j+1 of column j only; the rest of H must read as zero
     if (cudaMemsetAsync(dH, 0, (size_t)(d + 1) * d * 8, c->stream) != cudaSuccess) {
         cleanup();
         return pp_fail(PP_ECUDA, "build: memset failed");
     }
-    if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)c->n) * 130)) < 0 || (st = upload_vec(c, b, 1.0 / beta, V)) < 0 ||
+    if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)c->n) * 130)) < 0 ||
+        (st = load_unit(c, b, c->A.prec, V, &beta, "build")) < 0 ||
         (st = arnoldi_extend(c, nullptr, tau_of, c->A.prec, V, ldv, dH, d + 1, 0, d, c->vec[6], nullptr,
                              nullptr)) < 0) {
         cleanup();
@@ -1106,6 +1141,16 @@ static pp_status build_roots_two(pp_ctx *c, int d, const double *b1, const doubl
     if (d < 1 || d > 127) return pp_fail(PP_EINVAL, "degree must be in [1, 127] (got %d)", d);
     const int64_t n = c->n, n2 = 2 * n;
     if (d >= n2) return pp_fail(PP_EINVAL, "degree %d must be below 2n", d);
+    std::vector<double> h1, h2;  // host copies of device start vectors
+    if (on_device(b1) || on_device(b2)) {
+        h1.resize(n);
+        h2.resize(n);
+        CK(cudaMemcpyAsync(h1.data(), b1, (size_t)n * 8, cudaMemcpyDefault, c->stream));
+        CK(cudaMemcpyAsync(h2.data(), b2, (size_t)n * 8, cudaMemcpyDefault, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        b1 = h1.data();
+        b2 = h2.data();
+    }
     double s1 = 0, s2 = 0;
     for (int64_t i = 0; i < n; ++i) {
         s1 += b1[i] * b1[i];

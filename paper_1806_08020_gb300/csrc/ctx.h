@@ -150,6 +150,13 @@ pp_status arnoldi_extend(pp_ctx *c, const pp_poly *p, const pp_poly *tau_of, ppk
                          std::vector<std::pair<int, int>> *marks);
 void accumulate_times(Timers &tm, std::vector<std::pair<int, int>> &marks, double &t_apply, double &t_orth);
 pp_status upload_vec(pp_ctx *c, const double *h, double s, void *d);
+// True for device (or managed) memory, false for host memory.
+bool on_device(const void *p);
+// The unit vector x / ||x|| stored into dst in precision pr (F64 or F32 as the
+// context's vectors, or BF16); x: n FP64 values in host or device memory
+// (the norm is summed on the host, or on the device in a fixed order).
+// beta = ||x||; PP_EINVAL when x is zero or not finite.
+pp_status load_unit(pp_ctx *c, const double *x, ppk::Prec pr, void *dst, double *beta, const char *what);
 pp_status download_vecs(pp_ctx *c, const void *d, int64_t ld, int cols, std::vector<double> &out, ppk::Prec pr);
 // PP_ETIMEOUT (and the error word and reduction ticket cleared) when a
 // TMA-staged sweep gave up waiting since the last check; synchronises the stream.

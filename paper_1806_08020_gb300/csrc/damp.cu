@@ -29,16 +29,7 @@ pp_status first_cycle_ideal(pp_ctx *c, const pp_poly *p, const double *b, int m,
     CKS(D.alloc((void **)&dH, (size_t)ldh * m * 8));
     CKS(D.alloc_test_buffers(bpr != ppk::F64));
     double nb = 0;
-    for (int64_t i = 0; i < n; ++i) nb += b[i] * b[i];
-    nb = std::sqrt(nb);
-    if (!(nb > 0) || !std::isfinite(nb)) return pp_fail(PP_EINVAL, "damping: start vector is zero or not finite");
-    if (bpr == ppk::BF16) {
-        CKS(upload_vec(c, b, 1.0 / nb, c->vec[8]));
-        ppk::launch_convert(ppk::F32, ppk::BF16, (int)n, c->vec[8], V, c->stream);
-        CKS(check_launch(c));
-    } else {
-        CKS(upload_vec(c, b, 1.0 / nb, V));
-    }
+    CKS(load_unit(c, b, bpr, V, &nb, "damping"));
     CK(cudaMemsetAsync(dH, 0, (size_t)ldh * m * 8, c->stream));
     void *W = (p && p->inner) ? c->vec[0] : c->vec[6];
     CKS(arnoldi_extend(c, p, nullptr, bpr, V, ldv, dH, ldh, 0, m, W, nullptr, nullptr));
@@ -77,7 +68,7 @@ pp_status damp_start(pp_ctx *c, const double *b, std::vector<double> &out) {
     a.plain = 1;
     a.sigma = c->sigma;
     out.assign(n, 0.0);
-    cudaError_t e = cudaMemcpyAsync(x, b, (size_t)n * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = cudaMemcpyAsync(x, b, (size_t)n * 8, cudaMemcpyDefault, c->stream);  // b: host or device
     if (e == cudaSuccess) {
         ppk::launch_step(c->A64, a, c->stream);
         e = cudaGetLastError();
@@ -98,7 +89,9 @@ extern "C" pp_status pp_build_poly_damped(pp_ctx *c, int d, const double *b, int
     if (!c || !b || !out || d < 1 || nev < 1 || k <= nev || m < k || m > 127 || m >= c->n)
         return pp_fail(PP_EINVAL, "pp_build_poly_damped: need d >= 1, 1 <= nev < k <= m <= 127, m < n");
     *out = nullptr;
-    std::vector<double> start(b, b + c->n);
+    std::vector<double> start(c->n);  // b, or A b once damped (host copy; b may be on the device)
+    CK(cudaMemcpyAsync(start.data(), b, (size_t)c->n * 8, cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     bool dmp = false;
     for (;;) {
         pp_poly *p = nullptr;

@@ -43,19 +43,13 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
     CKS(D.alloc(&V2, (size_t)ldv * (m + 1) * esz));
     CKS(D.alloc_test_buffers(mixed));
     CKS(D.alloc((void **)&dH, (size_t)ldh * m * 8));
-    // start vector
-    std::vector<double> v0h(n, 1.0);
-    if (v0) std::copy(v0, v0 + n, v0h.begin());
+    // start vector (host or device; NULL: all ones)
     double nv = 0;
-    for (double x : v0h) nv += x * x;
-    nv = std::sqrt(nv);
-    if (!(nv > 0) || !std::isfinite(nv)) return pp_fail(PP_EINVAL, "pp_eigs: start vector is zero or not finite");
-    if (bpr == ppk::BF16) {  // through the FP32 scratch
-        CKS(upload_vec(c, v0h.data(), 1.0 / nv, c->vec[8]));
-        ppk::launch_convert(ppk::F32, ppk::BF16, (int)n, c->vec[8], V, c->stream);
-        CKS(check_launch(c));
+    if (v0) {
+        CKS(load_unit(c, v0, bpr, V, &nv, "pp_eigs"));
     } else {
-        CKS(upload_vec(c, v0h.data(), 1.0 / nv, V));
+        std::vector<double> ones(n, 1.0);
+        CKS(load_unit(c, ones.data(), bpr, V, &nv, "pp_eigs"));
     }
     CK(cudaMemsetAsync(dH, 0, (size_t)ldh * m * 8, c->stream));
     S.dots += 1;

@@ -551,6 +551,44 @@ __device__ __forceinline__ __nv_bfloat16 store_as<__nv_bfloat16, float>(float v)
     return __float2bfloat16_rn(v);
 }
 
+// ||x||^2 of an FP64 vector into out[0]: per-block partials, summed in block
+// order by the last block (the same bits on every run).
+__global__ void __launch_bounds__(kThreads) k_norm2(int n, const double *x, double *part, unsigned *ticket,
+                                                    double *out) {
+    __shared__ double wsum[kWarps];
+    double s = 0;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) s = fma(x[i], x[i], s);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0;
+        for (int w = 0; w < kWarps; ++w) b += wsum[w];
+        part[blockIdx.x] = b;
+    }
+    if (!last_block(ticket)) return;
+    reduce_partials(part, gridDim.x, 1, out);
+    __syncthreads();
+    if (threadIdx.x == 0) *ticket = 0;
+}
+
+// dst = x / sqrt(nrm2[0]) in the basis precision; the FP64 product is rounded
+// to FP32 first for FP32 and BF16 (as a host vector uploaded to FP32 storage).
+template <typename T>
+__global__ void k_unit_into(int n, const double *x, const double *nrm2, T *dst) {
+    const double sc = 1.0 / sqrt(*nrm2);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = x[i] * sc;
+        if constexpr (std::is_same<T, double>::value)
+            dst[i] = v;
+        else if constexpr (std::is_same<T, float>::value)
+            dst[i] = (float)v;
+        else
+            dst[i] = __float2bfloat16_rn((float)v);
+    }
+}
+
 // A BF16 basis column: out = bf16(w * scal) (w is the FP32 orthogonalised vector).
 __global__ void k_scale_bf16(int n, const float *w, const double *scal, __nv_bfloat16 *out) {
     const float sc = (float)*scal;
@@ -812,6 +850,23 @@ void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st) {
         cgs_dispatch<float>(a, grid_cap, st);
     else
         cgs_dispatch<__nv_bfloat16>(a, grid_cap, st);
+}
+
+void launch_norm2(int n, const double *x, double *part, unsigned *ticket, double *out, cudaStream_t st) {
+    int g = (n + kThreads - 1) / kThreads;
+    if (g > num_sms() * 4) g = num_sms() * 4;
+    if (g < 1) g = 1;
+    k_norm2<<<g, kThreads, 0, st>>>(n, x, part, ticket, out);
+}
+
+void launch_unit_into(Prec p, int n, const double *x, const double *nrm2, void *dst, cudaStream_t st) {
+    const int g = num_sms() * 4;
+    if (p == F64)
+        k_unit_into<double><<<g, kThreads, 0, st>>>(n, x, nrm2, (double *)dst);
+    else if (p == F32)
+        k_unit_into<float><<<g, kThreads, 0, st>>>(n, x, nrm2, (float *)dst);
+    else
+        k_unit_into<__nv_bfloat16><<<g, kThreads, 0, st>>>(n, x, nrm2, (__nv_bfloat16 *)dst);
 }
 
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st) {

@@ -134,6 +134,11 @@ void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st);
 // as launch_cgs with at most grid_cap blocks (the partial sums need grid_cap * (j+1) doubles)
 void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st);
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st);
+// out[0] = ||x||^2 (FP64 x on the device; part holds one double per block, at
+// most 4 blocks per SM; ticket is zero before and after).
+void launch_norm2(int n, const double *x, double *part, unsigned *ticket, double *out, cudaStream_t st);
+// dst = x / sqrt(nrm2[0]) stored in precision p.
+void launch_unit_into(Prec p, int n, const double *x, const double *nrm2, void *dst, cudaStream_t st);
 // out (BF16, n) = w * scal (w FP32): the new column of a BF16 basis
 void launch_scale_bf16(int n, const float *w, const double *scal, void *out, cudaStream_t st);
 

@@ -132,6 +132,22 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _vec_in(a, n: int):
+    """(keep-alive object, double*) for an input vector of n FP64 values: a CUDA
+    array (anything with __cuda_array_interface__, e.g. a torch tensor on the
+    GPU: float64, contiguous) is passed as its device pointer, anything else as
+    a host copy."""
+    cai = getattr(a, "__cuda_array_interface__", None)
+    if cai is not None:
+        if cai["typestr"] != "<f8" or tuple(cai["shape"]) not in ((n,), (n, 1)) or cai.get("strides") not in (None, (8,)):
+            raise ValueError("device start vector: need n contiguous float64 values")
+        return a, C.cast(C.c_void_p(int(cai["data"][0])), _D)
+    h = _f64(a)
+    if h.size != n:
+        raise ValueError(f"start vector: need {n} values, got {h.size}")
+    return h, _dp(h)
+
+
 # ---------------------------------------------------------------------------
 # Handles
 # ---------------------------------------------------------------------------
@@ -226,35 +242,36 @@ def pp_launch_count(ctx: Context) -> int:
 
 
 def pp_build_poly(ctx: Context, d: int, b) -> Poly:
-    b = _f64(b)
+    """GMRES polynomial of degree d from b (host array or float64 CUDA array)."""
+    b, bp = _vec_in(b, ctx.n)
     h = C.c_void_p()
-    st = _check(LIB.pp_build_poly(ctx.handle, int(d), _dp(b), C.byref(h)), allow=(PP_OK, PP_EBREAKDOWN))
+    st = _check(LIB.pp_build_poly(ctx.handle, int(d), bp, C.byref(h)), allow=(PP_OK, PP_EBREAKDOWN))
     return Poly(h.value, ctx, st)
 
 
 def pp_build_poly_two(ctx: Context, d: int, b1, b2) -> Poly:
     """Polynomial from two starting vectors (Section 5 box)."""
-    b1, b2 = _f64(b1), _f64(b2)
+    (b1, p1), (b2, p2) = _vec_in(b1, ctx.n), _vec_in(b2, ctx.n)
     h = C.c_void_p()
-    st = _check(LIB.pp_build_poly_two(ctx.handle, int(d), _dp(b1), _dp(b2), C.byref(h)),
+    st = _check(LIB.pp_build_poly_two(ctx.handle, int(d), p1, p2, C.byref(h)),
                 allow=(PP_OK, PP_EBREAKDOWN))
     return Poly(h.value, ctx, st)
 
 
 def pp_build_poly_damped(ctx: Context, d: int, b, m: int, k: int, nev: int) -> tuple[Poly, dict]:
     """Damping heuristic (Section 6.3 box); returns the polynomial and degree / damped / ideal."""
-    b = _f64(b)
+    b, bp = _vec_in(b, ctx.n)
     h = C.c_void_p()
     deg, dmp, ide = C.c_int(), C.c_int(), C.c_int()
-    st = _check(LIB.pp_build_poly_damped(ctx.handle, int(d), _dp(b), int(m), int(k), int(nev), C.byref(h),
+    st = _check(LIB.pp_build_poly_damped(ctx.handle, int(d), bp, int(m), int(k), int(nev), C.byref(h),
                                          C.byref(deg), C.byref(dmp), C.byref(ide)), allow=(PP_OK, PP_EBREAKDOWN))
     return Poly(h.value, ctx, st), {"degree": deg.value, "damped": bool(dmp.value), "ideal": bool(ide.value)}
 
 
 def pp_build_poly2(ctx: Context, d1: int, d2: int, b) -> Poly:
-    b = _f64(b)
+    b, bp = _vec_in(b, ctx.n)
     h = C.c_void_p()
-    st = _check(LIB.pp_build_poly2(ctx.handle, int(d1), int(d2), _dp(b), C.byref(h)), allow=(PP_OK, PP_EBREAKDOWN))
+    st = _check(LIB.pp_build_poly2(ctx.handle, int(d1), int(d2), bp, C.byref(h)), allow=(PP_OK, PP_EBREAKDOWN))
     return Poly(h.value, ctx, st)
 
 
@@ -337,11 +354,11 @@ def pp_eigs(ctx: Context, p: Poly | None, nev: int, m: int, k: int, rtol: float,
     cap = nev + 1
     lre, lim, res = np.zeros(cap), np.zeros(cap), np.zeros(cap)
     X = np.zeros((cap, n)) if want_vectors else None
-    v0a = _f64(v0) if v0 is not None else None
+    v0a, v0p = _vec_in(v0, n) if v0 is not None else (None, None)
     nout = C.c_int()
     st = pp_stats()
     status = _check(LIB.pp_eigs(ctx.handle, p.handle if p is not None else None, int(nev), int(m), int(k),
-                                float(rtol), _dp(v0a) if v0a is not None else None, _dp(lre), _dp(lim),
+                                float(rtol), v0p, _dp(lre), _dp(lim),
                                 _dp(X) if X is not None else None, _dp(res), C.byref(nout), C.byref(st)),
                     allow=(PP_OK, PP_ENOTCONV))
     k_ = nout.value

@@ -264,3 +264,34 @@ def test_repeated_solves_reuse_workspace(precision):
             assert e.status == 0
             continue
         assert np.array_equal(r, r0) and np.array_equal(e.lam, e0.lam) and np.array_equal(e.resid, e0.resid), i
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_device_start_vectors(precision):
+    """Start vectors passed as device arrays (normalised on the device) give the
+    solve of the same vectors passed from the host: the unit start vectors
+    differ only by the rounding of ||b|| (summed in another order), so the roots
+    and eigenvalues agree to a few units of rounding growth, and the device path
+    is deterministic (the same bits on a second call)."""
+    import torch
+    from paper_1806_08020_gb300 import pp
+    cfg = inputs.plain_small()
+    A = cfg["A"]
+    ctx = pp.pp_create(A, precision=precision)
+    b, v0 = inputs.start_vector(A.n, 7, 0), inputs.start_vector(A.n, 7, 1)
+    bd, vd = torch.from_numpy(b).cuda(), torch.from_numpy(v0).cuda()
+    ph, pd, pd2 = pp.pp_build_poly(ctx, 10, b), pp.pp_build_poly(ctx, 10, bd), pp.pp_build_poly(ctx, 10, bd)
+    rh, rd = np.sort_complex(pp.pp_poly_roots(ph)), np.sort_complex(pp.pp_poly_roots(pd))
+    assert np.array_equal(rd, np.sort_complex(pp.pp_poly_roots(pd2)))
+    if precision == 0:  # FP32 roots move with the O(u32) change of the start vector's rounding
+        assert np.max(np.abs(rh - rd) / np.abs(rh)) < 1e-10
+    eh = pp.pp_eigs(ctx, ph, 8, 30, 15, 1e-8, v0)
+    ed = pp.pp_eigs(ctx, ph, 8, 30, 15, 1e-8, vd)
+    assert eh.status == 0 and ed.status == 0
+    # both converged to residual 1e-8 ||A||_1 on a mildly non-normal matrix
+    lh, ld = np.sort_complex(eh.lam), np.sort_complex(ed.lam)
+    assert np.max(np.abs(lh - ld) / np.abs(lh)) <= 1e-6
+    with pytest.raises(pp.PPError):
+        pp.pp_build_poly(ctx, 10, torch.zeros(A.n, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        pp.pp_build_poly(ctx, 10, bd.float())
