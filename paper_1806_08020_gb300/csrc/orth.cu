@@ -39,8 +39,8 @@ __device__ bool last_block(unsigned *ticket, unsigned nblocks) {
 __device__ bool last_block(unsigned *ticket) { return last_block(ticket, gridDim.x * gridDim.y); }
 
 __device__ void reduce_partials(const double *part, int nblocks, int nout, double *out) {
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int o = warp; o < nout; o += kWarps) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int o = warp; o < nout; o += nw) {
         double s = 0;
         for (int b = lane; b < nblocks; b += 32) s += __ldcg(part + (size_t)b * nout + o);
 #pragma unroll
@@ -58,13 +58,14 @@ constexpr int kQ = kRows / 32;
 
 // Per-block partial sums of a sweep, then the last block's reduction and (mode
 // 2) the Hessenberg column.  acc[cc] is the block-local projection on column
-// warp + kWarps cc; nrm the squared norm of the updated vector's rows.
-template <int CPW>
+// warp + NW cc (NW warps per block); nrm the squared norm of the updated
+// vector's rows.
+template <int CPW, int NW = kWarps>
 __device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, const double (&acc)[CPW],
                                            double nrm) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const int j = a.j;
-    __shared__ double nrm_sh[kWarps];
+    __shared__ double nrm_sh[NW];
     const int nout = (a.mode == 0) ? j : (a.mode == 1 ? j + 1 : 1);
     double *part = a.part + (size_t)bid * nout;
     if (a.mode != 2) {
@@ -73,7 +74,7 @@ __device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, 
             double s = acc[cc];
 #pragma unroll
             for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            int c = warp + kWarps * cc;
+            int c = warp + NW * cc;
             if (lane == 0 && c < j) part[c] = s;
         }
     }
@@ -84,7 +85,7 @@ __device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, 
         __syncthreads();
         if (tid == 0) {
             double s = 0;
-            for (int ww = 0; ww < kWarps; ++ww) s += nrm_sh[ww];
+            for (int ww = 0; ww < NW; ++ww) s += nrm_sh[ww];
             part[a.mode == 1 ? j : 0] = s;
         }
     }
@@ -96,7 +97,7 @@ __device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, 
         __threadfence_block();
         __syncthreads();
         double nn = sqrt(a.out[0]);
-        for (int c = tid; c < j; c += kThreads) a.hcol[c] = a.h1[c] + a.h[c];
+        for (int c = tid; c < j; c += NW * 32) a.hcol[c] = a.h1[c] + a.h[c];
         if (tid == 0) {
             a.hcol[j] = nn;
             a.scal[0] = nn > 0 ? 1.0 / nn : 0.0;
@@ -105,19 +106,22 @@ __device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, 
 }
 
 // The sweep of block `bid` out of `nblk` blocks working on an FP64 basis:
-// FP64 throughout.
-template <int CPW>
+// FP64 throughout.  NW warps per block: warp w owns columns w + NW cc.  Four
+// warps (the default for bases of up to 52 columns) keep the column slots
+// within 3 of j and the cross-warp row sums at four terms; the FP64 pipe is
+// the bound, and both cost FP64 instructions.
+template <int CPW, int NW>
 __device__ __forceinline__ void cgs_body_f64(const CgsArgs &a, int bid, int nblk) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const double *V = (const double *)a.V;
     const double *w = (const double *)a.w;
     double *wout = (double *)a.wout;
     const int j = a.j, n = a.n;
-    __shared__ double red[kWarps][kRows];
+    __shared__ double red[NW][kRows];
     __shared__ double wsh[kRows];
-    __shared__ double hs[8 * CPW];
+    __shared__ double hs[NW * CPW];
     if (a.mode != 0)
-        for (int c = tid; c < j; c += kThreads) hs[c] = a.h[c];
+        for (int c = tid; c < j; c += NW * 32) hs[c] = a.h[c];
     __syncthreads();
     double acc[CPW];
 #pragma unroll
@@ -129,7 +133,7 @@ __device__ __forceinline__ void cgs_body_f64(const CgsArgs &a, int bid, int nblk
         double vv[CPW][kQ];
 #pragma unroll
         for (int cc = 0; cc < CPW; ++cc) {
-            int c = warp + kWarps * cc;
+            int c = warp + NW * cc;
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
                 int row = r0 + lane + 32 * q;
@@ -145,7 +149,7 @@ __device__ __forceinline__ void cgs_body_f64(const CgsArgs &a, int bid, int nblk
             }
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc)
-                if (warp + kWarps * cc < j)  // warp-uniform: no FMAs on columns past j
+                if (warp + NW * cc < j)  // warp-uniform: no FMAs on columns past j
 #pragma unroll
                     for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wv[q], acc[cc]);
             continue;
@@ -156,7 +160,7 @@ __device__ __forceinline__ void cgs_body_f64(const CgsArgs &a, int bid, int nblk
             double s = 0;
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc) {
-                int c = warp + kWarps * cc;
+                int c = warp + NW * cc;
                 if (c < j) s = fma(vv[cc][q], hs[c], s);
             }
             red[warp][lane + 32 * q] = s;
@@ -168,7 +172,7 @@ __device__ __forceinline__ void cgs_body_f64(const CgsArgs &a, int bid, int nblk
             if (row < n) {
                 double s = 0;
 #pragma unroll
-                for (int ww = 0; ww < kWarps; ++ww) s += red[ww][tid];
+                for (int ww = 0; ww < NW; ++ww) s += red[ww][tid];
                 v = __ldg(w + row) - s;
                 wout[row] = v;
                 nrm = fma(v, v, nrm);
@@ -179,12 +183,12 @@ __device__ __forceinline__ void cgs_body_f64(const CgsArgs &a, int bid, int nblk
         if (a.mode == 1) {
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc)
-                if (warp + kWarps * cc < j)
+                if (warp + NW * cc < j)
 #pragma unroll
                     for (int q = 0; q < kQ; ++q) acc[cc] = fma(vv[cc][q], wsh[lane + 32 * q], acc[cc]);
         }
     }
-    cgs_finish<CPW>(a, bid, nblk, acc, nrm);
+    cgs_finish<CPW, NW>(a, bid, nblk, acc, nrm);
 }
 
 // One term of the compensated dot product Dot2 (Ogita, Rump and Oishi,
@@ -292,17 +296,19 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
     cgs_finish<CPW>(a, bid, nblk, acc, nrm);
 }
 
-template <typename T, int CPW>
+template <typename T, int CPW, int NW>
 __device__ __forceinline__ void cgs_body(const CgsArgs &a, int bid, int nblk) {
-    if constexpr (sizeof(T) == 8)
-        cgs_body_f64<CPW>(a, bid, nblk);
-    else
+    if constexpr (sizeof(T) == 8) {
+        cgs_body_f64<CPW, NW>(a, bid, nblk);
+    } else {
+        static_assert(NW == kWarps, "FP32 and BF16 sweeps run eight warps per block");
         cgs_body_f32<T, CPW>(a, bid, nblk);
+    }
 }
 
-template <typename T, int CPW>
-__global__ void __launch_bounds__(kThreads) k_cgs(CgsArgs a) {
-    cgs_body<T, CPW>(a, blockIdx.x, gridDim.x);
+template <typename T, int CPW, int NW>
+__global__ void __launch_bounds__(NW * 32) k_cgs(CgsArgs a) {
+    cgs_body<T, CPW, NW>(a, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -474,9 +480,9 @@ __device__ __forceinline__ int find_instance(const BatchCgsInst *ci, int count, 
     return lo;
 }
 
-template <typename T, int CPW>
-__global__ void __launch_bounds__(kThreads) k_cgs_batch(const BatchCgsInst *ci, int count, const int *lo,
-                                                        const int *hi, int mode, int jj) {
+template <typename T, int CPW, int NW>
+__global__ void __launch_bounds__(NW * 32) k_cgs_batch(const BatchCgsInst *ci, int count, const int *lo,
+                                                       const int *hi, int mode, int jj) {
     const int i = find_instance(ci, count, blockIdx.x);
     if (jj < lo[i] || jj >= hi[i]) return;
     const BatchCgsInst &I = ci[i];
@@ -503,7 +509,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs_batch(const BatchCgsInst *ci, 
         a.hcol = I.H + (size_t)jj * I.ldh;
         a.scal = I.scal;
     }
-    cgs_body<T, CPW>(a, blockIdx.x - I.blk0, I.nblk);
+    cgs_body<T, CPW, NW>(a, blockIdx.x - I.blk0, I.nblk);
 }
 
 template <typename T>
@@ -692,21 +698,24 @@ __global__ void __launch_bounds__(kThreads) k_coldots(ColDotArgs a) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// The most blocks any CGS2 sweep launches (sizes the partial-sum buffers).
 int cgs_grid(int n) {
     int tiles = (n + kRows - 1) / kRows;
-    int g = num_sms() * 4;
+    int g = num_sms() * 8;
     return tiles < g ? tiles : g;
 }
 
-// Blocks of a CGS pass: one wave of resident blocks (at most 4 per SM, which
-// bounds the partial-sum buffer), never more than there are tiles.
-template <typename T, int CPW>
+// Blocks of a CGS pass: one wave of resident blocks (at most 8 per SM of four
+// warps or 4 of eight warps, which bounds the partial-sum buffer), never more
+// than there are tiles.
+template <typename T, int CPW, int NW>
 static int resident_grid(int n, int cap) {
     static int per_sm = 0;  // one per instantiation
     if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs<T, CPW>, kThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs<T, CPW, NW>, NW * 32, 0);
+        const int most = 32 / NW;
         if (per_sm < 1) per_sm = 1;
-        if (per_sm > 4) per_sm = 4;
+        if (per_sm > most) per_sm = most;
     }
     int tiles = (n + kRows - 1) / kRows;
     int g = per_sm * num_sms();
@@ -784,6 +793,21 @@ static void with_cpw(int cpw, F &&f) {
     }
 }
 
+// f(std::integral_constant<int, C>) with C = max(cpw, 1) for cpw <= CMAX.
+template <int CMAX, typename F>
+static void with_cpw_exact(int cpw, F &&f) {
+    if constexpr (CMAX > 1) {
+        if (cpw < CMAX) {
+            with_cpw_exact<CMAX - 1>(cpw, f);
+            return;
+        }
+    }
+    f(std::integral_constant<int, CMAX>{});
+}
+
+// FP64 bases of up to kCgs4Cols columns take the four-warp sweeps.
+constexpr int kCgs4Cols = 52;
+
 template <typename T>
 static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
@@ -800,8 +824,16 @@ static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
         return;
         }
     }
+    if constexpr (sizeof(T) == 8) {
+        if (a.j <= kCgs4Cols) {
+            with_cpw_exact<kCgs4Cols / 4>((a.j + 3) / 4, [&](auto C) {
+                k_cgs<T, C.value, 4><<<resident_grid<T, C.value, 4>(a.n, cap), 128, 0, st>>>(a);
+            });
+            return;
+        }
+    }
     with_cpw((a.j + kWarps - 1) / kWarps, [&](auto C) {
-        k_cgs<T, C.value><<<resident_grid<T, C.value>(a.n, cap), kThreads, 0, st>>>(a);
+        k_cgs<T, C.value, kWarps><<<resident_grid<T, C.value, kWarps>(a.n, cap), kThreads, 0, st>>>(a);
     });
 }
 
@@ -820,11 +852,17 @@ void launch_scale_bf16(int n, const float *w, const double *scal, void *out, cud
 
 void launch_cgs_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int mode,
                       int jj, cudaStream_t st) {
+    if (p == F64 && jj + 1 <= kCgs4Cols) {
+        with_cpw_exact<kCgs4Cols / 4>((jj + 1 + 3) / 4, [&](auto C) {
+            k_cgs_batch<double, C.value, 4><<<nblocks, 128, 0, st>>>(ci, count, lo, hi, mode, jj);
+        });
+        return;
+    }
     with_cpw((jj + 1 + kWarps - 1) / kWarps, [&](auto C) {
         if (p == F64)
-            k_cgs_batch<double, C.value><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj);
+            k_cgs_batch<double, C.value, kWarps><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj);
         else
-            k_cgs_batch<float, C.value><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj);
+            k_cgs_batch<float, C.value, kWarps><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj);
     });
 }
 
