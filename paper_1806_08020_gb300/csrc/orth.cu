@@ -39,13 +39,48 @@ __device__ bool last_block(unsigned *ticket, unsigned nblocks) {
 __device__ bool last_block(unsigned *ticket) { return last_block(ticket, gridDim.x * gridDim.y); }
 
 __device__ void reduce_partials(const double *part, int nblocks, int nout, double *out) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int o = warp; o < nout; o += nw) {
+    // Run by every thread of the last block while the other SMs wait, so the
+    // loads are spread over the whole block and issued eight at a time: thread
+    // t sums output t % nout over the blocks t / nout, t / nout + S, ... (S =
+    // threads / nout slices), then thread o adds its output's S slice sums in
+    // slice order.  The order is fixed, so every run gives the same bits.
+    __shared__ double slice_sum[kThreads];
+    const int nt = blockDim.x, t = threadIdx.x;
+    if (nout > nt || nt > kThreads) {  // not taken by the sweeps here (nout <= j + 1 <= threads)
+        for (int o = t; o < nout; o += nt) {
+            double s = 0;
+            for (int b = 0; b < nblocks; ++b) s += __ldcg(part + (size_t)b * nout + o);
+            out[o] = s;
+        }
+        return;
+    }
+    const int S = nt / nout;
+    double acc = 0;
+    if (t < S * nout) {
+        const int o = t % nout;
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0, a6 = 0, a7 = 0;
+        int b = t / nout;
+        for (; b + 7 * S < nblocks; b += 8 * S) {
+            const double *p = part + (size_t)b * nout + o;
+            const size_t st = (size_t)S * nout;
+            a0 += __ldcg(p);
+            a1 += __ldcg(p + st);
+            a2 += __ldcg(p + 2 * st);
+            a3 += __ldcg(p + 3 * st);
+            a4 += __ldcg(p + 4 * st);
+            a5 += __ldcg(p + 5 * st);
+            a6 += __ldcg(p + 6 * st);
+            a7 += __ldcg(p + 7 * st);
+        }
+        for (; b < nblocks; b += S) a0 += __ldcg(part + (size_t)b * nout + o);
+        acc = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    }
+    slice_sum[t] = acc;
+    __syncthreads();
+    if (t < nout) {
         double s = 0;
-        for (int b = lane; b < nblocks; b += 32) s += __ldcg(part + (size_t)b * nout + o);
-#pragma unroll
-        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) out[o] = s;
+        for (int k = 0; k < S; ++k) s += slice_sum[k * nout + t];
+        out[t] = s;
     }
 }
 
