@@ -448,7 +448,7 @@ pp_status check_sweeps(pp_ctx *c) {
     CK(cudaStreamSynchronize(c->stream));
     if (!e) return PP_OK;
     CK(cudaMemsetAsync(c->err(), 0, sizeof(int), c->stream));
-    CK(cudaMemsetAsync(c->d_ticket, 0, 64, c->stream));
+    CK(cudaMemsetAsync(c->d_ticket, 0, ppk::kTicketWords * sizeof(unsigned), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return pp_fail(PP_ETIMEOUT, "CGS2 sweep: a bounded wait for staged basis tiles expired");
 }
@@ -479,7 +479,7 @@ pp_status build_roots(pp_ctx *c, int d, const double *b, const pp_poly *tau_of, 
         cleanup();
         return pp_fail(PP_ECUDA, "build: memset failed");
     }
-    if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)c->n) * 130)) < 0 ||
+    if ((st = ensure_part(c, ppk::cgs_part_doubles(ppk::cgs_grid((int)c->n)))) < 0 ||
         (st = load_unit(c, b, c->A.prec, V, &beta, "build")) < 0 ||
         (st = arnoldi_extend(c, nullptr, tau_of, c->A.prec, V, ldv, dH, d + 1, 0, d, c->vec[6], nullptr,
                              nullptr)) < 0) {
@@ -873,12 +873,12 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     // the small FP64 area holding the error word of the staged kernels
     for (int i = 0; i < 9; ++i)
         if ((st = dmalloc(c, &c->vec[i], (size_t)c->ldv() * c->esz)) < 0) return fail(st);
-    if ((st = dmalloc(c, (void **)&c->d_ticket, 64)) < 0 || (st = dmalloc(c, (void **)&c->d_small, 4096 * 8)) < 0)
+    if ((st = dmalloc(c, (void **)&c->d_ticket, ppk::kTicketWords * sizeof(unsigned))) < 0 || (st = dmalloc(c, (void **)&c->d_small, 4096 * 8)) < 0)
         return fail(st);
     // the tuner's vectors: a finite nonzero pattern (0x3f bytes: 0.49 in FP64, 0.75 in FP32)
     if (cudaMemsetAsync(c->vec[0], 0x3f, (size_t)c->ldv() * c->esz, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->vec[3], 0, (size_t)c->ldv() * c->esz, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->d_ticket, 0, 64, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_ticket, 0, ppk::kTicketWords * sizeof(unsigned), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->d_small, 0, 4096 * 8, c->stream) != cudaSuccess)
         return fail(pp_fail(PP_ECUDA, "pp_create: memset failed"));
     M.err = c->err();
@@ -1029,7 +1029,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     c->A64.fmt = 1;
     c->A64.csr = {(int)n, d_rowptr, d_col, d_val};
     if (pr == ppk::F64) c->A64 = M;
-    if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)n) * 130)) < 0) return fail(st);
+    if ((st = ensure_part(c, ppk::cgs_part_doubles(ppk::cgs_grid((int)n)))) < 0) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: setup kernels failed"));
     if (c->bprec != ppk::F64 && make_twin) {
         // FP64 twin on the same stream: the mixed-precision solve continues in FP64
@@ -1187,7 +1187,7 @@ static pp_status build_roots_two(pp_ctx *c, int d, const double *b1, const doubl
         return st;
     }
     mine.push_back(dH);
-    if ((st = ensure_part(c, (size_t)ppk::cgs_grid((int)n2) * 130)) < 0) {
+    if ((st = ensure_part(c, ppk::cgs_part_doubles(ppk::cgs_grid((int)n2)))) < 0) {
         cleanup();
         return st;
     }

@@ -61,7 +61,7 @@ struct Driver {
         CKS(alloc((void **)&dq, (size_t)4 * (wcap + 1) * 8));
         CKS(alloc((void **)&dmu, (size_t)3 * (wcap + 1) * 8));
         CKS(alloc((void **)&dpartner, (size_t)(wcap + 1) * 4));
-        CKS(ensure_part(c, std::max((size_t)ppk::cgs_grid((int)n) * 130, (size_t)(wcap + 1) * 3 * 1024)));
+        CKS(ensure_part(c, std::max(ppk::cgs_part_doubles(ppk::cgs_grid((int)n)), (size_t)(wcap + 1) * 3 * 1024)));
         return PP_OK;
     }
 

@@ -13,10 +13,11 @@ namespace {
 
 constexpr int kMaxCols = 128;    // largest j accepted
 constexpr int kMaxBlocks = 608;  // grid cap of the three passes (4 blocks x 152 SMs)
-constexpr size_t kPartDoubles = (size_t)kMaxBlocks * (kMaxCols + 2);
+// block partials and the sums of groups of 32 blocks (two-level grid reduction)
+constexpr size_t kPartDoubles = ((size_t)kMaxBlocks + (kMaxBlocks + 31) / 32) * (kMaxCols + 2);
 constexpr size_t kH1 = kPartDoubles, kH2 = kH1 + 256, kScal = kH2 + 256, kNrm = kScal + 1, kTicket = kScal + 8;
-constexpr size_t kScratchDoubles = kTicket + 8;
-// 608 x 130 + 520 doubles: about 636 KB, held by every GPU that loads the library until exit.
+constexpr size_t kScratchDoubles = kTicket + ppk::kTicketWords / 2;
+// (608 + 19) x 130 + 552 doubles: about 656 KB, held by every GPU that loads the library until exit.
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -57,7 +58,7 @@ extern "C" pp_status pp_orthogonalize_noalloc(int64_t n, const double *V_dev, in
     unsigned *ticket = (unsigned *)(base + kTicket);
     // the reduction ticket must start at zero; an earlier call leaves it at zero
     // unless it was interrupted, so clear it every time
-    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
+    cudaError_t e = cudaMemsetAsync(ticket, 0, ppk::kTicketWords * sizeof(unsigned), s);
     if (e != cudaSuccess) return pp_fail(PP_ECUDA, "pp_orthogonalize_noalloc: %s", cudaGetErrorString(e));
     int grid = ppk::cgs_grid((int)n);
     if (grid > kMaxBlocks) grid = kMaxBlocks;

@@ -124,8 +124,17 @@ __device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, 
             part[a.mode == 1 ? j : 0] = s;
         }
     }
-    if (!last_block(a.ticket, nblk)) return;
-    reduce_partials(a.part, nblk, nout, a.out);
+    // two-level reduction: the last block of each group of 32 sums the group's
+    // partials (block order), the last group sums the group sums (group order)
+    const int ng = (nblk + 31) / 32, g = bid / 32;
+    const int gsize = nblk - 32 * g < 32 ? nblk - 32 * g : 32;
+    double *gpart = a.part + (size_t)nblk * nout;
+    if (!last_block(a.ticket + 1 + g, gsize)) return;
+    reduce_partials(a.part + (size_t)g * 32 * nout, gsize, nout, gpart + (size_t)g * nout);
+    __syncthreads();
+    if (tid == 0) a.ticket[1 + g] = 0;
+    if (!last_block(a.ticket, ng)) return;
+    reduce_partials(gpart, ng, nout, a.out);
     __syncthreads();
     if (tid == 0) *a.ticket = 0;
     if (a.mode == 2) {
@@ -733,10 +742,12 @@ __global__ void __launch_bounds__(kThreads) k_coldots(ColDotArgs a) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-// The most blocks any CGS2 sweep launches (sizes the partial-sum buffers).
+// The most blocks any CGS2 sweep launches (sizes the partial-sum buffers; at
+// most 32 (kTicketWords - 1) blocks, so every group has a ticket word).
 int cgs_grid(int n) {
     int tiles = (n + kRows - 1) / kRows;
     int g = num_sms() * 8;
+    if (g > 32 * (kTicketWords - 1)) g = 32 * (kTicketWords - 1);
     return tiles < g ? tiles : g;
 }
 

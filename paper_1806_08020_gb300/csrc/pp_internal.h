@@ -130,6 +130,13 @@ struct CgsArgs {
     int stall = 0;       // test hook: a staged sweep issues no copies, so its waits expire
 };
 int cgs_grid(int n);
+// Grid reductions of the CGS2 sweeps: block partial sums, then the last block
+// of each group of 32 consecutive blocks sums its group, then the last group
+// sums the group sums.  Tickets: word 0 counts groups, word 1 + g blocks of
+// group g (all zero between launches).  Scratch for a grid of `grid` blocks
+// and at most 130 outputs: the block partials followed by the group sums.
+constexpr int kTicketWords = 64;
+inline size_t cgs_part_doubles(int grid) { return ((size_t)grid + (size_t)(grid + 31) / 32) * 130; }
 void launch_cgs(Prec p, const CgsArgs &a, cudaStream_t st);
 // as launch_cgs with at most grid_cap blocks (the partial sums need grid_cap * (j+1) doubles)
 void launch_cgs_grid(Prec p, const CgsArgs &a, int grid_cap, cudaStream_t st);
