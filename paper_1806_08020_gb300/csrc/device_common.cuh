@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <utility>
+
 namespace ppk {
 
 // Basis element loads widened to FP32 (FP32 or BF16 storage).
@@ -83,6 +85,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
         if ((it & 63) == 0 && global_ns() - t0 > kWaitNs) return false;
     }
     return false;
+}
+
+// Programmatic dependent launch.  A kernel launched by launch_dependent() may
+// be scheduled while the kernel before it on the stream is still finishing;
+// it calls grid_wait() before touching memory, which returns once that kernel
+// has completed and its writes are visible, so the overlap covers only the
+// launch and block scheduling.  grid_trigger() lets the next kernel on the
+// stream be scheduled that early (it still waits for this one to complete).
+__device__ __forceinline__ void grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                                    Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 }  // namespace ppk

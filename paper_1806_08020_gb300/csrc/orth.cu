@@ -352,6 +352,8 @@ __device__ __forceinline__ void cgs_body(const CgsArgs &a, int bid, int nblk) {
 
 template <typename T, int CPW, int NW>
 __global__ void __launch_bounds__(NW * 32) k_cgs(CgsArgs a) {
+    grid_trigger();
+    grid_wait();
     cgs_body<T, CPW, NW>(a, blockIdx.x, gridDim.x);
 }
 
@@ -569,6 +571,8 @@ __global__ void k_scale_batch(const BatchCgsInst *ci, int count, const int *lo, 
 
 template <typename T>
 __global__ void k_scale(int n, T *x, const double *scal) {
+    grid_trigger();
+    grid_wait();
     double s = *scal;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         x[i] = (T)((double)x[i] * s);
@@ -873,13 +877,13 @@ static void cgs_dispatch(const CgsArgs &a, int cap, cudaStream_t st) {
     if constexpr (sizeof(T) == 8) {
         if (a.j <= kCgs4Cols) {
             with_cpw_exact<kCgs4Cols / 4>((a.j + 3) / 4, [&](auto C) {
-                k_cgs<T, C.value, 4><<<resident_grid<T, C.value, 4>(a.n, cap), 128, 0, st>>>(a);
+                launch_dependent(k_cgs<T, C.value, 4>, resident_grid<T, C.value, 4>(a.n, cap), 128, 0, st, a);
             });
             return;
         }
     }
     with_cpw((a.j + kWarps - 1) / kWarps, [&](auto C) {
-        k_cgs<T, C.value, kWarps><<<resident_grid<T, C.value, kWarps>(a.n, cap), kThreads, 0, st>>>(a);
+        launch_dependent(k_cgs<T, C.value, kWarps>, resident_grid<T, C.value, kWarps>(a.n, cap), kThreads, 0, st, a);
     });
 }
 
@@ -956,9 +960,9 @@ void launch_unit_into(Prec p, int n, const double *x, const double *nrm2, void *
 void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st) {
     int g = num_sms() * 4;
     if (p == F64)
-        k_scale<double><<<g, kThreads, 0, st>>>(n, (double *)x, scal);
+        launch_dependent(k_scale<double>, g, kThreads, 0, st, n, (double *)x, scal);
     else
-        k_scale<float><<<g, kThreads, 0, st>>>(n, (float *)x, scal);
+        launch_dependent(k_scale<float>, g, kThreads, 0, st, n, (float *)x, scal);
 }
 
 void launch_rotate(Prec p, int n, const void *V, int64_t ldv, int m, const double *Q, int kk, void *out,

@@ -189,6 +189,8 @@ __device__ __forceinline__ Acc dia_row(const DiaView &D, const int *off_s, const
 
 template <typename T, typename V, typename Acc, int KIND, bool SIGMA>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass_dia(DiaView D, StepArgs s) {
+    grid_trigger();
+    grid_wait();
     __shared__ int off_s[kDiaMax];
     for (int d = threadIdx.x; d < D.ndiag; d += blockDim.x) off_s[d] = D.off[d];
     __syncthreads();
@@ -210,6 +212,8 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_dia(DiaView D, StepArg
 
 template <typename T, typename V, typename Acc>
 __global__ void __launch_bounds__(kPassMaxThreads) k_step_dia(DiaView D, StepArgs s) {
+    grid_trigger();
+    grid_wait();
     __shared__ int off_s[kDiaMax];
     for (int d = threadIdx.x; d < D.ndiag; d += blockDim.x) off_s[d] = D.off[d];
     __syncthreads();
@@ -220,6 +224,8 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_step_dia(DiaView D, StepArg
 
 template <typename T, typename V, typename Acc, int KIND, bool SIGMA, int FMT>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass(SellView S, CsrView R, StepArgs s) {
+    grid_trigger();
+    grid_wait();
     const T *x = (const T *)s.x;
     T *y = (T *)s.y;
     auto finish = [&](int row, Acc u) {
@@ -360,6 +366,8 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_tma(SellView A, StepAr
 // General pass (running sum, optional output, outer epilogue): see StepArgs.
 template <typename T, typename V, typename Acc, int FMT>
 __global__ void __launch_bounds__(kPassMaxThreads) k_step(SellView S, CsrView R, StepArgs s) {
+    grid_trigger();
+    grid_wait();
     if constexpr (FMT >= 5) {  // two rows per thread
         const int r0 = blockIdx.x * 2 * blockDim.x + threadIdx.x, r1 = r0 + blockDim.x;
         if (r0 >= S.n) return;
@@ -475,11 +483,11 @@ static void pass_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
     const bool general = s.r || s.oy || !s.y;
     const bool sig = s.sigma != 0.0;
     if (general || (!s.plain && !s.aux && s.a1 != 0.0)) {  // not one of the specialised forms
-        k_step<T, T, T, FMT><<<blocks, threads, 0, st>>>(A.sell, A.csr, s);
+        launch_dependent(k_step<T, T, T, FMT>, blocks, threads, 0, st, A.sell, A.csr, s);
         return;
     }
     int kind = s.plain ? 0 : (s.aux ? 2 : 1);
-#define PP_PASS(K, S) k_pass<T, T, T, K, S, FMT><<<blocks, threads, 0, st>>>(A.sell, A.csr, s)
+#define PP_PASS(K, S) launch_dependent(k_pass<T, T, T, K, S, FMT>, blocks, threads, 0, st, A.sell, A.csr, s)
     if (kind == 0) {
         if (sig) PP_PASS(0, true); else PP_PASS(0, false);
     } else if (kind == 1) {
@@ -538,11 +546,11 @@ static void dia_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
     const bool general = s.r || s.oy || !s.y;
     const bool sig = s.sigma != 0.0;
     if (general || (!s.plain && !s.aux && s.a1 != 0.0)) {
-        k_step_dia<T, T, T><<<blocks, threads, 0, st>>>(A.dia, s);
+        launch_dependent(k_step_dia<T, T, T>, blocks, threads, 0, st, A.dia, s);
         return;
     }
     const int kind = s.plain ? 0 : (s.aux ? 2 : 1);
-#define PP_DPASS(K, S) k_pass_dia<T, T, T, K, S><<<blocks, threads, 0, st>>>(A.dia, s)
+#define PP_DPASS(K, S) launch_dependent(k_pass_dia<T, T, T, K, S>, blocks, threads, 0, st, A.dia, s)
     if (kind == 0) {
         if (sig) PP_DPASS(0, true); else PP_DPASS(0, false);
     } else if (kind == 1) {
