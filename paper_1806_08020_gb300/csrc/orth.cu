@@ -529,6 +529,8 @@ __device__ __forceinline__ int find_instance(const BatchCgsInst *ci, int count, 
 template <typename T, int CPW, int NW>
 __global__ void __launch_bounds__(NW * 32) k_cgs_batch(const BatchCgsInst *ci, int count, const int *lo,
                                                        const int *hi, int mode, int jj) {
+    grid_trigger();
+    grid_wait();
     const int i = find_instance(ci, count, blockIdx.x);
     if (jj < lo[i] || jj >= hi[i]) return;
     const BatchCgsInst &I = ci[i];
@@ -560,6 +562,8 @@ __global__ void __launch_bounds__(NW * 32) k_cgs_batch(const BatchCgsInst *ci, i
 
 template <typename T>
 __global__ void k_scale_batch(const BatchCgsInst *ci, int count, const int *lo, const int *hi, int jj) {
+    grid_trigger();
+    grid_wait();
     const int i = find_instance(ci, count, blockIdx.x);
     if (jj < lo[i] || jj >= hi[i]) return;
     const BatchCgsInst &I = ci[i];
@@ -904,24 +908,24 @@ void launch_cgs_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, co
                       int jj, cudaStream_t st) {
     if (p == F64 && jj + 1 <= kCgs4Cols) {
         with_cpw_exact<kCgs4Cols / 4>((jj + 1 + 3) / 4, [&](auto C) {
-            k_cgs_batch<double, C.value, 4><<<nblocks, 128, 0, st>>>(ci, count, lo, hi, mode, jj);
+            launch_dependent(k_cgs_batch<double, C.value, 4>, nblocks, 128, 0, st, ci, count, lo, hi, mode, jj);
         });
         return;
     }
     with_cpw((jj + 1 + kWarps - 1) / kWarps, [&](auto C) {
         if (p == F64)
-            k_cgs_batch<double, C.value, kWarps><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj);
+            launch_dependent(k_cgs_batch<double, C.value, kWarps>, nblocks, kThreads, 0, st, ci, count, lo, hi, mode, jj);
         else
-            k_cgs_batch<float, C.value, kWarps><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, mode, jj);
+            launch_dependent(k_cgs_batch<float, C.value, kWarps>, nblocks, kThreads, 0, st, ci, count, lo, hi, mode, jj);
     });
 }
 
 void launch_scale_batch(Prec p, const BatchCgsInst *ci, int count, int nblocks, const int *lo, const int *hi, int jj,
                         cudaStream_t st) {
     if (p == F64)
-        k_scale_batch<double><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, jj);
+        launch_dependent(k_scale_batch<double>, nblocks, kThreads, 0, st, ci, count, lo, hi, jj);
     else
-        k_scale_batch<float><<<nblocks, kThreads, 0, st>>>(ci, count, lo, hi, jj);
+        launch_dependent(k_scale_batch<float>, nblocks, kThreads, 0, st, ci, count, lo, hi, jj);
 }
 
 int cgs_batch_blocks(int n) {

@@ -390,6 +390,8 @@ template <typename T>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassInst *pi, const BatchPassEntry *tab,
                                                                 const int2 *items, int nitems, const int *lo,
                                                                 const int *hi, int jj) {
+    grid_trigger();
+    grid_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int2 itm = items[it];
@@ -595,9 +597,9 @@ void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *ta
     if (g < 1) g = 1;
     const int threads = 32 * groups;
     if (p == F64)
-        k_pass_batch<double><<<g, threads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
+        launch_dependent(k_pass_batch<double>, g, threads, 0, st, pi, tab, items, nitems, lo, hi, jj);
     else
-        k_pass_batch<float><<<g, threads, 0, st>>>(pi, tab, items, nitems, lo, hi, jj);
+        launch_dependent(k_pass_batch<float>, g, threads, 0, st, pi, tab, items, nitems, lo, hi, jj);
 }
 
 void launch_sell_fill(Prec p, int n, int nslices, int cshift, const int *rowptr, const int *col, const double *val,
