@@ -22,6 +22,8 @@ from .ppa import (  # noqa: F401
     cgs2,
     damped_poly,
     eigs,
+    harmonic_restart_matrix,
+    thick_restart,
     first_cycle_rayleigh,
     gershgorin_shift,
     gmres_arnoldi,

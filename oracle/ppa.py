@@ -439,10 +439,59 @@ def _target_sort(lam: np.ndarray, target: str) -> np.ndarray:
     return np.array(sorted(range(lam.size), key=key), dtype=int)
 
 
+def harmonic_restart_matrix(H: np.ndarray, m: int, tau: float) -> tuple[np.ndarray, np.ndarray]:
+    """Harmonic Ritz values of the Arnoldi relation B V_m = V_{m+1} H (H is
+    (m+1) x m) with respect to the target tau (Section 4's restart kept
+    harmonic Ritz vectors in the harmonic Arnoldi variant of Example 2; Morgan
+    and Zeng's harmonic restarted Arnoldi).
+
+    (theta, V_m g) is a harmonic Ritz pair when (B - tau) V_m g - (theta - tau) V_m g
+    is orthogonal to (B - tau) V_m.  With M = H_m - tau I, h = h_{m+1,m} and
+    f = M^{-T} e_m this is the eigenproblem of K = H_m + h^2 f e_m^T.  Returns
+    (K, c) with c = [-h f; 1]: every harmonic residual is a multiple of V_{m+1} c.
+    """
+    Hm = H[:m, :m]
+    h = H[m, m - 1]
+    em = np.zeros(m)
+    em[-1] = 1.0
+    f = np.linalg.solve((Hm - tau * np.eye(m)).T, em)
+    K = Hm + h * h * np.outer(f, em)
+    return K, np.concatenate([-h * f, [1.0]])
+
+
+def thick_restart(V: np.ndarray, H: np.ndarray, m: int, Q: np.ndarray,
+                  cvec: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """The restarted basis V_{kk+1} and its (m+1) x m Hessenberg array (leading
+    (kk+1) x kk block filled) from B V_m = V_{m+1} H and the orthonormal m x kk
+    coefficients Q of the kept vectors (Section 4).
+
+    Ritz restart (cvec None): V_kk = V_m Q, v_{kk+1} = v_{m+1},
+    H_kk = [Q^T H_m Q ; h_{m+1,m} e_m^T Q].
+    Harmonic restart: P = [[Q; 0], p] with p the residual direction cvec
+    orthogonalised against [Q; 0] (twice) and normalised; V_{kk+1} = V_{m+1} P,
+    H_kk = P^T H Q.  Both keep B V_kk = V_{kk+1} H_kk.
+    """
+    kk = Q.shape[1]
+    Hn = np.zeros((m + 1, m))
+    if cvec is None:
+        Vk = np.column_stack([V[:, :m] @ Q, V[:, m]])
+        Hn[:kk, :kk] = Q.T @ H[:m, :m] @ Q
+        Hn[kk, :kk] = H[m, m - 1] * Q[m - 1, :]
+        return Vk, Hn
+    P = np.zeros((m + 1, kk + 1))
+    P[:m, :kk] = Q
+    p = np.array(cvec, dtype=float)
+    for _ in range(2):
+        p = p - P[:, :kk] @ (P[:, :kk].T @ p)
+    P[:, kk] = p / np.linalg.norm(p)
+    Hn[:kk + 1, :kk] = P.T @ (H @ Q)
+    return V[:, :m + 1] @ P, Hn
+
+
 def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: int, k: int,
          rtol: float, v0: np.ndarray, c: Counters, target_point: float = 1.0,
          target: str = "SM", max_cycles: int = 2000, sigma: float = 0.0,
-         log: Callable[[int, float], None] | None = None) -> EigResult:
+         log: Callable[[int, float], None] | None = None, restart: str = "ritz") -> EigResult:
     """Thick-restarted Arnoldi(m, k) on ``op`` (Section 2 box step 2; Section 4).
 
     * Build V_{m+1}, H_{m+1,m} with CGS2 (one reorthogonalisation pass).
@@ -460,7 +509,14 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
     ``sigma`` is the shift of ``op``'s matrix; Rayleigh quotients use A itself.
     ``log`` (optional) is called as log(cycle, max relative residual) after
     each convergence test; it does not affect the arithmetic.
+    ``restart="harmonic"``: the harmonic Arnoldi variant (Example 2): harmonic
+    Ritz values (w.r.t. ``target_point``) and vectors replace the Ritz ones in
+    the ordering, the convergence test and the restart, which keeps
+    V_{k+1} = V_{m+1} P with P = orth([Q_k; 0], c) and H_k = P^T H Q_k (see
+    ``harmonic_restart_matrix``).
     """
+    if restart not in ("ritz", "harmonic"):
+        raise ValueError("restart must be 'ritz' or 'harmonic'")
     n = v0.size
     nA = norm1(A)
     V = np.zeros((n, m + 1))
@@ -481,7 +537,11 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
             H[j + 1, j] = hn
             V[:, j + 1] = w / hn
         Hm = H[:m, :m]
-        nu, S = np.linalg.eig(Hm)
+        if restart == "harmonic":
+            K, cvec = harmonic_restart_matrix(H, m, target_point)
+            nu, S = np.linalg.eig(K)
+        else:
+            nu, S = np.linalg.eig(Hm)
         order = ritz_order(nu, target_point)
         nw = nev + (1 if nu[order[nev - 1]].imag > 0 else 0)
         want = order[:nw]
@@ -523,12 +583,9 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
                 cols.append(S[:, i].real)
                 cols.append(S[:, i].imag)
         Q, _ = np.linalg.qr(np.stack(cols, axis=1))
-        V[:, :kk] = V[:, :m] @ Q
-        V[:, kk] = V[:, m]
-        c.vops += m * kk
-        Hn = np.zeros((m + 1, m))
-        Hn[:kk, :kk] = Q.T @ Hm @ Q
-        Hn[kk, :kk] = H[m, m - 1] * Q[m - 1, :]
+        Vk, Hn = thick_restart(V, H, m, Q, cvec if restart == "harmonic" else None)
+        V[:, :kk + 1] = Vk
+        c.vops += (m + 1) * (kk + 1) if restart == "harmonic" else m * kk
         H = Hn
         j0 = kk
     srt = _target_sort(lam, target)
