@@ -64,6 +64,13 @@ enum { PP_FMT_AUTO = 0, PP_FMT_CSR = 1, PP_FMT_SELL = 2, PP_FMT_DIA = 3 };
 /* Which eigenvalues: smallest magnitude (Section 2) or smallest real part
  * (run on A - sigma I with sigma the leftmost Gershgorin point, Section 2 footnote 1). */
 enum { PP_TARGET_SM = 0, PP_TARGET_SR = 1 };
+/* Restart of pp_eigs (Section 4; Example 2).  Harmonic: the values ordered,
+ * tested and kept are the harmonic Ritz values of the operator with respect to
+ * its target point (1 for pi(A), 0 for plain Arnoldi), i.e. theta with
+ * (Op - t) y - (theta - t) y orthogonal to (Op - t) V_m; the restart keeps
+ * V_{m+1} P, P = orth([Q_k; 0], c), c = [-h f; 1], f = (H_m - t I)^{-T} e_m,
+ * so the residual direction shared by all harmonic pairs stays in the basis. */
+enum { PP_RESTART_RITZ = 0, PP_RESTART_HARMONIC = 1 };
 
 typedef struct {
     int precision;      /* PP_FP64 (default), PP_FP32, PP_FP32_BF16 */
@@ -82,6 +89,9 @@ typedef struct {
                            2 = loads of up to eight entries issued together; 3 = slice data staged
                            in shared memory by bulk copies (SELL-32 only); 4 = two rows per thread */
     void *stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
+    int restart;        /* pp_eigs restart: PP_RESTART_RITZ (default) keeps Ritz vectors;
+                           PP_RESTART_HARMONIC keeps harmonic Ritz vectors (the harmonic
+                           Arnoldi variant of Example 2, for interior targets) */
 } pp_opts;
 
 /* Counters of Section 4 (mvps, dot products, vector operations) plus timings. */
@@ -326,7 +336,8 @@ typedef struct pp_batch pp_batch;
 /*
  * pp_batch_create — upload `count` independent sparse matrices (host CSR each,
  * as pp_create) for solving together.  opts applies to all (PP_FP32 for the
- * mixed-precision path); the device format is SELL-32.
+ * mixed-precision path); the device format is SELL-32.  Errors: PP_EINVAL for
+ * PP_FP32_BF16 or a harmonic restart (the batched engine keeps Ritz vectors).
  */
 pp_status pp_batch_create(pp_batch **out, int count, const int64_t *n, const int64_t *const *rowptr,
                           const int32_t *const *colind, const double *const *vals, const pp_opts *opts);
@@ -362,7 +373,8 @@ typedef struct pp_server pp_server;
  * a request that converges is retired at once (its device memory is freed)
  * and the queue head is admitted in its place, so requests that arrive while
  * others run join them on the device.  opts: precision (PP_FP32 = FP32 apply,
- * FP64 test and refinement), target, max_cycles, refine_steps, stream.
+ * FP64 test and refinement), target, max_cycles, refine_steps, stream
+ * (PP_FP32_BF16 and a harmonic restart: PP_EINVAL).
  * keep_vectors: return eigenvectors in pp_server_result (host memory n x
  * (nev + 1) per request).
  */

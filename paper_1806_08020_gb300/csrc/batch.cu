@@ -599,6 +599,10 @@ pp_status pp_batch_create(pp_batch **out, int count, const int64_t *n, const int
         delete b;
         return pp_fail(PP_EINVAL, "pp_batch_create: the batched engine runs PP_FP64 or PP_FP32");
     }
+    if (b->opts.restart != PP_RESTART_RITZ) {
+        delete b;
+        return pp_fail(PP_EINVAL, "pp_batch_create: the batched engine restarts with Ritz vectors only");
+    }
     if (b->opts.stream) {
         b->stream = (cudaStream_t)b->opts.stream;
     } else {
@@ -694,6 +698,10 @@ pp_status pp_server_create(pp_server **out, const pp_opts *opts, int64_t mem_bud
     if (s->opts.precision == PP_FP32_BF16) {
         delete s;
         return pp_fail(PP_EINVAL, "pp_server_create: the served engine runs PP_FP64 or PP_FP32");
+    }
+    if (s->opts.restart != PP_RESTART_RITZ) {
+        delete s;
+        return pp_fail(PP_EINVAL, "pp_server_create: the served engine restarts with Ritz vectors only");
     }
     if (s->opts.stream) {
         s->stream = (cudaStream_t)s->opts.stream;

@@ -574,6 +574,7 @@ void pp_opts_default(pp_opts *o) {
     o->sell_c = 0;
     o->sell_sigma = 0;
     o->stream = nullptr;
+    o->restart = PP_RESTART_RITZ;
 }
 
 pp_status pp_trim(pp_ctx *c) {
@@ -834,6 +835,8 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     if (c->opts.sell_sigma > 1) return fail(pp_fail(PP_EINVAL, "pp_create: sell_sigma must be 0 or 1"));
     if (c->opts.sell_index != 0 && c->opts.sell_index != 32)
         return fail(pp_fail(PP_EINVAL, "pp_create: sell_index must be 0 or 32"));
+    if (c->opts.restart != PP_RESTART_RITZ && c->opts.restart != PP_RESTART_HARMONIC)
+        return fail(pp_fail(PP_EINVAL, "pp_create: restart must be PP_RESTART_RITZ or PP_RESTART_HARMONIC"));
     if (c->opts.sell_loop < 0 || c->opts.sell_loop > 4)
         return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop must be 0 to 4"));
     std::vector<int> cands;

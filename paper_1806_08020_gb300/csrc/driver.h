@@ -376,10 +376,18 @@ struct Cycle {
     std::vector<cd> nu;
     std::vector<int> order;
     Slots sl;
+    bool harmonic = false;
+    std::vector<double> cvec;  // harmonic: [-h f; 1], the direction of every harmonic residual
 };
 
-inline pp_status wanted_set(const std::vector<double> &H, int ldh, int m, int nev, double target, Cycle &cy) {
+// With harmonic set, the values are the harmonic Ritz values with respect to
+// the target t: eigenvalues of K = H_m + h^2 f e_m^T, f = (H_m - t I)^{-T} e_m,
+// h = h_{m+1,m} (Example 2's harmonic Arnoldi; the Galerkin condition
+// (Op - t) y - (theta - t) y orthogonal to (Op - t) V_m).
+inline pp_status wanted_set(const std::vector<double> &H, int ldh, int m, int nev, double target, Cycle &cy,
+                            bool harmonic = false) {
     cy.m = m;
+    cy.harmonic = harmonic;
     cy.Hm.assign((size_t)m * m, 0.0);
     cy.wr.assign(m, 0.0);
     cy.wi.assign(m, 0.0);
@@ -389,6 +397,19 @@ inline pp_status wanted_set(const std::vector<double> &H, int ldh, int m, int ne
     for (double v : cy.Hm)
         if (!std::isfinite(v)) return pp_fail(PP_ENUMERIC, "non-finite Hessenberg entry");
     std::vector<double> Hc = cy.Hm;
+    if (harmonic) {
+        const double h = H[m + (size_t)(m - 1) * ldh];
+        std::vector<double> Mt((size_t)m * m);
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < m; ++i) Mt[i + (size_t)j * m] = cy.Hm[j + (size_t)i * m] - (i == j ? target : 0.0);
+        std::vector<double> f(m, 0.0);
+        f[m - 1] = 1.0;
+        if (!ppd::lu_solve(m, Mt, f.data()))
+            return pp_fail(PP_ENUMERIC, "harmonic Ritz values: H_m - t I is singular");
+        for (int i = 0; i < m; ++i) Hc[i + (size_t)(m - 1) * m] += h * h * f[i];
+        cy.cvec.assign(m + 1, 1.0);
+        for (int i = 0; i < m; ++i) cy.cvec[i] = -h * f[i];
+    }
     if (!ppd::dense_eig(m, Hc.data(), m, cy.wr.data(), cy.wi.data(), cy.Sv.data(), m))
         return pp_fail(PP_ENUMERIC, "Ritz values: QR failed");
     cy.nu.resize(m);
@@ -420,8 +441,50 @@ inline pp_status wanted_set(const std::vector<double> &H, int ldh, int m, int ne
     return PP_OK;
 }
 
+// Harmonic restart: from the kept coefficients Q (m x kk, orthonormal), the
+// rotation P = [[Q; 0], p] ((m+1) x (kk+1), p = c orthogonalised against
+// [Q; 0] twice and normalised) and Hn = P^T Hbar Q ((kk+1) x kk leading block
+// of an ldh x m array), Hbar = [H_m; h e_m^T].  Q is replaced by P.
+inline int harmonic_basis(const Cycle &cy, const std::vector<double> &H, int ldh, int kk, std::vector<double> &Q,
+                          std::vector<double> &Hn) {
+    const int m = cy.m, m1 = m + 1;
+    std::vector<double> P((size_t)m1 * (kk + 1), 0.0);
+    for (int cc = 0; cc < kk; ++cc)
+        for (int r = 0; r < m; ++r) P[r + (size_t)cc * m1] = Q[r + (size_t)cc * m];
+    std::vector<double> p = cy.cvec;
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<double> proj(kk, 0.0);
+        for (int cc = 0; cc < kk; ++cc)
+            for (int r = 0; r < m1; ++r) proj[cc] += P[r + (size_t)cc * m1] * p[r];
+        for (int cc = 0; cc < kk; ++cc)
+            for (int r = 0; r < m1; ++r) p[r] -= P[r + (size_t)cc * m1] * proj[cc];
+    }
+    double nrm = 0;
+    for (double v : p) nrm += v * v;
+    nrm = std::sqrt(nrm);
+    for (int r = 0; r < m1; ++r) P[r + (size_t)kk * m1] = p[r] / nrm;
+    // Hbar Q: (m+1) x kk
+    std::vector<double> HQ((size_t)m1 * kk, 0.0);
+    for (int cc = 0; cc < kk; ++cc)
+        for (int r = 0; r < m1; ++r) {
+            double s = 0;
+            for (int t = 0; t < m; ++t) s += H[r + (size_t)t * ldh] * Q[t + (size_t)cc * m];
+            HQ[r + (size_t)cc * m1] = s;
+        }
+    Hn.assign((size_t)ldh * m, 0.0);
+    for (int cc = 0; cc < kk; ++cc)
+        for (int r = 0; r <= kk; ++r) {
+            double s = 0;
+            for (int t = 0; t < m1; ++t) s += P[t + (size_t)r * m1] * HQ[t + (size_t)cc * m1];
+            Hn[r + (size_t)cc * ldh] = s;
+        }
+    Q.swap(P);
+    return kk;
+}
+
 // Thick restart (Section 4): keep k Ritz vectors (k - 1 when a pair would
 // split), Q = qr([Re, Im] of their coefficients), Hn = [Q^T H_m Q ; h e_m^T Q].
+// A harmonic cycle continues in harmonic_basis (Q becomes the (m+1) x (kk+1) P).
 inline int restart_basis(const Cycle &cy, const std::vector<double> &H, int ldh, int k, std::vector<double> &Q,
                          std::vector<double> &Hn) {
     const int m = cy.m;
@@ -442,6 +505,7 @@ inline int restart_basis(const Cycle &cy, const std::vector<double> &H, int ldh,
     }
     Q.assign((size_t)m * kk, 0.0);
     ppd::thin_qr(m, kk, B.data(), Q.data());
+    if (cy.harmonic) return harmonic_basis(cy, H, ldh, kk, Q, Hn);
     std::vector<double> HQ((size_t)m * kk, 0.0);
     Hn.assign((size_t)ldh * m, 0.0);
     for (int cc = 0; cc < kk; ++cc)

@@ -78,7 +78,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
         double th0 = now();
         CKS(check_sweeps(c));
         accumulate_times(tm, marks, S.t_apply, S.t_orth);
-        CKS(wanted_set(H, ldh, m, nev, target, cy));
+        CKS(wanted_set(H, ldh, m, nev, target, cy, c->opts.restart == PP_RESTART_HARMONIC));
         CKS(D.ritz_test(V, bpr, m, cy.Sw, cy.sl, rtol, R, S));
         S.nconv = R.nconv;
         trace_cycle("eigs", c, cycle, bpr == ppk::F64 ? 64 : (bpr == ppk::F32 ? 32 : 16), R,
@@ -134,12 +134,18 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
         std::vector<double> Q, Hn;
         int kk = restart_basis(cy, H, ldh, k, Q, Hn);
         CK(cudaMemcpyAsync(D.dQ, Q.data(), Q.size() * 8, cudaMemcpyHostToDevice, c->stream));
-        ppk::launch_rotate(bpr, (int)n, V, ldv, m, D.dQ, kk, V2, ldv, c->stream);
-        CKS(check_launch(c));
-        CK(cudaMemcpyAsync((char *)V2 + (size_t)kk * ldv * esz, (char *)V + (size_t)m * ldv * esz, n * esz,
-                           cudaMemcpyDeviceToDevice, c->stream));
+        if (cy.harmonic) {  // V_{kk+1} = V_{m+1} P
+            ppk::launch_rotate(bpr, (int)n, V, ldv, m + 1, D.dQ, kk + 1, V2, ldv, c->stream);
+            CKS(check_launch(c));
+            S.vops += (int64_t)(m + 1) * (kk + 1);
+        } else {  // V_kk = V_m Q, v_{kk+1} = v_{m+1}
+            ppk::launch_rotate(bpr, (int)n, V, ldv, m, D.dQ, kk, V2, ldv, c->stream);
+            CKS(check_launch(c));
+            CK(cudaMemcpyAsync((char *)V2 + (size_t)kk * ldv * esz, (char *)V + (size_t)m * ldv * esz, n * esz,
+                               cudaMemcpyDeviceToDevice, c->stream));
+            S.vops += (int64_t)m * kk;
+        }
         std::swap(V, V2);
-        S.vops += (int64_t)m * kk;
         CK(cudaMemcpyAsync(dH, Hn.data(), Hn.size() * 8, cudaMemcpyHostToDevice, c->stream));
         j0 = kk;
         S.t_restart += now() - th0;

@@ -17,6 +17,7 @@ Problem families (the paper's Section 4-8 examples and the scaled configs):
   ``-100 lap u + 2000 u_x``).
 * Diagonal test matrices of Examples 4, 6 and 7 and the Figure 1 spectrum.
 * Random nonsymmetric banded matrices for the request-stream workload.
+* Rotation blocks with a fanned-out complex spectrum (Example 2's stand-in).
 """
 from __future__ import annotations
 
@@ -165,6 +166,36 @@ def banded_random(n: int, w: int, seed: int) -> CSR:
     cols = np.arange(n)[:, None] + np.arange(-w, w + 1)[None, :]
     valid = (cols >= 0) & (cols < n)
     return _from_stencil(n, offs, coef, valid)
+
+
+def rotation_blocks(nb: int, bmax: float, seed: int) -> CSR:
+    """Stand-in for Example 2's complex spectrum (Af23560 is not available):
+    n = 2 nb, 2 x 2 blocks [[a_i, b_i], [-b_i, a_i]] (eigenvalues a_i +- i b_i)
+    with a_i uniform in [0.05, 10] (sorted) and b_i uniform in [0, bmax] times
+    sqrt(a_i / 10), so the spectrum fans out into large imaginary parts away
+    from the origin, plus a weak coupling: each row i also gets 0.01 * N(0,1)
+    at column (i + 7 + (i * 7919) % (n - 7)) % n (never in its own block)."""
+    rng = np.random.default_rng([seed, 2])
+    n = 2 * nb
+    a = np.sort(rng.uniform(0.05, 10.0, nb))
+    b = rng.uniform(0.0, bmax, nb) * np.sqrt(a / 10.0)
+    cw = 0.01 * rng.standard_normal(n)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        blk = i // 2
+        j0 = 2 * blk
+        far = (i + 7 + (i * 7919) % (n - 7)) % n
+        ent = {j0: a[blk] if i == j0 else -b[blk], j0 + 1: b[blk] if i == j0 else a[blk]}
+        if far // 2 != blk:
+            ent[far] = ent.get(far, 0.0) + cw[i]
+        for j in sorted(ent):
+            rows.append(i)
+            cols.append(j)
+            vals.append(ent[j])
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, np.asarray(rows) + 1, 1)
+    return CSR(n, np.cumsum(rowptr).astype(np.int64), np.asarray(cols, dtype=np.int32),
+               np.asarray(vals, dtype=np.float64))
 
 
 def start_vector(n: int, seed: int, stream: int) -> np.ndarray:

@@ -21,13 +21,14 @@ PP_EINVAL, PP_ENOMEM, PP_ECUDA, PP_ETIMEOUT, PP_ENUMERIC = -1, -2, -3, -4, -5
 PP_FP64, PP_FP32, PP_FP32_BF16 = 0, 1, 2
 PP_FMT_AUTO, PP_FMT_CSR, PP_FMT_SELL, PP_FMT_DIA = 0, 1, 2, 3
 PP_TARGET_SM, PP_TARGET_SR = 0, 1
+PP_RESTART_RITZ, PP_RESTART_HARMONIC = 0, 1
 
 
 class pp_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("format", C.c_int), ("target", C.c_int), ("sigma", C.c_double),
                 ("add_roots", C.c_int), ("max_cycles", C.c_int), ("refine_steps", C.c_int),
                 ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sell_index", C.c_int), ("sell_loop", C.c_int),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("restart", C.c_int)]
 
 
 class pp_stats(C.Structure):

@@ -45,7 +45,7 @@ def cpu_residuals(A, lam, X):
     return out
 
 
-def oracle_solve(Acsr, d, nev, m, k, seed, target="SR", rtol=1e-8, d2=None):
+def oracle_solve(Acsr, d, nev, m, k, seed, target="SR", rtol=1e-8, d2=None, restart="ritz"):
     A = O.to_scipy(Acsr)
     c = O.Counters()
     sigma = O.gershgorin_shift(A) if target == "SR" else 0.0
@@ -60,7 +60,7 @@ def oracle_solve(Acsr, d, nev, m, k, seed, target="SR", rtol=1e-8, d2=None):
     else:
         P = O.build_poly(op, b, d, c)
     R = O.eigs(A, make_operator(op, P, c), nev, m, k, rtol, v0, c, target_point=1.0 if d else 0.0,
-               target=target, sigma=sigma)
+               target=target, sigma=sigma, restart=restart)
     return A, P, R
 
 
@@ -295,3 +295,56 @@ def test_device_start_vectors(precision):
         pp.pp_build_poly(ctx, 10, torch.zeros(A.n, dtype=torch.float64, device="cuda"))
     with pytest.raises(ValueError):
         pp.pp_build_poly(ctx, 10, bd.float())
+
+
+@pytest.mark.parametrize("case", ["plain_arnoldi", "complex", "banded", "sm_diag", "double"])
+def test_eigs_harmonic_restart_matches_oracle(case):
+    """Harmonic restart (PP_RESTART_HARMONIC, Example 2's variant) against the
+    oracle's harmonic restart: the same eigenpairs (kappa-gated values, every
+    residual <= rtol on A) and the same number of cycles within one."""
+    from paper_1806_08020_gb300 import pp
+    if case == "plain_arnoldi":
+        Acsr, d, nev, m, k, tgt, d2 = inputs.convection_diffusion_2d(20, 10.0), 0, 5, 30, 12, "SR", None
+    elif case == "complex":
+        Acsr, d, nev, m, k, tgt, d2 = inputs.convection_diffusion_2d(12, 60.0), 6, 6, 30, 11, "SR", None
+    elif case == "banded":
+        Acsr, d, nev, m, k, tgt, d2 = inputs.banded_random(600, 4, 2), 5, 6, 30, 11, "SR", None
+    elif case == "sm_diag":
+        Acsr, d, nev, m, k, tgt, d2 = inputs.diagonal(np.arange(1, 1001.0)), 10, 8, 30, 13, "SM", None
+    else:
+        Acsr, d, nev, m, k, tgt, d2 = inputs.convection_diffusion_2d(40, 10.0), 4, 6, 30, 11, "SR", 5
+    A, P, R = oracle_solve(Acsr, d, nev, m, k, 31, target=tgt, d2=d2, restart="harmonic")
+    _, poly, res = gpu_solve(Acsr, d, nev, m, k, 31, target=tgt, d2=d2, restart=pp.PP_RESTART_HARMONIC)
+    if Acsr.n <= 2000:
+        w, kap = eig_condition(Acsr.to_dense())
+        kf = lambda lam: kap[np.argmin(np.abs(w - lam))]  # noqa: E731
+    else:
+        kf = None
+    check_eigs(A, R, res, kf)
+    assert abs(res.stats["cycles"] - R.cycles) <= 1, (res.stats["cycles"], R.cycles)
+
+
+def test_harmonic_restart_option_errors():
+    from paper_1806_08020_gb300 import pp
+    A = inputs.plain_small()["A"]
+    with pytest.raises(pp.PPError):
+        pp.pp_create(A, restart=7)
+
+
+def test_harmonic_restart_on_a_fanned_complex_spectrum():
+    """Example 2's situation on a stand-in matrix: a degree-10 polynomial cannot
+    damp the eigenvalues with large imaginary parts, so the wanted ones are
+    interior for pi(A).  Both restarts match their oracle runs (eigenpairs and
+    cycles within two), and the harmonic restart needs fewer products with A."""
+    from paper_1806_08020_gb300 import pp
+    Acsr = inputs.rotation_blocks(1000, 20.0, 3)
+    w, kap = eig_condition(Acsr.to_dense())
+    kf = lambda lam: kap[np.argmin(np.abs(w - lam))]  # noqa: E731
+    mv = {}
+    for rs, code in (("ritz", pp.PP_RESTART_RITZ), ("harmonic", pp.PP_RESTART_HARMONIC)):
+        A, P, R = oracle_solve(Acsr, 10, 15, 50, 25, 5, target="SM", restart=rs)
+        _, poly, res = gpu_solve(Acsr, 10, 15, 50, 25, 5, target="SM", restart=code, max_cycles=300)
+        check_eigs(A, R, res, kf)
+        assert abs(res.stats["cycles"] - R.cycles) <= 2, (rs, res.stats["cycles"], R.cycles)
+        mv[rs] = res.stats["mvps"]
+    assert mv["harmonic"] < mv["ritz"], mv
