@@ -176,13 +176,14 @@ __device__ __forceinline__ Acc row_sum(const SellView &S, const CsrView &R, cons
 // the matrix has no entry the stored value is 0 and adds 0 * x exactly.
 template <typename T, typename V, typename Acc>
 __device__ __forceinline__ Acc dia_row(const DiaView &D, const int *off_s, const T *__restrict__ x, int row) {
-    const V *val = (const V *)D.val + row;
+    // the row's block of 32 rows holds its ndiag values 32 apart
+    const V *val = (const V *)D.val + (size_t)(row >> 5) * ((size_t)D.ndiag * 32) + (row & 31);
     Acc acc = 0;
 #pragma unroll 8
     for (int d = 0; d < D.ndiag; ++d) {
         const int c = row + off_s[d];
         const Acc xv = (c >= 0 && c < D.n) ? (Acc)__ldg(x + c) : (Acc)0;
-        acc = fma((Acc)__ldg(val + (size_t)d * D.ld), xv, acc);
+        acc = fma((Acc)__ldg(val + d * 32), xv, acc);
     }
     return acc;
 }
@@ -449,7 +450,7 @@ __global__ void k_dia_fill(int n, const int *rowptr, const int *col, const doubl
         double v = 0.0;
         while (k < end && col[k] < c) ++k;
         if (k < end && col[k] == c) v = val[k];
-        dval[(size_t)d * ld + row] = (V)v;
+        dval[(size_t)(row >> 5) * ((size_t)ndiag * 32) + (size_t)d * 32 + (row & 31)] = (V)v;
     }
 }
 

@@ -58,8 +58,11 @@ struct CsrView {
 };
 
 // Diagonal storage (for stencil and banded matrices): ndiag offsets off[d]
-// (increasing), values val[d * ld + row] = A(row, row + off[d]) or 0 where the
-// matrix has no entry or row + off[d] lies outside [0, n).  No column indices.
+// (increasing) and the values A(row, row + off[d]) (0 where the matrix has no
+// entry or row + off[d] lies outside [0, n)) in blocks of 32 rows: the entry
+// of diagonal d in row r is at val[(r / 32) * (ndiag * 32) + d * 32 + r % 32],
+// so a warp's values for all diagonals are one contiguous run.  ld (n rounded
+// up to 32) rows are allocated.  No column indices.
 struct DiaView {
     int n;
     int ndiag;
