@@ -174,16 +174,44 @@ __device__ __forceinline__ Acc row_sum(const SellView &S, const CsrView &R, cons
 // Row sum over the diagonals (DIA): no index loads; the offsets are in shared
 // memory.  Diagonals run in increasing offset, i.e. the row's CSR order; where
 // the matrix has no entry the stored value is 0 and adds 0 * x exactly.
+template <typename Acc, int K>
+__device__ __forceinline__ Acc dia_fmas(const Acc (&a)[8], const Acc (&xv)[8], Acc acc) {
+#pragma unroll
+    for (int u = 0; u < K; ++u) acc = fma(a[u], xv[u], acc);
+    return acc;
+}
+
 template <typename T, typename V, typename Acc>
 __device__ __forceinline__ Acc dia_row(const DiaView &D, const int *off_s, const T *__restrict__ x, int row) {
     // the row's block of 32 rows holds its ndiag values 32 apart
     const V *val = (const V *)D.val + (size_t)(row >> 5) * ((size_t)D.ndiag * 32) + (row & 31);
     Acc acc = 0;
-#pragma unroll 8
-    for (int d = 0; d < D.ndiag; ++d) {
-        const int c = row + off_s[d];
-        const Acc xv = (c >= 0 && c < D.n) ? (Acc)__ldg(x + c) : (Acc)0;
-        acc = fma((Acc)__ldg(val + d * 32), xv, acc);
+    // eight diagonals at a time: all their loads issued before the products
+    for (int d0 = 0; d0 < D.ndiag; d0 += 8) {
+        Acc a[8], xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int d = d0 + u;
+            a[u] = 0;
+            xv[u] = 0;
+            if (d < D.ndiag) {
+                const int c = row + off_s[d];
+                a[u] = (Acc)__ldg(val + d * 32);
+                if (c >= 0 && c < D.n) xv[u] = (Acc)__ldg(x + c);
+            }
+        }
+        // exactly min(8, ndiag - d0) products (a warp-uniform branch): padded
+        // slots would still occupy the FP64 pipe, the bound of the FP64 pass
+        switch (D.ndiag - d0 < 8 ? D.ndiag - d0 : 8) {
+            case 1: acc = dia_fmas<Acc, 1>(a, xv, acc); break;
+            case 2: acc = dia_fmas<Acc, 2>(a, xv, acc); break;
+            case 3: acc = dia_fmas<Acc, 3>(a, xv, acc); break;
+            case 4: acc = dia_fmas<Acc, 4>(a, xv, acc); break;
+            case 5: acc = dia_fmas<Acc, 5>(a, xv, acc); break;
+            case 6: acc = dia_fmas<Acc, 6>(a, xv, acc); break;
+            case 7: acc = dia_fmas<Acc, 7>(a, xv, acc); break;
+            default: acc = dia_fmas<Acc, 8>(a, xv, acc); break;
+        }
     }
     return acc;
 }
