@@ -547,8 +547,9 @@ def run_precision3d(args, ws, rank, local):
     stream = torch.cuda.Stream()
     out = {}
     for name, prec in (("mixed_fp32", pp.PP_FP32), ("mixed_bf16_basis", pp.PP_FP32_BF16), ("fp64", pp.PP_FP64)):
+        fmt = {"auto": pp.PP_FMT_AUTO, "sell": pp.PP_FMT_SELL, "dia": pp.PP_FMT_DIA, "csr": pp.PP_FMT_CSR}[args.format]
         ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, max_cycles=60, sell_loop=args.sell_loop,
-                           sell_c=args.sell_c)
+                           sell_c=args.sell_c, format=fmt)
 
         def solve():
             poly = pp.pp_build_poly2(ctx, cfg["d1"], cfg["d2"], b)
@@ -714,6 +715,8 @@ def main():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--serve-max-cycles", type=int, default=300)
     ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--format", default="auto", choices=["auto", "sell", "dia", "csr"],
+                    help="device format of the precision_3d arm (pp_opts.format); auto lets the tuner pick")
     ap.add_argument("--sell-c", type=int, default=0, choices=[0, 16, 32],
                     help="SELL chunk height (pp_opts.sell_c): 0 tuner; 16 or 32 fixes it and the block size (256)")
     ap.add_argument("--sell-loop", type=int, default=0, choices=[0, 1, 2, 3, 4],
