@@ -264,8 +264,12 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
     const float *w = (const float *)a.w;
     float *wout = (float *)a.wout;  // FP32 always (a BF16 basis column is written by the scaling kernel)
     const int j = a.j, n = a.n;
-    __shared__ float red[kWarps][kRows];
-    __shared__ float wsh[kRows];
+    // 128-row tiles: four rows per lane and column, so each warp has twice the
+    // loads of the FP64 sweep in flight (the FP32 sweeps are bound by memory
+    // latency, not arithmetic)
+    constexpr int RT = 2 * kRows, QT = RT / 32;
+    __shared__ float red[kWarps][RT];
+    __shared__ float wsh[RT];
     __shared__ float hs[8 * CPW];
     if (a.mode != 0)
         for (int c = tid; c < j; c += kThreads) hs[c] = (float)a.h[c];
@@ -274,23 +278,23 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
 #pragma unroll
     for (int cc = 0; cc < CPW; ++cc) hi[cc] = lo[cc] = 0.f;
     double nrm = 0;
-    const int ntiles = (n + kRows - 1) / kRows;
+    const int ntiles = (n + RT - 1) / RT;
     for (int tile = bid; tile < ntiles; tile += nblk) {
-        const int r0 = tile * kRows;
-        float vv[CPW][kQ];
+        const int r0 = tile * RT;
+        float vv[CPW][QT];
 #pragma unroll
         for (int cc = 0; cc < CPW; ++cc) {
             int c = warp + kWarps * cc;
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) {
+            for (int q = 0; q < QT; ++q) {
                 int row = r0 + lane + 32 * q;
                 vv[cc][q] = (c < j && row < n) ? ld_f32(V + (size_t)c * a.ldv + row) : 0.f;
             }
         }
         if (a.mode == 0) {
-            float wv[kQ];
+            float wv[QT];
 #pragma unroll
-            for (int q = 0; q < kQ; ++q) {
+            for (int q = 0; q < QT; ++q) {
                 int row = r0 + lane + 32 * q;
                 wv[q] = row < n ? __ldg(w + row) : 0.f;
             }
@@ -298,11 +302,11 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
             for (int cc = 0; cc < CPW; ++cc)
                 if (warp + kWarps * cc < j)
 #pragma unroll
-                    for (int q = 0; q < kQ; ++q) hi[cc] = fmaf(vv[cc][q], wv[q], hi[cc]);
+                    for (int q = 0; q < QT; ++q) hi[cc] = fmaf(vv[cc][q], wv[q], hi[cc]);
             continue;
         }
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) {
+        for (int q = 0; q < QT; ++q) {
             float s = 0;
 #pragma unroll
             for (int cc = 0; cc < CPW; ++cc) {
@@ -312,7 +316,7 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
             red[warp][lane + 32 * q] = s;
         }
         __syncthreads();
-        if (tid < kRows) {
+        if (tid < RT) {
             int row = r0 + tid;
             float v = 0;
             if (row < n) {
@@ -331,7 +335,7 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
             for (int cc = 0; cc < CPW; ++cc)
                 if (warp + kWarps * cc < j)
 #pragma unroll
-                    for (int q = 0; q < kQ; ++q) dot2_term(vv[cc][q], wsh[lane + 32 * q], hi[cc], lo[cc]);
+                    for (int q = 0; q < QT; ++q) dot2_term(vv[cc][q], wsh[lane + 32 * q], hi[cc], lo[cc]);
         }
     }
     double acc[CPW];
@@ -759,22 +763,21 @@ int cgs_grid(int n) {
     return tiles < g ? tiles : g;
 }
 
-// Blocks of a CGS pass: one wave of resident blocks (at most 8 per SM of four
-// warps or 4 of eight warps, which bounds the partial-sum buffer), never more
-// than there are tiles.
+// Blocks of a CGS pass: one wave of resident blocks (at most 8 per SM, which
+// bounds the partial-sum buffer at cgs_grid), never more than there are tiles.
 template <typename T, int CPW, int NW>
 static int resident_grid(int n, int cap) {
     static int per_sm = 0;  // one per instantiation
     if (!per_sm) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cgs<T, CPW, NW>, NW * 32, 0);
-        const int most = 32 / NW;
+        const int most = 8;
         if (per_sm < 1) per_sm = 1;
         if (per_sm > most) per_sm = most;
     }
-    int tiles = (n + kRows - 1) / kRows;
     int g = per_sm * num_sms();
     if (cap > 0 && g > cap) g = cap;
-    return tiles < g ? tiles : g;
+    const int most_blocks = cgs_grid(n);  // also caps at the tile count
+    return g < most_blocks ? g : most_blocks;
 }
 
 // TMA-staged sweeps are opt-in (PP_TMA_CGS in the environment): on the bases
