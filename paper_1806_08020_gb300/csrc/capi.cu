@@ -616,12 +616,23 @@ static int64_t sell_padded(int64_t n, const int64_t *rowptr, int cs) {
 // columns of every row increase strictly and there are at most kDiaMax of them.
 static bool dia_offsets(int64_t n, const int64_t *rowptr, const int32_t *colind, std::vector<int> &off) {
     std::set<int> seen;
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-            if (k > rowptr[i] && colind[k] <= colind[k - 1]) return false;
-            seen.insert((int)(colind[k] - i));
-            if ((int)seen.size() > ppk::kDiaMax) return false;
+    std::vector<int> prev;  // the previous row's offsets: stencil rows repeat them
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t k0 = rowptr[i], len = rowptr[i + 1] - k0;
+        bool same = (int64_t)prev.size() == len;
+        for (int64_t t = 0; t < len; ++t) {
+            const int64_t k = k0 + t;
+            if (t > 0 && colind[k] <= colind[k - 1]) return false;
+            same = same && prev[t] == (int)(colind[k] - i);
         }
+        if (same) continue;
+        prev.resize(len);
+        for (int64_t t = 0; t < len; ++t) {
+            prev[t] = (int)(colind[k0 + t] - i);
+            seen.insert(prev[t]);
+        }
+        if ((int)seen.size() > ppk::kDiaMax) return false;
+    }
     off.assign(seen.begin(), seen.end());
     return true;
 }

@@ -528,7 +528,8 @@ inline int restart_basis(const Cycle &cy, const std::vector<double> &H, int ldh,
 // Outputs sorted by the target (SR: Re, |Im|, Im > 0 first; SM: |lam|, Re, Im > 0
 // first); X gets unit vectors (a pair's Re, Im columns scaled by its complex norm).
 inline void write_outputs(int target, int64_t n, const Slots &sl, const RitzOut &R, const std::vector<double> &Yh,
-                          double *lam_re, double *lam_im, double *resid, double *X, double &maxres) {
+                          double *lam_re, double *lam_im, double *resid, double *X, double &maxres,
+                          std::vector<int> *order = nullptr) {
     const int nw = sl.nw;
     std::vector<int> srt(nw);
     for (int s = 0; s < nw; ++s) srt[s] = s;
@@ -544,6 +545,7 @@ inline void write_outputs(int target, int64_t n, const Slots &sl, const RitzOut 
         }
         return lim[a] > lim[b];
     });
+    if (order) *order = srt;
     maxres = 0;
     for (int s = 0; s < nw; ++s) {
         int o = srt[s];
@@ -575,6 +577,37 @@ inline void write_outputs(int target, int64_t n, const Slots &sl, const RitzOut 
             }
         }
     }
+}
+
+// The eigenvector block of write_outputs formed on the device and copied once
+// into the caller's X: slot s (in the sorted order) is the column of Y (FP64,
+// leading dimension ld) scaled to unit (complex) norm, the columns of a pair
+// being its Re and Im parts (Im sign as in write_outputs).  Xd: FP64 device
+// scratch of ld x nw.  The norms are summed on the device.
+inline pp_status vectors_out(pp_ctx *c, int64_t n, const Slots &sl, const RitzOut &R, const double *Y, int64_t ld,
+                             const std::vector<int> &srt, double *Xd, double *X) {
+    const int nw = sl.nw;
+    double *nrm = c->d_small + 3200;  // 2 per slot
+    CK(cudaMemsetAsync(nrm, 0, (size_t)2 * nw * sizeof(double), c->stream));
+    for (int s = 0; s < nw; ++s) {
+        const int o = srt[s];
+        const bool pair = sl.partner[o] != o;
+        const int cr = pair ? std::min(o, sl.partner[o]) : o, ci = pair ? cr + 1 : o;
+        ppk::launch_norm2((int)n, Y + (size_t)cr * ld, c->d_part, c->d_ticket, nrm + 2 * s, c->stream);
+        CKS(check_launch(c));
+        if (pair) {
+            ppk::launch_norm2((int)n, Y + (size_t)ci * ld, c->d_part, c->d_ticket, nrm + 2 * s + 1, c->stream);
+            CKS(check_launch(c));
+        }
+        const bool first = !pair || R.lim[o] > 0 || (R.lim[o] == 0 && o == cr);
+        const double sgn = (pair && !first && R.lim[cr] < 0) ? -1.0 : 1.0;
+        const double *src = (!pair || first) ? Y + (size_t)(pair ? cr : o) * ld : Y + (size_t)ci * ld;
+        ppk::launch_slot_scale((int)n, src, nrm + 2 * s, sgn, Xd + (size_t)s * ld, c->stream);
+        CKS(check_launch(c));
+    }
+    CK(cudaMemcpy2DAsync(X, (size_t)n * 8, Xd, (size_t)ld * 8, (size_t)n * 8, nw, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PP_OK;
 }
 
 }  // namespace ppi

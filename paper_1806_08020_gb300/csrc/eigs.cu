@@ -150,10 +150,11 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
         j0 = kk;
         S.t_restart += now() - th0;
     }
-    std::vector<double> Yh;
-    if (X) CKS(download_vecs(c, D.Y64, ldv, cy.sl.nw, Yh, ppk::F64));
     double maxres = 0;
-    write_outputs(c->opts.target, n, cy.sl, R, Yh, lam_re, lam_im, resid, X, maxres);
+    std::vector<int> srt;
+    write_outputs(c->opts.target, n, cy.sl, R, {}, lam_re, lam_im, resid, nullptr, maxres, &srt);
+    // eigenvectors scaled and ordered on the device, one copy into X (AY64 is free after the last test)
+    if (X) CKS(vectors_out(c, n, cy.sl, R, D.Y64, ldv, srt, D.AY64, X));
     *nout = cy.sl.nw;
     S.converged = converged ? 1 : 0;
     S.max_resid = maxres;

@@ -651,6 +651,13 @@ __global__ void k_unit_into(int n, const double *x, const double *nrm2, T *dst) 
     }
 }
 
+// dst = src * sgn / sqrt(nrm2[0] + nrm2[1]) (an output eigenvector scaled to
+// unit real or complex norm).
+__global__ void k_slot_scale(int n, const double *src, const double *nrm2, double sgn, double *dst) {
+    const double sc = sgn / sqrt(nrm2[0] + nrm2[1]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i] * sc;
+}
+
 // A BF16 basis column: out = bf16(w * scal) (w is the FP32 orthogonalised vector).
 __global__ void k_scale_bf16(int n, const float *w, const double *scal, __nv_bfloat16 *out) {
     const float sc = (float)*scal;
@@ -952,6 +959,10 @@ void launch_norm2(int n, const double *x, double *part, unsigned *ticket, double
     if (g > num_sms() * 4) g = num_sms() * 4;
     if (g < 1) g = 1;
     k_norm2<<<g, kThreads, 0, st>>>(n, x, part, ticket, out);
+}
+
+void launch_slot_scale(int n, const double *src, const double *nrm2, double sgn, double *dst, cudaStream_t st) {
+    k_slot_scale<<<num_sms() * 4, kThreads, 0, st>>>(n, src, nrm2, sgn, dst);
 }
 
 void launch_unit_into(Prec p, int n, const double *x, const double *nrm2, void *dst, cudaStream_t st) {

@@ -147,6 +147,8 @@ void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st);
 // out[0] = ||x||^2 (FP64 x on the device; part holds one double per block, at
 // most 4 blocks per SM; ticket is zero before and after).
 void launch_norm2(int n, const double *x, double *part, unsigned *ticket, double *out, cudaStream_t st);
+// dst = src * sgn / sqrt(nrm2[0] + nrm2[1]) (FP64 device vectors).
+void launch_slot_scale(int n, const double *src, const double *nrm2, double sgn, double *dst, cudaStream_t st);
 // dst = x / sqrt(nrm2[0]) stored in precision p.
 void launch_unit_into(Prec p, int n, const double *x, const double *nrm2, void *dst, cudaStream_t st);
 // out (BF16, n) = w * scal (w FP32): the new column of a BF16 basis

@@ -354,7 +354,7 @@ def pp_eigs(ctx: Context, p: Poly | None, nev: int, m: int, k: int, rtol: float,
     n = ctx.n
     cap = nev + 1
     lre, lim, res = np.zeros(cap), np.zeros(cap), np.zeros(cap)
-    X = np.zeros((cap, n)) if want_vectors else None
+    X = np.empty((cap, n)) if want_vectors else None  # slot-major: the library writes column s at X[s]
     v0a, v0p = _vec_in(v0, n) if v0 is not None else (None, None)
     nout = C.c_int()
     st = pp_stats()
@@ -363,7 +363,8 @@ def pp_eigs(ctx: Context, p: Poly | None, nev: int, m: int, k: int, rtol: float,
                                 _dp(X) if X is not None else None, _dp(res), C.byref(nout), C.byref(st)),
                     allow=(PP_OK, PP_ENOTCONV))
     k_ = nout.value
-    return EigsResult(lre[:k_] + 1j * lim[:k_], X[:k_].T.copy() if X is not None else None, res[:k_], status,
+    # X[:, j] is slot j's vector: a transposed view of the slot-major block (no copy)
+    return EigsResult(lre[:k_] + 1j * lim[:k_], X[:k_].T if X is not None else None, res[:k_], status,
                       st.to_dict())
 
 
@@ -447,7 +448,7 @@ def pp_batch_solve(b: Batch, d, bvecs, v0s, nev: int, m: int, k: int, rtol: floa
     for i in range(cnt):
         k_ = nout[i]
         st = stats[i].to_dict()
-        out.append(EigsResult(lre[i][:k_] + 1j * lim[i][:k_], Xs[i][:k_].T.copy() if want_vectors else None,
+        out.append(EigsResult(lre[i][:k_] + 1j * lim[i][:k_], Xs[i][:k_].T if want_vectors else None,
                               res[i][:k_], PP_OK if st["converged"] else PP_ENOTCONV, st))
     return status, out
 
@@ -516,7 +517,7 @@ def pp_server_result(s: Server, rid: int):
     _check(status, allow=(PP_OK, PP_ENOTCONV))
     k_ = nout.value
     del s.meta[rid]
-    return EigsResult(lre[:k_] + 1j * lim[:k_], X[:k_].T.copy() if X is not None else None, res[:k_], status,
+    return EigsResult(lre[:k_] + 1j * lim[:k_], X[:k_].T if X is not None else None, res[:k_], status,
                       st.to_dict()), lat.value
 
 
