@@ -65,7 +65,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if failed:
         raise RuntimeError("build failed:\n" + "\n".join(failed))
     tmp = LIB + ".tmp"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))

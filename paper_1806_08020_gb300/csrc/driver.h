@@ -3,6 +3,8 @@
 // the FP64 Ritz test on A, and the FP64 refinement of the mixed-precision mode.
 #pragma once
 
+#include <thread>
+
 #include "ctx.h"
 
 #include <algorithm>
@@ -579,6 +581,27 @@ inline void write_outputs(int target, int64_t n, const Slots &sl, const RitzOut 
     }
 }
 
+// Fault in the pages of a large host buffer with several threads (one write
+// per 4 KB page).  A device-to-host copy into pages never touched is slow: the
+// copy then takes every page fault itself.
+inline void touch_pages(void *p, size_t bytes) {
+    char *b = (char *)p;
+    const size_t page = 4096;
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt < 1 ? 1 : (nt > 16 ? 16 : nt);
+    if (bytes < ((size_t)16 << 20)) nt = 1;
+    const size_t chunk = (bytes / nt + page - 1) / page * page;
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) {
+        const size_t lo = t * chunk, hi = std::min(bytes, lo + chunk);
+        if (lo >= hi) break;
+        th.emplace_back([b, lo, hi, page]() {
+            for (size_t off = lo; off < hi; off += page) b[off] = 0;
+        });
+    }
+    for (auto &x : th) x.join();
+}
+
 // The eigenvector block of write_outputs formed on the device and copied once
 // into the caller's X: slot s (in the sorted order) is the column of Y (FP64,
 // leading dimension ld) scaled to unit (complex) norm, the columns of a pair
@@ -605,6 +628,7 @@ inline pp_status vectors_out(pp_ctx *c, int64_t n, const Slots &sl, const RitzOu
         ppk::launch_slot_scale((int)n, src, nrm + 2 * s, sgn, Xd + (size_t)s * ld, c->stream);
         CKS(check_launch(c));
     }
+    touch_pages(X, (size_t)n * nw * sizeof(double));  // while the device scales
     CK(cudaMemcpy2DAsync(X, (size_t)n * 8, Xd, (size_t)ld * 8, (size_t)n * 8, nw, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PP_OK;
