@@ -32,6 +32,34 @@ def test_library_exports_every_declared_symbol():
     assert set(pp.exported_symbols()) <= names
 
 
+def _header_struct_fields(text, name):
+    """(field, C type) pairs of ``typedef struct { ... } name;`` in the header."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    out = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if decl:
+            ctype, field = decl.rsplit(None, 1)
+            out.append((field.lstrip("*"), ctype + ("*" if field.startswith("*") else "")))
+    return out
+
+
+@pytest.mark.parametrize("name", ["pp_opts", "pp_stats"])
+def test_binding_structs_match_the_header(name):
+    """The ctypes structures of the binding have the header's fields, in order,
+    with the same widths (a mismatch would shift every later field)."""
+    import ctypes
+    text = open(os.path.join(ROOT, "include", "pp.h")).read()
+    fields = _header_struct_fields(text, name)
+    py = getattr(pp, name)._fields_
+    assert [f for f, _ in fields] == [f for f, _ in py]
+    width = {"int": 4, "int32_t": 4, "int64_t": 8, "double": 8, "void*": ctypes.sizeof(ctypes.c_void_p)}
+    for (f, ctype), (_, pytype) in zip(fields, py):
+        assert width[ctype] == ctypes.sizeof(pytype), (f, ctype, pytype)
+
+
 def _match(a, b):
     """max distance from each of a to the nearest of b (relative)."""
     return max(np.min(np.abs(b - z)) / max(1.0, abs(z)) for z in a)
