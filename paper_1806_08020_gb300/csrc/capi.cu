@@ -770,11 +770,29 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     int64_t nnz = rowptr[n];
     if (rowptr[0] != 0 || nnz < 0 || nnz >= (int64_t)1 << 31 || n >= (int64_t)1 << 31)
         return pp_fail(PP_EINVAL, "pp_create: rowptr must start at 0 and nnz, n < 2^31");
+    // one pass over the entries: validation, the column sums of ||A||_1, the
+    // Gershgorin bound of the shift, and whether 16-bit column offsets fit
+    // (row pointers first: with them monotone and ending at nnz, every row stays inside the arrays)
     for (int64_t i = 0; i < n; ++i)
         if (rowptr[i + 1] < rowptr[i]) return pp_fail(PP_EINVAL, "pp_create: rowptr not monotone at %lld", (long long)i);
-    for (int64_t k = 0; k < nnz; ++k)
-        if (colind[k] < 0 || colind[k] >= n || !std::isfinite(vals[k]))
-            return pp_fail(PP_EINVAL, "pp_create: bad entry %lld", (long long)k);
+    std::vector<double> colsum(n, 0.0);
+    double gl = INFINITY;
+    bool fits16 = true;
+    for (int64_t i = 0; i < n; ++i) {
+        double diag = 0, off = 0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            const int64_t col = colind[k];
+            const double v = vals[k];
+            if (col < 0 || col >= n || !std::isfinite(v)) return pp_fail(PP_EINVAL, "pp_create: bad entry %lld", (long long)k);
+            colsum[col] += std::fabs(v);
+            if (col == i)
+                diag += v;
+            else
+                off += std::fabs(v);
+            fits16 = fits16 && std::llabs((long long)(col - i)) <= 32767;
+        }
+        gl = std::min(gl, diag - off);
+    }
     pp_ctx *c = new pp_ctx();
     pp_opts_default(&c->opts);
     if (opts) c->opts = *opts;
@@ -785,19 +803,6 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     c->n = n;
     c->nnz = nnz;
     // ||A||_1 and the Gershgorin shift on the host (exact, deterministic)
-    std::vector<double> colsum(n, 0.0);
-    double gl = INFINITY;
-    for (int64_t i = 0; i < n; ++i) {
-        double diag = 0, off = 0;
-        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-            colsum[colind[k]] += std::fabs(vals[k]);
-            if (colind[k] == i)
-                diag += vals[k];
-            else
-                off += std::fabs(vals[k]);
-        }
-        gl = std::min(gl, diag - off);
-    }
     c->norm1 = *std::max_element(colsum.begin(), colsum.end());
     if (std::isnan(c->opts.sigma)) {
         if (c->opts.target == PP_TARGET_SR)
@@ -866,13 +871,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     int fmt = c->opts.format;
     if (fmt == PP_FMT_AUTO) fmt = (best_pad <= (int64_t)(1.3 * (double)nnz) + 32 * 8) ? PP_FMT_SELL : PP_FMT_CSR;
     if (cands.empty()) fmt = PP_FMT_CSR;
-    bool off16 = c->opts.sell_index == 0;
-    for (int64_t i = 0; i < n && off16; ++i)
-        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
-            if (std::llabs((long long)colind[k] - (long long)i) > 32767) {
-                off16 = false;
-                break;
-            }
+    const bool off16 = c->opts.sell_index == 0 && fits16;
     ppk::Matrix M;
     M.n = (int)n;
     M.prec = pr;
