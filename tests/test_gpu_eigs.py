@@ -205,6 +205,15 @@ def test_eigs_argument_errors():
     bad = inputs.CSR(3, np.array([0, 1, 2, 3]), np.array([0, 5, 2], dtype=np.int32), np.ones(3))
     with pytest.raises(pp.PPError):
         pp.pp_create(bad)
+    nan = inputs.CSR(3, np.array([0, 1, 2, 3]), np.array([0, 1, 2], dtype=np.int32), np.array([1.0, np.nan, 1.0]))
+    with pytest.raises(pp.PPError):
+        pp.pp_create(nan)
+    # a non-monotone row pointer whose middle entry points past the arrays: rejected before any entry is read
+    back = inputs.CSR(3, np.array([0, 9, 1, 3]), np.array([0, 1, 2], dtype=np.int32), np.ones(3))
+    with pytest.raises(pp.PPError):
+        pp.pp_create(back)
+    # the column-offset width follows the widest |col - row| (16 bits when every one is below 2^15)
+    assert pp.pp_format_info(pp.pp_create(inputs.banded_random(40000, 3, 1), format=pp.PP_FMT_SELL))["index_bits"] == 16
 
 
 def test_eigs_not_converged_status():
