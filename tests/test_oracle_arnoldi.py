@@ -160,3 +160,23 @@ def test_example6_counts():
     assert abs(np.mean(vo40) / g["vops_d40"] - 1) < 0.10
     # one cycle = 40 (GMRES) + 50*40 mvps; two cycles add 30*40
     assert 2000 <= np.mean(mv40) <= 3300
+
+
+def test_cgs2_is_the_orthogonal_projection():
+    """CGS2 (Section 4: one orthogonalisation and one reorthogonalisation pass)
+    against the projection computed another way (least squares): the output is
+    w - V c with c = argmin ||w - V c||, and it is orthogonal to V to working
+    precision even when w lies almost in span(V); a single pass is not."""
+    rng = np.random.default_rng(4)
+    n, j = 400, 25
+    V, _ = np.linalg.qr(rng.standard_normal((n, j)))
+    for eps in (1.0, 1e-10):
+        w = V @ rng.standard_normal(j) + eps * rng.standard_normal(n)
+        out, h = O.cgs2(V, w.copy(), O.Counters())
+        coef = np.linalg.lstsq(V, w, rcond=None)[0]
+        assert np.allclose(h, coef, rtol=0, atol=1e-13 * np.linalg.norm(w))
+        assert np.linalg.norm(V.T @ out) <= 1e-14 * np.linalg.norm(w) * np.sqrt(j)
+        assert np.linalg.norm(out - (w - V @ coef)) <= 1e-13 * np.linalg.norm(w)
+    # one pass only (the planted mistake): orthogonality is lost for the nearly dependent w
+    one = w - V @ (V.T @ w)
+    assert np.linalg.norm(V.T @ one) > 1e3 * np.linalg.norm(V.T @ out)
