@@ -319,7 +319,8 @@ def run_ours(args, ws, rank, local):
                  "precision": "FP32 apply/basis, FP64 residuals and refinement on A",
                  "cycles_per_solve": mixed_cycles, "fp64_cycles": r32.stats["fp64_cycles"], "max_resid": mixed_res,
                  # eigenvalue condition numbers here reach 1e17: the residual bound is the accuracy statement
-                 "rel_err_vs_fp64_per_eigenpair": [float("%.3g" % e) for e in _match_errors(r32.lam, res.lam)]}
+                 "rel_err_vs_fp64_per_eigenpair": [float("%.3g" % e) for e in _match_errors(r32.lam, res.lam)],
+                 "rel_err_vs_oracle_per_eigenpair": _oracle_errors(r32.lam) if rank == 0 else None}
     ctx32.close()
 
     out = {
@@ -332,6 +333,10 @@ def run_ours(args, ws, rank, local):
                    "parallelism": f"replicas x{ws}",
                    "l2": "working set (basis 51 x 8 MB + matrix 60 MB) exceeds the 129 MB L2",
                    "cycles_per_solve": cycles, "max_resid": maxres,
+                   # against the oracle's solve of the same inputs; the operator is so non-normal
+                   # (eigenvalue condition numbers up to ~1e17) that residual <= rtol is the accuracy
+                   # statement and these distances only say which pseudo-eigenvalues were found
+                   "rel_err_vs_oracle_per_eigenpair": _oracle_errors(res.lam) if rank == 0 else None,
                    # Section 4's counters for one solve (eigensolve, and the GMRES build), as in the
                    # paper's tables: mvps = products with A, dots = inner products, vops = vector ops
                    "counters_per_solve": counters,
@@ -522,6 +527,23 @@ def run_serve(args, ws, rank, local):
             "load": {"offered_req_per_s": round(offered, 2), "achieved_req_per_s": round(len(done) / wall, 2),
                      "converged": conv, "requests": len(done)},
             "gpu_launches": int(pp.pp_server_launch_count(S)), "clocks": clk.summary()}
+
+
+def _oracle_errors(lam: np.ndarray) -> list[float] | None:
+    """Per-eigenpair |lam - nearest oracle eigenvalue| / |oracle eigenvalue| against the oracle's
+    full solve of the n = 1e6 workload (tests/golden/plain_large_oracle.txt, written by a script
+    that runs only the oracle; seed of rank 0).  None when the file is missing or unreadable."""
+    try:
+        ref = []
+        for line in open(os.path.join(ROOT, "tests", "golden", "plain_large_oracle.txt")):
+            f = line.split()
+            if f and f[0].startswith("lam") and f[0][3:].isdigit():
+                ref.append(complex(float(f[1]), float(f[2])))
+        if not ref:
+            return None
+        return [float("%.3g" % e) for e in _match_errors(np.asarray(lam), np.asarray(ref))]
+    except Exception:
+        return None
 
 
 def _match_errors(lam_a: np.ndarray, lam_b: np.ndarray) -> list[float]:
