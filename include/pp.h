@@ -453,6 +453,24 @@ pp_status pp_leja_order(int count, const double *re, const double *im, double *o
 pp_status pp_add_stability_roots(int count, const double *re, const double *im, int cap,
                                  double *out_re, double *out_im, int *out_count);
 
+/*
+ * pp_restart_basis — the host step of one thick restart of pp_eigs (Section 4;
+ * Example 2's harmonic variant when harmonic != 0), from the Arnoldi relation
+ * Op V_m = V_{m+1} H with H ((m+1) x m, column-major, ldh >= m+1): the values
+ * (Ritz values of H_m, or harmonic Ritz values with respect to target) ordered
+ * by distance to target, the k nearest kept (k - 1 when a conjugate pair would
+ * split), and
+ *   Ritz:     Q = (m x kk, ld m) orthonormal basis of their vectors' Re/Im
+ *             parts; the new basis is [V_m Q, v_{m+1}];
+ *   harmonic: Q = P ((m+1) x (kk+1), ld m+1); the new basis is V_{m+1} P.
+ * Hn (ldh x m) receives the new leading (kk+1) x kk block, zero elsewhere.
+ * Host arrays; Q needs (m+1) * (m+1) doubles.  Outputs *kk and the values in
+ * order (re, im: m each, may be NULL).  Requires 1 <= k < m <= 127.
+ * Errors: PP_EINVAL, PP_ENUMERIC (QR failed, H_m - target I singular).
+ */
+pp_status pp_restart_basis(int m, const double *H, int ldh, int k, double target, int harmonic, double *Q,
+                           double *Hn, int *kk, double *re, double *im);
+
 #ifdef __cplusplus
 }
 #endif

@@ -165,3 +165,23 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
     if (!converged) return pp_fail(PP_ENOTCONV, "pp_eigs: not converged in %lld cycles", (long long)S.cycles);
     return PP_OK;
 }
+
+extern "C" pp_status pp_restart_basis(int m, const double *H, int ldh, int k, double target, int harmonic,
+                                      double *Q, double *Hn, int *kk, double *re, double *im) {
+    if (!H || !Q || !Hn || !kk || m < 2 || m > 127 || k < 1 || k >= m || ldh < m + 1)
+        return pp_fail(PP_EINVAL, "pp_restart_basis: need 1 <= k < m <= 127, ldh >= m + 1");
+    std::vector<double> Hv((size_t)ldh * m);
+    std::copy(H, H + Hv.size(), Hv.begin());
+    Cycle cy;
+    CKS(wanted_set(Hv, ldh, m, 1, target, cy, harmonic != 0));
+    std::vector<double> Qv, Hnv;
+    const int kept = restart_basis(cy, Hv, ldh, k, Qv, Hnv);
+    std::copy(Qv.begin(), Qv.end(), Q);
+    std::copy(Hnv.begin(), Hnv.end(), Hn);
+    *kk = kept;
+    for (int i = 0; i < m; ++i) {
+        if (re) re[i] = cy.nu[cy.order[i]].real();
+        if (im) im[i] = cy.nu[cy.order[i]].imag();
+    }
+    return PP_OK;
+}

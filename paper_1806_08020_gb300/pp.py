@@ -96,6 +96,7 @@ _SIGS = {
     "pp_harmonic_ritz": (C.c_int, [C.c_int, _D, C.c_int, _D, _D]),
     "pp_leja_order": (C.c_int, [C.c_int, _D, _D, _D, _D]),
     "pp_add_stability_roots": (C.c_int, [C.c_int, _D, _D, C.c_int, _D, _D, _I]),
+    "pp_restart_basis": (C.c_int, [C.c_int, _D, C.c_int, C.c_int, C.c_double, C.c_int, _D, _D, _I, _D, _D]),
 }
 
 
@@ -566,3 +567,18 @@ def pp_add_stability_roots(roots) -> np.ndarray:
     cnt = C.c_int()
     _check(LIB.pp_add_stability_roots(r.size, _dp(re), _dp(im), cap, _dp(ore), _dp(oim), C.byref(cnt)))
     return (ore + 1j * oim)[: cnt.value]
+
+
+def pp_restart_basis(H: np.ndarray, k: int, target: float, harmonic: bool = False):
+    """Host step of one thick restart (see include/pp.h): returns (Q or P, Hn, kk, ordered values)."""
+    H = np.asfortranarray(H, dtype=np.float64)
+    m = H.shape[1]
+    Q = np.zeros((m + 1) * (m + 1))
+    Hn = np.zeros((m + 1, m), order="F")
+    kk = C.c_int()
+    re, im = np.zeros(m), np.zeros(m)
+    _check(LIB.pp_restart_basis(int(m), H.ctypes.data_as(_D), int(m + 1), int(k), float(target), int(bool(harmonic)),
+                                _dp(Q), Hn.ctypes.data_as(_D), C.byref(kk), _dp(re), _dp(im)))
+    kv = kk.value
+    rows, cols = (m + 1, kv + 1) if harmonic else (m, kv)
+    return Q[: rows * cols].reshape((rows, cols), order="F"), Hn, kv, re + 1j * im

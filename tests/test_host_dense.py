@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import oracle.ppa as ppa
 from paper_1806_08020_gb300 import inputs
 
 pp = pytest.importorskip("paper_1806_08020_gb300.pp")
@@ -169,3 +170,58 @@ def test_host_entry_points_reject_bad_input():
         pp.pp_leja_order(np.array([1 + 1j, 2 - 1j]))
     with pytest.raises(pp.PPError):
         pp.pp_harmonic_ritz(np.zeros((3, 2)))
+
+
+def _arnoldi_dense(B, v, m):
+    n = B.shape[0]
+    V = np.zeros((n, m + 1))
+    H = np.zeros((m + 1, m))
+    V[:, 0] = v / np.linalg.norm(v)
+    for j in range(m):
+        w = B @ V[:, j]
+        for _ in range(2):
+            h = V[:, : j + 1].T @ w
+            w = w - V[:, : j + 1] @ h
+            H[: j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        V[:, j + 1] = w / H[j + 1, j]
+    return V, H
+
+
+@pytest.mark.parametrize("harmonic", [False, True])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_restart_basis_matches_oracle(harmonic, seed):
+    """The library's host restart step (Ritz or harmonic, Section 4 / Example 2)
+    against the oracle's: the same ordered values, the same kept subspace, and
+    the Arnoldi relation with the new basis."""
+    rng = np.random.default_rng(seed)
+    n, m, k, tau = 80, 16, 7, 1.0
+    B = rng.standard_normal((n, n)) / np.sqrt(n) + np.diag(np.linspace(0.0, 3.0, n))
+    V, H = _arnoldi_dense(B, rng.standard_normal(n), m)
+    Q, Hn, kk, vals = pp.pp_restart_basis(H, k, tau, harmonic)
+    if harmonic:
+        K, cvec = O.harmonic_restart_matrix(H, m, tau)
+        nu = np.linalg.eigvals(K)
+    else:
+        cvec = None
+        nu = np.linalg.eigvals(H[:m, :m])
+    order = ppa.ritz_order(nu, tau)
+    assert np.allclose(vals, nu[order], rtol=1e-10, atol=1e-12)
+    assert kk == (k - 1 if nu[order[k - 1]].imag > 0 else k)
+    Vk = V @ Q if harmonic else np.column_stack([V[:, :m] @ Q, V[:, m]])
+    assert Vk.shape[1] == kk + 1
+    assert np.allclose(Vk.T @ Vk, np.eye(kk + 1), atol=1e-12)
+    assert np.linalg.norm(B @ Vk[:, :kk] - Vk @ Hn[: kk + 1, :kk]) <= 1e-11 * np.linalg.norm(B, 2)
+    # the oracle's restart from its own vectors spans the same space
+    w, S = np.linalg.eig(K if harmonic else H[:m, :m])
+    o = ppa.ritz_order(w, tau)
+    cols = []
+    for i in o[:kk]:
+        if w[i].imag == 0:
+            cols.append(S[:, i].real)
+        elif w[i].imag > 0:
+            cols += [S[:, i].real, S[:, i].imag]
+    Qo, _ = np.linalg.qr(np.stack(cols, axis=1))
+    Vo, _ = O.thick_restart(V, H, m, Qo, cvec)
+    Pk, Po = Vk[:, :kk], Vo[:, :kk]
+    assert np.linalg.norm(Pk @ (Pk.T @ Po) - Po) <= 1e-9
