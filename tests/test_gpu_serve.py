@@ -114,6 +114,13 @@ def test_admission_by_memory():
     assert seen_queue and len(done) == 3
     for res, lat in done.values():
         assert res.status in (0, 1)
+    # a request that alone exceeds the budget is refused at submission (nothing queued)
+    tiny = pp.pp_server_create(mem_budget=int(0.5 * need), precision=pp.PP_FP32)
+    A, d, nev, m, k, seed = reqs[0]
+    with pytest.raises(pp.PPError) as refused:
+        pp.pp_server_submit(tiny, A, d, nev, m, k, 1e-8, inputs.start_vector(A.n, seed, 0))
+    assert refused.value.status == pp.PP_ENOMEM
+    assert pp.pp_server_step(tiny) == (0, 0)
 
 
 def test_request_stream_small():
