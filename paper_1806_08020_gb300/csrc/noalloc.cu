@@ -24,7 +24,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device, looked up once per device.
+// Device address of g_scratch on the current device, looked up once per device
+// and kept for the life of the process (a cudaDeviceReset after the first call
+// would leave it stale; the header says so).
 pp_status scratch_on_current_device(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -93,24 +93,28 @@ def test_precision_3d_small_closed_form(precision):
         assert abs(res.lam[j] - z) <= 10 * kj * (r + res.resid[j]) * nA + 1e-10 * abs(z), (z, res.lam[j])
 
 
-def test_precision_3d_full_size():
-    """N = 160 (n = 4,096,000), beta = 50, double polynomial 10 x 20, Arnoldi(40, 21), nev = 16, FP32 + refine.
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_precision_3d_full_size(precision):
+    """N = 160 (n = 4,096,000), beta = 50, double polynomial 10 x 20, Arnoldi(40, 21), nev = 16.
 
-    Bounded at 15 cycles: the eigenvalue condition numbers of this operator
-    (~1e7) put the FP32 phase at its floor early and the FP64 continuation
-    converges slowly; the test asserts the residual of every pair reported as
-    converged and records how many converged within the bound.
+    Binding at the benchmark's size: the solve must converge (PP_OK) within
+    four cycles (measured: two FP32 cycles and the FP64 refinement for the
+    mixed path, no FP64 cycle; two FP64 cycles for the FP64 path), every
+    returned slot (16, one more if a conjugate pair straddles the boundary)
+    must meet ||A x - lam x|| <= 1e-8 ||A||_1 recomputed on the CPU from the
+    returned vectors, and every eigenvalue must lie within 10 kappa_j ||r||
+    ||A||_1 of a closed-form eigenvalue (kappa_j of the x-mode, ~1e7 here).
     """
     from paper_1806_08020_gb300 import pp
     cfg = inputs.precision_3d()
-    Acsr, res = run_3d(160, 50.0, cfg["d1"], cfg["d2"], cfg["m"], cfg["k"], cfg["nev"], cfg["seed"], pp.PP_FP32,
-                       max_cycles=15)
-    A = O.to_scipy(Acsr)
-    assert res.status in (pp.PP_OK, pp.PP_ENOTCONV)
-    rc = cpu_residuals(A, res.lam, res.X)
-    ok = res.resid <= 1e-8
-    assert np.all(rc[ok] <= 1.01e-8)
-    lam, kap = closed_form_3d(160, 50.0)
-    print("3-D full size:", {k: res.stats[k] for k in ("cycles", "fp64_cycles", "nconv", "t_total", "t_apply",
-                                                       "max_resid")},
-          "converged", int(ok.sum()), "of", res.lam.size, "max kappa of the 16 smallest", kap[:16].max())
+    prec = pp.PP_FP32 if precision == "fp32" else pp.PP_FP64
+    Acsr, res = run_3d(160, 50.0, cfg["d1"], cfg["d2"], cfg["m"], cfg["k"], cfg["nev"], cfg["seed"], prec,
+                       max_cycles=4)
+    print("3-D full size:", precision, {k: res.stats[k] for k in ("cycles", "fp64_cycles", "nconv", "t_total",
+                                                                 "t_apply", "max_resid")})
+    assert res.status == pp.PP_OK
+    assert res.stats["cycles"] <= 4
+    if precision == "fp32":
+        assert res.stats["fp64_cycles"] == 0
+    assert res.lam.size in (cfg["nev"], cfg["nev"] + 1)
+    check(Acsr, res, 160, 50.0, cfg["nev"])
