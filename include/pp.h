@@ -92,6 +92,10 @@ typedef struct {
     int restart;        /* pp_eigs restart: PP_RESTART_RITZ (default) keeps Ritz vectors;
                            PP_RESTART_HARMONIC keeps harmonic Ritz vectors (the harmonic
                            Arnoldi variant of Example 2, for interior targets) */
+    int dia_loop;       /* DIA row loop: 0 (default) = the tuner picks; 1 = one row per thread;
+                           2 = four or 3 = two consecutive rows per thread with 16- or 8-byte
+                           loads (FP32 contexts; taken only when the vectors are so aligned,
+                           else one row per thread) */
 } pp_opts;
 
 /* Counters of Section 4 (mvps, dot products, vector operations) plus timings. */
@@ -163,10 +167,10 @@ pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);
  * pp_format_info — the device format of A chosen at pp_create: fmt
  * (PP_FMT_CSR, PP_FMT_SELL or PP_FMT_DIA), the SELL chunk height (0 otherwise),
  * the column index width in bits (16 or 32; 0 for DIA), the block size of the product kernels, the
- * SELL row loop (0: unrolled by four; 1: the loads of up to eight entries
- * issued together; 2: slice data staged by bulk copies; 3: two rows per
- * thread), and the stored entries including padding.  Any output pointer
- * may be NULL.
+ * row loop (SELL: 0 unrolled by four; 1 the loads of up to eight entries
+ * issued together; 2 slice data staged by bulk copies; 3 two rows per
+ * thread.  DIA: 0 one row per thread; 1 four, 2 two rows per thread), and the
+ * stored entries including padding.  Any output pointer may be NULL.
  */
 pp_status pp_format_info(const pp_ctx *ctx, int *fmt, int *chunk, int *index_bits, int *threads, int *row_loop,
                          int64_t *stored);
@@ -223,6 +227,16 @@ pp_status pp_build_poly2(pp_ctx *ctx, int d1, int d2, const double *b, pp_poly *
  */
 pp_status pp_poly_from_roots(pp_ctx *ctx, int count, const double *re, const double *im,
                              pp_poly **out);
+
+/*
+ * pp_poly2_from_roots — double polynomial (Section 8) with given roots:
+ * y = pi_2(tau(A)) x with tau(z) = 1 - pi_1(z), pi_1 having roots re1/im1
+ * (count1) and pi_2 roots re2/im2 (count2), each applied in the given order
+ * (no reordering, no added roots); the same rules as pp_poly_from_roots for
+ * each list.  Errors: PP_EINVAL.
+ */
+pp_status pp_poly2_from_roots(pp_ctx *ctx, int count1, const double *re1, const double *im1, int count2,
+                              const double *re2, const double *im2, pp_poly **out);
 
 /*
  * pp_poly_roots — roots in application order (including added roots).
@@ -316,13 +330,16 @@ pp_status pp_orthogonalize(pp_ctx *ctx, const void *V_dev, int64_t ldv, int j, v
  * receives w2 / ||w2||; h_dev (device, j + 1 doubles) receives h1 + h2 and
  * then ||w2||.  Asynchronous: nothing is copied to the host.
  *
- * Scratch: a file-scope __device__ array of about 636 KB (partial sums for at
- * most 608 blocks x 130 values, the two coefficient vectors, the norm and the
+ * Scratch: a file-scope __device__ array of about 656 KB ((608 + 19) x 130 +
+ * 552 doubles: partial sums for at most 608 blocks x 130 values and the sums
+ * of their groups of 32, the two coefficient vectors, the norm and the
  * reduction ticket), held by every GPU that loads the library until the
  * process exits.  Limits: 1 <= j <= 128 (beyond that PP_EINVAL with a
  * message); n < 2^31.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call uses the same array and
+ * device address (cudaGetSymbolAddress) with that device current and keeps it
+ * for the life of the process; make that first call before any stream
+ * capture, and do not reset the device (cudaDeviceReset) after it: the kept
+ * address would then be stale.  Every call uses the same array and
  * leaves the last call's contents in it (the ticket is cleared at the start
  * of each call); calls that overlap on the GPU, e.g. on two streams, race on
  * it, so issue them on one stream or otherwise serialise them.
@@ -411,6 +428,20 @@ int64_t pp_server_launch_count(const pp_server *s);
  * when FP32 cannot reach rtol). */
 int64_t pp_server_request_bytes(const pp_server *s, int64_t n, int64_t nnz, int m, int nev);
 void pp_server_destroy(pp_server *s);
+
+/* ----- Measurement support (not part of the method) ----- */
+
+/*
+ * pp_measure_fp64_rate — FP64 (non-tensor) FMA throughput of the current GPU
+ * in flop/s: a kernel of eight independent FMA chains per thread on eight
+ * 256-thread blocks per SM, timed with CUDA events on `stream` (NULL = legacy
+ * default stream), best of three launches after one warm-up (about 50 ms in
+ * all).  The FP64 polynomial passes and CGS2 sweeps are bound by FP64
+ * arithmetic on GB300, so their roofline divides by this measured rate.  The
+ * paper has no counterpart.  Synchronises the stream.  Errors: PP_EINVAL,
+ * PP_ECUDA.
+ */
+pp_status pp_measure_fp64_rate(void *stream, double *flops_per_s);
 
 /* ----- Host FP64 dense steps (no GPU needed; used by the calls above) ----- */
 

@@ -736,7 +736,7 @@ static double time_product(pp_ctx *c, const ppk::Matrix &M) {
 struct TuneChoice {
     int cs = 5, threads = 256, loop = 0, cap = 0;
     bool dia = false;
-    int dia_threads = 256;
+    int dia_threads = 256, dia_wide = 0;
 };
 static std::mutex g_tune_mu;
 static std::map<uint64_t, TuneChoice> g_tune_cache;
@@ -855,6 +855,8 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         return fail(pp_fail(PP_EINVAL, "pp_create: restart must be PP_RESTART_RITZ or PP_RESTART_HARMONIC"));
     if (c->opts.sell_loop < 0 || c->opts.sell_loop > 4)
         return fail(pp_fail(PP_EINVAL, "pp_create: sell_loop must be 0 to 4"));
+    if (c->opts.dia_loop < 0 || c->opts.dia_loop > 3)
+        return fail(pp_fail(PP_EINVAL, "pp_create: dia_loop must be 0 to 3"));
     std::vector<int> cands;
     if (c->opts.sell_c) cands.push_back(c->opts.sell_c == 16 ? 4 : 5);
     else cands = {5, 4};
@@ -899,7 +901,8 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     double sell_t = INFINITY;  // the tuner's time of the chosen SELL format
     std::vector<void *> sell_mem;
     if (fmt == PP_FMT_DIA) fmt = PP_FMT_SELL;  // DIA replaces SELL below when the matrix allows it
-    const bool cacheable = c->opts.format == PP_FMT_AUTO && !c->opts.sell_c && !c->opts.sell_loop && fmt == PP_FMT_SELL;
+    const bool cacheable = c->opts.format == PP_FMT_AUTO && !c->opts.sell_c && !c->opts.sell_loop && !c->opts.dia_loop &&
+                           fmt == PP_FMT_SELL;
     const uint64_t sig = cacheable ? matrix_signature(n, rowptr, colind, c->esz, off16) : 0;
     bool cached = false;
     TuneChoice choice;
@@ -1008,22 +1011,32 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         D.tma = 0;
         D.dia = {(int)n, nd, ld, d_off, d_dval};
         double dia_t = INFINITY;
-        int dia_threads = cached ? choice.dia_threads : 256;
+        int dia_threads = cached ? choice.dia_threads : 256, dia_wide = cached ? choice.dia_wide : 0;
+        // row loops (FP32): 0 one row per thread, 1 four rows, 2 two rows; FP64: one row
+        std::vector<int> wl = {0};
+        if (pr == ppk::F32) wl = {0, 1, 2};
+        if (c->opts.dia_loop) wl = {pr == ppk::F32 ? c->opts.dia_loop - 1 : 0};
         if (!cached)
-            for (int t : {128, 256, 512}) {
-                D.threads = t;
-                double tt = time_product(c, D);
-                if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
-                if (tt < dia_t) {
-                    dia_t = tt;
-                    dia_threads = t;
+            for (int w : wl)
+                for (int t : {128, 256, 512}) {
+                    if (w != 0 && t > 256) continue;  // the multi-row kernels take at most 256 threads
+                    D.threads = t;
+                    D.wide = w;
+                    double tt = time_product(c, D);
+                    if (tt < 0) return fail(pp_fail(PP_ECUDA, "pp_create: tuner launch failed"));
+                    if (tt < dia_t) {
+                        dia_t = tt;
+                        dia_threads = t;
+                        dia_wide = w;
+                    }
                 }
-            }
         choice.dia = cached ? choice.dia : dia_t < sell_t;
         choice.dia_threads = dia_threads;
+        choice.dia_wide = dia_wide;
         if (c->opts.format == PP_FMT_DIA || choice.dia) {
             for (void *q : sell_mem) dfree(c, q);
             D.threads = dia_threads;
+            D.wide = dia_wide;
             M = D;
             c->stored = (int64_t)nd * n;
         } else {
@@ -1129,7 +1142,7 @@ pp_status pp_format_info(const pp_ctx *c, int *fmt, int *chunk, int *index_bits,
     if (chunk) *chunk = sell ? 1 << c->A.sell.cshift : 0;
     if (index_bits) *index_bits = c->A.fmt == 3 ? 0 : ((sell && c->A.sell.off) ? 16 : 32);
     if (threads) *threads = c->A.fmt != 1 ? c->A.threads : 256;
-    if (row_loop) *row_loop = sell ? (c->A.tma ? 2 : (c->A.wide == 2 ? 3 : c->A.wide)) : 0;
+    if (row_loop) *row_loop = sell ? (c->A.tma ? 2 : (c->A.wide == 2 ? 3 : c->A.wide)) : (c->A.fmt == 3 ? c->A.wide : 0);
     if (stored) *stored = c->stored;
     return PP_OK;
 }
@@ -1276,13 +1289,16 @@ pp_status pp_build_poly2(pp_ctx *c, int d1, int d2, const double *b, pp_poly **o
     return (s1 == PP_EBREAKDOWN || s2 == PP_EBREAKDOWN) ? PP_EBREAKDOWN : PP_OK;
 }
 
-pp_status pp_poly_from_roots(pp_ctx *c, int count, const double *re, const double *im, pp_poly **out) {
-    if (!c || count < 1 || !re || !im || !out) return pp_fail(PP_EINVAL, "pp_poly_from_roots: bad arguments");
+// A polynomial with the given roots in the given order (validated: finite,
+// non-zero, conjugate pairs adjacent with im > 0 first).
+static pp_status roots_poly(pp_ctx *c, int count, const double *re, const double *im, const char *who,
+                            pp_poly **out) {
+    if (!c || count < 1 || !re || !im || !out) return pp_fail(PP_EINVAL, "%s: bad arguments", who);
     std::vector<cd> r(count);
     for (int i = 0; i < count; ++i) {
         r[i] = cd(re[i], im[i]);
         if (!std::isfinite(re[i]) || !std::isfinite(im[i]) || (re[i] == 0 && im[i] == 0))
-            return pp_fail(PP_EINVAL, "pp_poly_from_roots: root %d is zero or not finite", i);
+            return pp_fail(PP_EINVAL, "%s: root %d is zero or not finite", who, i);
     }
     for (int i = 0; i < count;) {
         if (r[i].imag() == 0) {
@@ -1290,7 +1306,7 @@ pp_status pp_poly_from_roots(pp_ctx *c, int count, const double *re, const doubl
             continue;
         }
         if (r[i].imag() < 0 || i + 1 >= count || r[i + 1] != std::conj(r[i]))
-            return pp_fail(PP_EINVAL, "pp_poly_from_roots: pair at %d not adjacent (im > 0 first)", i);
+            return pp_fail(PP_EINVAL, "%s: pair at %d not adjacent (im > 0 first)", who, i);
         i += 2;
     }
     pp_poly *p = new pp_poly();
@@ -1298,6 +1314,25 @@ pp_status pp_poly_from_roots(pp_ctx *c, int count, const double *re, const doubl
     p->roots = r;
     p->steps = steps_of(r);
     p->degree = count;
+    *out = p;
+    return PP_OK;
+}
+
+pp_status pp_poly_from_roots(pp_ctx *c, int count, const double *re, const double *im, pp_poly **out) {
+    return roots_poly(c, count, re, im, "pp_poly_from_roots", out);
+}
+
+pp_status pp_poly2_from_roots(pp_ctx *c, int count1, const double *re1, const double *im1, int count2,
+                              const double *re2, const double *im2, pp_poly **out) {
+    if (!out) return pp_fail(PP_EINVAL, "pp_poly2_from_roots: bad arguments");
+    pp_poly *inner = nullptr, *p = nullptr;
+    CKS(roots_poly(c, count1, re1, im1, "pp_poly2_from_roots (inner)", &inner));
+    pp_status st = roots_poly(c, count2, re2, im2, "pp_poly2_from_roots (outer)", &p);
+    if (st < 0) {
+        delete inner;
+        return st;
+    }
+    p->inner = inner;
     *out = p;
     return PP_OK;
 }

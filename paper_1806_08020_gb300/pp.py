@@ -28,7 +28,7 @@ class pp_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("format", C.c_int), ("target", C.c_int), ("sigma", C.c_double),
                 ("add_roots", C.c_int), ("max_cycles", C.c_int), ("refine_steps", C.c_int),
                 ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sell_index", C.c_int), ("sell_loop", C.c_int),
-                ("stream", C.c_void_p), ("restart", C.c_int)]
+                ("stream", C.c_void_p), ("restart", C.c_int), ("dia_loop", C.c_int)]
 
 
 class pp_stats(C.Structure):
@@ -67,6 +67,7 @@ _SIGS = {
     "pp_build_poly_two": (C.c_int, [_P, C.c_int, _D, _D, C.POINTER(_P)]),
     "pp_build_poly_damped": (C.c_int, [_P, C.c_int, _D, C.c_int, C.c_int, C.c_int, C.POINTER(_P), _I, _I, _I]),
     "pp_poly_from_roots": (C.c_int, [_P, C.c_int, _D, _D, C.POINTER(_P)]),
+    "pp_poly2_from_roots": (C.c_int, [_P, C.c_int, _D, _D, C.c_int, _D, _D, C.POINTER(_P)]),
     "pp_poly_roots": (C.c_int, [_P, _D, _D, C.c_int, _I]),
     "pp_poly_inner_roots": (C.c_int, [_P, _D, _D, C.c_int, _I]),
     "pp_poly_info": (C.c_int, [_P, _I, _I]),
@@ -96,6 +97,7 @@ _SIGS = {
     "pp_harmonic_ritz": (C.c_int, [C.c_int, _D, C.c_int, _D, _D]),
     "pp_leja_order": (C.c_int, [C.c_int, _D, _D, _D, _D]),
     "pp_add_stability_roots": (C.c_int, [C.c_int, _D, _D, C.c_int, _D, _D, _I]),
+    "pp_measure_fp64_rate": (C.c_int, [_P, _D]),
     "pp_restart_basis": (C.c_int, [C.c_int, _D, C.c_int, C.c_int, C.c_double, C.c_int, _D, _D, _I, _D, _D]),
 }
 
@@ -282,6 +284,17 @@ def pp_poly_from_roots(ctx: Context, roots) -> Poly:
     re, im = _f64(r.real), _f64(r.imag)
     h = C.c_void_p()
     _check(LIB.pp_poly_from_roots(ctx.handle, int(r.size), _dp(re), _dp(im), C.byref(h)))
+    return Poly(h.value, ctx, PP_OK)
+
+
+def pp_poly2_from_roots(ctx: Context, inner_roots, outer_roots) -> Poly:
+    """Double polynomial pi_2(tau(A)), tau = 1 - pi_1, with the given root lists (Section 8)."""
+    r1 = np.asarray(inner_roots, dtype=complex)
+    r2 = np.asarray(outer_roots, dtype=complex)
+    re1, im1, re2, im2 = _f64(r1.real), _f64(r1.imag), _f64(r2.real), _f64(r2.imag)
+    h = C.c_void_p()
+    _check(LIB.pp_poly2_from_roots(ctx.handle, int(r1.size), _dp(re1), _dp(im1), int(r2.size), _dp(re2), _dp(im2),
+                                   C.byref(h)))
     return Poly(h.value, ctx, PP_OK)
 
 
@@ -582,3 +595,10 @@ def pp_restart_basis(H: np.ndarray, k: int, target: float, harmonic: bool = Fals
     kv = kk.value
     rows, cols = (m + 1, kv + 1) if harmonic else (m, kv)
     return Q[: rows * cols].reshape((rows, cols), order="F"), Hn, kv, re + 1j * im
+
+
+def pp_measure_fp64_rate(stream: int = 0) -> float:
+    """Measured FP64 FMA throughput of the current GPU in flop/s."""
+    r = C.c_double()
+    _check(LIB.pp_measure_fp64_rate(C.c_void_p(int(stream)), C.byref(r)))
+    return r.value
