@@ -251,6 +251,189 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_step_dia(DiaView D, StepArg
     step_epilogue<T, Acc>(row, dia_row<T, V, Acc>(D, off_s, (const T *)s.x, row), s);
 }
 
+// FP32 DIA with R (2 or 4) consecutive rows per thread (r0 = R q): the values
+// of a diagonal for the R rows are one 8- or 16-byte load (the 32-row blocks
+// keep them adjacent), x for a diagonal whose offset is a multiple of R is one
+// such load too (else R loads), and the epilogue's vectors move in 8- or
+// 16-byte loads and stores.  The loads of up to eight diagonals are issued
+// before their products.  Products run in increasing diagonal order per row
+// with the same operands as dia_row, so the results are bit-identical to the
+// one-row kernels.  Needs every vector pointer 4R-byte aligned (checked at
+// dispatch).
+template <int R>
+struct VecR;
+template <>
+struct VecR<4> {
+    __device__ static __forceinline__ void ld(const float *p, float (&o)[4]) {
+        const float4 v = __ldg((const float4 *)p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+    __device__ static __forceinline__ void st(float *p, const float (&v)[4]) {
+        *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct VecR<2> {
+    __device__ static __forceinline__ void ld(const float *p, float (&o)[2]) {
+        const float2 v = __ldg((const float2 *)p);
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+    __device__ static __forceinline__ void st(float *p, const float (&v)[2]) { *(float2 *)p = make_float2(v[0], v[1]); }
+};
+
+template <int R>
+__device__ __forceinline__ void dia_rows(const DiaView &D, const int *off_s, const float *__restrict__ x, int r0,
+                                         float (&u)[R]) {
+    const float *val = (const float *)D.val + (size_t)(r0 >> 5) * ((size_t)D.ndiag * 32) + (r0 & 31);
+#pragma unroll
+    for (int q = 0; q < R; ++q) u[q] = 0.f;
+    for (int d0 = 0; d0 < D.ndiag; d0 += 8) {
+        float a[8][R], xv[8][R];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int d = d0 + t;
+#pragma unroll
+            for (int q = 0; q < R; ++q) a[t][q] = xv[t][q] = 0.f;
+            if (d < D.ndiag) {
+                VecR<R>::ld(val + d * 32, a[t]);
+                const int o = off_s[d], c = r0 + o;
+                if (o % R == 0 && c >= 0 && c + R - 1 < D.n) {
+                    VecR<R>::ld(x + c, xv[t]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < R; ++q)
+                        if (c + q >= 0 && c + q < D.n) xv[t][q] = __ldg(x + c + q);
+                }
+            }
+        }
+        const int cnt = D.ndiag - d0 < 8 ? D.ndiag - d0 : 8;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (t < cnt)  // warp-uniform
+#pragma unroll
+                for (int q = 0; q < R; ++q) u[q] = fmaf(a[t][q], xv[t][q], u[q]);
+    }
+}
+
+// The general pass (step_epilogue) on R rows.
+template <int R>
+__device__ __forceinline__ void step_epilogue_rows(int r0, float (&u)[R], const StepArgs &s) {
+    float xi[R];
+    VecR<R>::ld((const float *)s.x + r0, xi);
+    if (s.sigma != 0.0) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) u[q] = u[q] - (float)s.sigma * xi[q];
+    }
+    if (s.plain) {
+        VecR<R>::st((float *)s.y + r0, u);
+        return;
+    }
+    float delta[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) delta[q] = (float)s.a1 * xi[q] + (float)s.a2 * u[q];
+    if (s.y) {
+        float base[R];
+        if (s.aux) {
+            VecR<R>::ld((const float *)s.aux + r0, base);
+        } else {
+#pragma unroll
+            for (int q = 0; q < R; ++q) base[q] = xi[q];
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) base[q] = base[q] - delta[q];
+        VecR<R>::st((float *)s.y + r0, base);
+    }
+    if (s.r) {
+        float rv[R];
+        if (s.r_init) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) rv[q] = delta[q];
+        } else {
+            VecR<R>::ld((const float *)s.r + r0, rv);
+#pragma unroll
+            for (int q = 0; q < R; ++q) rv[q] = rv[q] + delta[q];
+        }
+        if (s.r_write) VecR<R>::st((float *)s.r + r0, rv);
+        if (s.oy) {
+            float ob[R], od[R];
+            VecR<R>::ld((const float *)s.obase + r0, ob);
+#pragma unroll
+            for (int q = 0; q < R; ++q) od[q] = (float)s.b2 * rv[q];
+            if (s.ox) {
+                float ox[R];
+                VecR<R>::ld((const float *)s.ox + r0, ox);
+#pragma unroll
+                for (int q = 0; q < R; ++q) od[q] += (float)s.b1 * ox[q];
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) ob[q] = ob[q] - od[q];
+            VecR<R>::st((float *)s.oy + r0, ob);
+        }
+    }
+}
+
+// KIND as k_pass_dia (0 plain, 1 real root, 2 pair second pass); GENERAL: the
+// running-sum pass (step_epilogue).  A last group of rows that runs past n
+// takes the one-row code for each of its rows.
+template <int R, int KIND, bool SIGMA, bool GENERAL>
+__global__ void __launch_bounds__(256) k_dia_rows(DiaView D, StepArgs s) {
+    grid_trigger();
+    grid_wait();
+    __shared__ int off_s[kDiaMax];
+    for (int d = threadIdx.x; d < D.ndiag; d += blockDim.x) off_s[d] = D.off[d];
+    __syncthreads();
+    const int r0 = R * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (r0 >= D.n) return;
+    const float *x = (const float *)s.x;
+    if (r0 + R - 1 >= D.n) {  // ragged tail: one row at a time
+        for (int row = r0; row < D.n; ++row) {
+            float u = dia_row<float, float, float>(D, off_s, x, row);
+            if (GENERAL) {
+                step_epilogue<float, float>(row, u, s);
+            } else {
+                if (SIGMA) u = fmaf(-(float)s.sigma, x[row], u);
+                float *y = (float *)s.y;
+                if (KIND == 0)
+                    y[row] = u;
+                else if (KIND == 1)
+                    y[row] = fmaf(-(float)s.a2, u, x[row]);
+                else
+                    y[row] = fmaf(-(float)s.a2, u, fmaf(-(float)s.a1, x[row], ((const float *)s.aux)[row]));
+            }
+        }
+        return;
+    }
+    float u[R];
+    dia_rows<R>(D, off_s, x, r0, u);
+    if (GENERAL) {
+        step_epilogue_rows<R>(r0, u, s);
+        return;
+    }
+    float xi[R], out[R];
+    VecR<R>::ld(x + r0, xi);
+    if (SIGMA) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) u[q] = fmaf(-(float)s.sigma, xi[q], u[q]);
+    }
+    if (KIND == 0) {
+        VecR<R>::st((float *)s.y + r0, u);
+    } else if (KIND == 1) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) out[q] = fmaf(-(float)s.a2, u[q], xi[q]);
+        VecR<R>::st((float *)s.y + r0, out);
+    } else {
+        float ax[R];
+        VecR<R>::ld((const float *)s.aux + r0, ax);
+#pragma unroll
+        for (int q = 0; q < R; ++q) out[q] = fmaf(-(float)s.a2, u[q], fmaf(-(float)s.a1, xi[q], ax[q]));
+        VecR<R>::st((float *)s.y + r0, out);
+    }
+}
+
 template <typename T, typename V, typename Acc, int KIND, bool SIGMA, int FMT>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass(SellView S, CsrView R, StepArgs s) {
     grid_trigger();
@@ -570,8 +753,45 @@ static bool tma_pass_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t s
     return true;
 }
 
+// The R-rows-per-thread FP32 DIA kernels (R = 4 for row loop 1, R = 2 for row
+// loop 2) when the tuner chose them and every vector the pass touches is
+// 4R-byte aligned; false otherwise.
+template <int R>
+static bool dia_rows_launch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    for (const void *p : {s.x, s.aux, (const void *)s.y, (const void *)s.r, s.obase, s.ox, (const void *)s.oy})
+        if (p && ((uintptr_t)p & (uintptr_t)(4 * R - 1)) != 0) return false;
+    const int threads = A.threads > 256 ? 256 : A.threads;
+    const int groups = (A.n + R - 1) / R;
+    const int blocks = (groups + threads - 1) / threads;
+    const bool general = s.r || s.oy || !s.y;
+    const bool sig = s.sigma != 0.0;
+    if (general || (!s.plain && !s.aux && s.a1 != 0.0)) {
+        launch_dependent(k_dia_rows<R, 0, false, true>, blocks, threads, 0, st, A.dia, s);
+        return true;
+    }
+    const int kind = s.plain ? 0 : (s.aux ? 2 : 1);
+#define PP_DR(K, S) launch_dependent(k_dia_rows<R, K, S, false>, blocks, threads, 0, st, A.dia, s)
+    if (kind == 0) {
+        if (sig) PP_DR(0, true); else PP_DR(0, false);
+    } else if (kind == 1) {
+        if (sig) PP_DR(1, true); else PP_DR(1, false);
+    } else {
+        if (sig) PP_DR(2, true); else PP_DR(2, false);
+    }
+#undef PP_DR
+    return true;
+}
+
+static bool dia_rows_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    if (A.prec != F32) return false;
+    if (A.wide == 1) return dia_rows_launch<4>(A, s, st);
+    if (A.wide == 2) return dia_rows_launch<2>(A, s, st);
+    return false;
+}
+
 template <typename T>
 static void dia_dispatch(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    if (dia_rows_dispatch(A, s, st)) return;
     const int threads = A.threads;
     const int blocks = (A.n + threads - 1) / threads;
     const bool general = s.r || s.oy || !s.y;

@@ -97,7 +97,8 @@ struct Matrix {
     int n = 0;
     int fmt = 2;  // 1 CSR, 2 SELL, 3 DIA
     int threads = 256;  // block size of the SELL pass kernels (64..512, chosen by the tuner)
-    int wide = 0;       // SELL row loop: 0 unrolled by four, 1 chunks of eight loads, 2 two rows per thread (tuner)
+    int wide = 0;       // SELL row loop: 0 unrolled by four, 1 chunks of eight loads, 2 two rows per thread (tuner);
+                        // DIA (FP32): 1 four, 2 two consecutive rows per thread with vector loads (tuner)
     int tma = 0;        // SELL-32 slice data staged by bulk copies (tuner); needs tile_cap and err
     int tile_cap = 0;   // most stored entries in threads/32 consecutive slices
     int *err = nullptr; // the context's error word (bounded waits of the staged kernels)

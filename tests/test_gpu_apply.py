@@ -206,7 +206,8 @@ def _wide_band_matrix():
 def test_sell_formats_bit_identical(kind, precision):
     """Every device format gives the same pi(A) x bit for bit: CSR, SELL with
     chunk height 16 or 32, 16- or 32-bit column indices, any row loop (plain,
-    wide, or slice data staged by bulk copies), and whatever chunk height,
+    wide, or slice data staged by bulk copies), DIA with one or (FP32) four
+    rows per thread, and whatever chunk height,
     block size and row loop the tuner picks.  Each row sums its entries in CSR
     order in every format (SELL padding adds 0 * x = 0 exactly)."""
     from paper_1806_08020_gb300 import pp
@@ -226,6 +227,9 @@ def test_sell_formats_bit_identical(kind, precision):
                 "c32_i32_two_rows": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=4),
                 "c32_i32_staged": dict(format=pp.PP_FMT_SELL, sell_c=32, sell_index=32, sell_loop=3),
                 "dia": dict(format=pp.PP_FMT_DIA),
+                "dia_one_row": dict(format=pp.PP_FMT_DIA, dia_loop=1),
+                "dia_four_rows": dict(format=pp.PP_FMT_DIA, dia_loop=2),
+                "dia_two_rows": dict(format=pp.PP_FMT_DIA, dia_loop=3),
                 "tuned": dict(format=pp.PP_FMT_SELL),
                 "auto": dict()}
     out, info = {}, {}
@@ -242,6 +246,9 @@ def test_sell_formats_bit_identical(kind, precision):
     assert info["c32_staged"]["row_loop"] == 2 and info["c32_i32_staged"]["index_bits"] == 32
     assert info["c16_two_rows"]["row_loop"] == 3
     assert info["dia"]["fmt"] == pp.PP_FMT_DIA and info["dia"]["index_bits"] == 0
+    assert info["dia_one_row"]["row_loop"] == 0
+    assert info["dia_four_rows"]["row_loop"] == (1 if precision == 1 else 0)  # several rows: FP32 only
+    assert info["dia_two_rows"]["row_loop"] == (2 if precision == 1 else 0)
     # the second auto context on this matrix takes the first one's cached choice
     assert info["auto"] == pp.pp_format_info(ref_ctx)
     for name in variants:
