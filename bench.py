@@ -16,6 +16,15 @@ eigenvectors back to the host).  With N > 1 (torchrun) every rank solves its
 own seeded instance (weak scaling, no collective on the data path).
 ``--impl reference`` times the CPU oracle on a bounded sample of the same
 workload and extrapolates to a full solve.
+
+The default line also carries the rest of the metric, each leg with its own
+clocks: ``mixed_fp32`` (the same workload in mixed precision), ``precision_3d``
+(n = 160^3 3-D workload, double polynomial: mixed vs FP64 vs BF16 basis, and
+the fused pi_2(tau(A)) v apply against measured HBM bandwidth), ``batch`` (64
+uneven instances: batched mixed vs batched FP64 vs FP64 one by one) and
+``serve_sample`` (a prefix of the Poisson request stream through the
+continuous-batching server in FP32 and FP64: p50/p99 latency, offered and
+achieved load).  Every arm counts nev eigenpairs per converged solve.
 """
 from __future__ import annotations
 
@@ -150,7 +159,8 @@ def _profile_traffic(name: str) -> float | None:
 def _format_name(f: dict) -> str:
     loops = {0: "unrolled", 1: "wide", 2: "staged (bulk copies)", 3: "two rows per thread"}
     if f["fmt"] == 3:
-        return f"k_pass_dia (DIA, {f['stored']} stored values, {f['threads']} threads/block)"
+        rows = {0: "one row", 1: "four rows", 2: "two rows"}.get(f["row_loop"], "?")
+        return f"k_pass_dia (DIA, {f['stored']} stored values, {f['threads']} threads/block, {rows} per thread)"
     if f["fmt"] == 1:
         return "k_pass (CSR)"
     return (f"k_pass (SELL-{f['chunk']}, {f['index_bits']}-bit columns, {f['threads']} threads/block, "
@@ -231,7 +241,7 @@ def run_ours(args, ws, rank, local):
         for _ in range(args.steps):
             poly, res = one_solve()
             st = res.stats
-            pairs += int(np.sum(res.resid <= cfg["rtol"])) if res.status == 0 else 0
+            pairs += count_pairs(res, cfg["nev"], cfg["rtol"])
             t_apply += st["t_apply"]
             cycles.append(st["cycles"])
             counters = {k: int(st[k]) for k in ("mvps", "dots", "vops")}
@@ -257,7 +267,7 @@ def run_ours(args, ws, rank, local):
         p2 = pp.pp_build_poly(c2, cfg["d"], b)
         r2 = pp.pp_eigs(c2, p2, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=True)
         d2h = r2.X.nbytes + r2.lam.nbytes * 2 + r2.resid.nbytes
-        e2e_pairs += int(np.sum(r2.resid <= cfg["rtol"])) if r2.status == 0 else 0
+        e2e_pairs += count_pairs(r2, cfg["nev"], cfg["rtol"])
         p2.close()
         c2.close()
     barrier()
@@ -276,14 +286,20 @@ def run_ours(args, ws, rank, local):
     achieved_tflops = flops_apply * applies_total / t_apply / 1e12
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs") or 6800.0
-    # FP64 (non-tensor) peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flops x SM clock
+    # FP64 (non-tensor) peak: measured by the library's FMA-throughput kernel; the unit-count
+    # figure (152 SMs x 2 FP64 FMA/clk x 2 flops x SM clock) and cuBLAS DGEMM shown beside it
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    fp64_derived = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    fp64_peak, dgemm = fp64_peaks(stream, dev, local)
     traffic = _profile_traffic("sell_root_step_fp64_n1e6.txt")
     # the FP64 pipe is the most utilised unit of this kernel (ncu: FP64 pipe ~73 %, DRAM ~45 % cold)
-    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                "frac": round(achieved_tflops / fp64_peak, 4), "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x %.0f MHz (FP64 non-tensor)" % sm_mhz,
+    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(fp64_peak["tflops"], 4),
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / fp64_peak["tflops"], 4), "traffic": traffic,
+                "peak_source": "measured: FP64 FMA-throughput kernel (pp_measure_fp64_rate), clocks " +
+                               json.dumps(fp64_peak["clocks"]),
+                "peak_derived": round(fp64_derived, 4),
+                "peak_derived_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x %.0f MHz" % sm_mhz,
+                "dgemm_tflops": dgemm,
                 "kernel": _format_name(fmt) + " (fused root step; real and pair passes)",
                 "bytes_per_launch": round(bytes_apply / launches_apply),
                 "flops_per_launch": round(flops_apply / launches_apply),
@@ -307,7 +323,7 @@ def run_ours(args, ws, rank, local):
     m0.record(stream)
     for _ in range(args.steps):
         r32 = solve32()
-        mixed_pairs += int(np.sum(r32.resid <= cfg["rtol"])) if r32.status == 0 else 0
+        mixed_pairs += count_pairs(r32, cfg["nev"], cfg["rtol"])
         mixed_res = max(mixed_res, float(np.max(r32.resid)))
         mixed_cycles.append(r32.stats["cycles"])
     m1.record(stream)
@@ -322,6 +338,15 @@ def run_ours(args, ws, rank, local):
                  "rel_err_vs_fp64_per_eigenpair": [float("%.3g" % e) for e in _match_errors(r32.lam, res.lam)],
                  "rel_err_vs_oracle_per_eigenpair": _oracle_errors(r32.lam) if rank == 0 else None}
     ctx32.close()
+
+    # the rest of the metric on its other workloads (one GPU per rank; rank 0 reports them)
+    legs = {}
+    if not args.no_legs:
+        t_leg = time.perf_counter()
+        legs["precision_3d"] = leg_precision3d(local, rank)
+        legs["batch"] = leg_batch(local, rank)
+        legs["serve_sample"] = leg_serve(local, rank, args.serve_sample)
+        legs["legs_wall_s"] = round(time.perf_counter() - t_leg, 1)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -349,6 +374,7 @@ def run_ours(args, ws, rank, local):
         "roofline": roofline,
         "clocks": clk.summary(),
         "mixed_fp32": out_mixed,
+        **legs,
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, seed, budget_s=args.cpu_budget, cycles=statistics.median(cycles))
@@ -357,20 +383,52 @@ def run_ours(args, ws, rank, local):
     return out
 
 
+def fp64_peaks(stream, dev, local) -> tuple[dict, float | None]:
+    """The measured FP64 FMA rate (library kernel, best of three launches, clocks
+    sampled meanwhile) and, for reference, cuBLAS DGEMM at 4096^3 through torch."""
+    import torch
+
+    from paper_1806_08020_gb300 import pp
+    with ClockSampler(local) as clk:
+        rate = max(pp.pp_measure_fp64_rate(stream.cuda_stream) for _ in range(3))
+    dgemm = None
+    try:
+        a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        bm = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        torch.matmul(a, bm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            torch.matmul(a, bm)
+        e1.record()
+        torch.cuda.synchronize()
+        dgemm = round(3 * 2 * 4096**3 / (e0.elapsed_time(e1) * 1e-3) / 1e12, 4)
+        del a, bm
+    except Exception:
+        pass
+    return {"tflops": rate / 1e12, "clocks": clk.summary()}, dgemm
+
+
 def cpu_baseline(cfg, seed, budget_s=20.0, cycles=None):
     """The oracle as it stands on the host cores, on a bounded sample of the workload.
 
-    Sample: the oracle's GMRES(d) build plus the first S Arnoldi steps on pi(A)
-    (S chosen to fit the budget), timed; extrapolated to a full solve of
-    m + (cycles - 1)(m - k) steps.  The cycle count is the oracle's own from
+    Sample: the oracle's GMRES(d) build, then the first S Arnoldi steps on pi(A)
+    (S chosen to fit the budget), each step timed; then one cycle's dense work
+    (nev + 1 Ritz vectors and their products with A, the restart product V Q)
+    on the sampled basis.  A step's cost grows with the basis size j (CGS2), so
+    the step times are fitted as a + b j and summed over the solve's schedule
+    (j = 0..m-1, then j = k..m-1 in each later cycle), the dense work scaled to
+    m columns per cycle.  The cycle count is the oracle's own from
     tests/golden/plain_large_oracle.txt (written by a script that runs only the
-    oracle) when present, else the GPU run's.
+    oracle) when present, else the GPU run's.  Counts nev eigenpairs per solve.
     """
     import oracle as O
     from oracle.ppa import make_operator
 
     A = O.to_scipy(cfg["A"])
     n = A.shape[0]
+    m, k, nev = cfg["m"], cfg["k"], cfg["nev"]
     c = O.Counters()
     sigma = O.gershgorin_shift(A)
     op = O.Operator(A, sigma, c)
@@ -380,15 +438,30 @@ def cpu_baseline(cfg, seed, budget_s=20.0, cycles=None):
     P = O.build_poly(op, b, cfg["d"], c)
     t_build = time.perf_counter() - t0
     opp = make_operator(op, P, c)
-    V = np.zeros((n, cfg["m"] + 1))
+    V = np.zeros((n, m + 1))
     V[:, 0] = v0 / np.linalg.norm(v0)
-    steps = 0
-    t1 = time.perf_counter()
-    while steps < cfg["m"] and (steps == 0 or time.perf_counter() - t0 < budget_s):
-        w, _ = O.cgs2(V[:, : steps + 1], opp(V[:, steps]), c)
-        V[:, steps + 1] = w / np.linalg.norm(w)
-        steps += 1
-    t_step = (time.perf_counter() - t1) / max(steps, 1)
+    tj = []
+    while len(tj) < m and (not tj or time.perf_counter() - t0 < budget_s):
+        j = len(tj)
+        t1 = time.perf_counter()
+        w, _ = O.cgs2(V[:, : j + 1], opp(V[:, j]), c)
+        V[:, j + 1] = w / np.linalg.norm(w)
+        tj.append(time.perf_counter() - t1)
+    S = len(tj)
+    if S >= 2:
+        bfit, afit = np.polyfit(np.arange(S, dtype=float), np.asarray(tj), 1)
+        bfit = max(bfit, 0.0)
+    else:
+        afit, bfit = tj[0], 0.0
+    # one cycle's dense work on the sampled basis, scaled to m columns
+    nw = nev + 1
+    rng = np.random.default_rng(0)
+    t2 = time.perf_counter()
+    Y = V[:, :S] @ rng.standard_normal((S, nw))
+    for q in range(nw):
+        A @ Y[:, q]
+    V[:, :S] @ rng.standard_normal((S, k))
+    t_dense = (time.perf_counter() - t2) * m / S
     src = "gpu run"
     try:
         g = dict(line.split(None, 1) for line in open(os.path.join(ROOT, "tests", "golden", "plain_large_oracle.txt"))
@@ -398,96 +471,112 @@ def cpu_baseline(cfg, seed, budget_s=20.0, cycles=None):
     except Exception:
         pass
     cycles = int(cycles or 1)
-    total_steps = cfg["m"] + (cycles - 1) * (cfg["m"] - cfg["k"])
-    t_solve = t_build + total_steps * t_step
-    return {"value": round(cfg["nev"] / t_solve, 5), "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+    sched = list(range(m)) + [j for _ in range(cycles - 1) for j in range(k, m)]
+    t_solve = t_build + sum(afit + bfit * j for j in sched) + cycles * t_dense
+    return {"value": round(nev / t_solve, 5), "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
             "kind": "oracle",
-            "sample": f"GMRES({cfg['d']}) build + {steps} of {total_steps} Arnoldi steps "
-                      f"({time.perf_counter() - t0:.1f} s); extrapolated with {cycles} cycles ({src}); "
-                      "scipy SpMV single-threaded, BLAS on all cores",
+            "sample": f"GMRES({cfg['d']}) build ({t_build:.1f} s) + {S} of {len(sched)} Arnoldi steps, timed one by "
+                      f"one and fitted as a + b j (a {afit:.3f} s, b {bfit * 1e3:.2f} ms per basis column), plus one "
+                      f"cycle's Ritz vectors and restart product; extrapolated over {cycles} cycles ({src}); "
+                      f"{time.perf_counter() - t0:.1f} s of CPU work; scipy SpMV single-threaded, BLAS on all cores; "
+                      f"nev = {nev} eigenpairs per solve",
             "seconds_per_solve_est": round(t_solve, 1)}
 
 
-def run_batch(args, ws, rank, local):
-    """64 uneven 2-D CD instances: batched mixed precision vs the plain FP64 method per instance."""
+def count_pairs(res, nev: int, rtol: float) -> int:
+    """Converged wanted eigenpairs of one solve: the first nev slots (sorted by the
+    target) with residual <= rtol.  A conjugate pair straddling the boundary makes
+    the library return nev + 1 slots; the extra slot is not counted, so every arm
+    (GPU, batched, served and the oracle) counts the same nev wanted pairs."""
+    if res.status != 0:
+        return 0
+    return int(np.sum(np.asarray(res.resid)[:nev] <= rtol))
+
+
+def _max_match_error(lam_a, lam_b) -> float | None:
+    e = _match_errors(np.asarray(lam_a), np.asarray(lam_b)) if len(lam_a) and len(lam_b) else []
+    return float("%.3g" % max(e)) if e else None
+
+
+def leg_batch(local: int, rank: int, instances: int = 64) -> dict:
+    """64 uneven 2-D CD instances (grid side U{64..512}, beta U[1,200], d U{20..80},
+    Arnoldi(30,13), nev 8): the batched engine in mixed precision and in FP64, and
+    the plain FP64 method one instance after the other, each timed with CUDA events
+    on its stream; per instance the largest distance of the mixed eigenvalues to the
+    batched FP64 ones."""
     import torch
 
     from paper_1806_08020_gb300 import pp
 
-    torch.cuda.set_device(local)
-    specs = inputs.batch_instances(count=args.instances)
+    specs = inputs.batch_instances(count=instances)
     mats = [inputs.convection_diffusion_2d(sp["N"], sp["beta"]) for sp in specs]
     bs = [inputs.start_vector(A.n, sp["seed"] + 7919 * rank, 0) for A, sp in zip(mats, specs)]
     vs = [inputs.start_vector(A.n, sp["seed"] + 7919 * rank, 1) for A, sp in zip(mats, specs)]
     ds = [sp["d"] for sp in specs]
+    nev, m, k, rtol = 8, 30, 13, 1e-8
     stream = torch.cuda.Stream()
-    B = pp.pp_batch_create(mats, precision=pp.PP_FP32, stream=stream.cuda_stream)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    l0 = pp.pp_batch_launch_count(B)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        status, res = pp.pp_batch_solve(B, ds, bs, vs, 8, 30, 13, 1e-8, want_vectors=False)
-        ev1.record(stream)
+    out = {}
+    results = {}
+    for name, prec in (("batched_mixed", pp.PP_FP32), ("batched_fp64", pp.PP_FP64)):
+        B = pp.pp_batch_create(mats, precision=prec, stream=stream.cuda_stream)
         torch.cuda.synchronize()
-    t = ev0.elapsed_time(ev1) * 1e-3
-    pairs = sum(int(np.sum(r.resid <= 1e-8)) for r in res if r.status == 0)
-    conv = sum(r.status == 0 for r in res)
-    launches = pp.pp_batch_launch_count(B) - l0
-    # the same batched engine in FP64
-    B64 = pp.pp_batch_create(mats, precision=pp.PP_FP64, stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    eb0.record(stream)
-    st64, res64 = pp.pp_batch_solve(B64, ds, bs, vs, 8, 30, 13, 1e-8, want_vectors=False)
-    eb1.record(stream)
-    torch.cuda.synchronize()
-    tb64 = eb0.elapsed_time(eb1) * 1e-3
-    pairsb64 = sum(int(np.sum(r.resid <= 1e-8)) for r in res64 if r.status == 0)
-    convb64 = sum(r.status == 0 for r in res64)
-    B64.close()
-    # the plain FP64 GPU method, one instance after the other
+        l0 = pp.pp_batch_launch_count(B)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            _, res = pp.pp_batch_solve(B, ds, bs, vs, nev, m, k, rtol, want_vectors=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        pairs = sum(count_pairs(r, nev, rtol) for r in res)
+        out[name] = {"value": round(pairs / t, 3), "unit": UNIT, "seconds": round(t, 3), "eigenpairs": pairs,
+                     "converged": int(sum(r.status == 0 for r in res)),
+                     "fp64_continuations": int(sum(1 for r in res if prec == pp.PP_FP32 and r.stats["fp64_cycles"] > 0)),
+                     "cycles_total": int(sum(r.stats["cycles"] for r in res)),
+                     "gpu_launches": int(pp.pp_batch_launch_count(B) - l0), "clocks": clk.summary()}
+        results[name] = res
+        B.close()
+    # the plain FP64 GPU method (pp_eigs), one instance after the other
     t64, pairs64, conv64 = 0.0, 0, 0
     for A, d, b, v in zip(mats, ds, bs, vs):
         ctx = pp.pp_create(A, stream=stream.cuda_stream, max_cycles=300)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r = pp.pp_eigs(ctx, pp.pp_build_poly(ctx, d, b), 8, 30, 13, 1e-8, v, want_vectors=False)
+        r = pp.pp_eigs(ctx, pp.pp_build_poly(ctx, d, b), nev, m, k, rtol, v, want_vectors=False)
         e1.record(stream)
         torch.cuda.synchronize()
         t64 += e0.elapsed_time(e1) * 1e-3
-        pairs64 += int(np.sum(r.resid <= 1e-8)) if r.status == 0 else 0
+        pairs64 += count_pairs(r, nev, rtol)
         conv64 += r.status == 0
         ctx.close()
+    out["plain_fp64_sequential"] = {"value": round(pairs64 / t64, 3), "unit": UNIT, "seconds": round(t64, 3),
+                                    "eigenpairs": pairs64, "converged": int(conv64)}
+    errs = [_max_match_error(a.lam, b.lam) for a, b in zip(results["batched_mixed"], results["batched_fp64"])]
+    errs = [e for e in errs if e is not None]
+    out["rel_err_mixed_vs_fp64"] = {"max": max(errs) if errs else None,
+                                    "median": float("%.3g" % statistics.median(errs)) if errs else None,
+                                    "note": "per instance, largest |lam_mixed - lam_fp64| / |lam_fp64| over its "
+                                            "eigenpairs; both meet residual <= 1e-8 ||A||_1 on A in FP64"}
+    out["workload"] = (f"batch of {len(mats)} CD instances, N U{{64..512}}, beta U[1,200], d U{{20..80}}, "
+                       f"Arnoldi(30,13), nev 8, rtol 1e-8; sum n = {int(sum(A.n for A in mats))}")
+    return out
+
+
+def run_batch(args, ws, rank, local):
+    """The batch workload on its own line."""
+    leg = leg_batch(local, rank, args.instances)
+    m = leg["batched_mixed"]
     return {"metric": "eigenpairs/s at residual 1e-8, batched mixed precision (64 uneven 2-D CD instances)",
-            "value": round(pairs / t, 3), "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
-            "ms_per_step": round(t * 1e3, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 apply / f64 refine", "data": "synthetic (seeded generator)",
-            "config": {"workload": f"batch of {len(mats)} CD instances, N U{{64..512}}, beta U[1,200], d U{{20..80}}, "
-                                   "Arnoldi(30,13), nev 8", "sum_n": int(sum(A.n for A in mats)),
-                       "converged": conv, "fp64_continuations": sum(1 for r in res if r.stats["fp64_cycles"] > 0),
-                       "cycles": [r.stats["cycles"] for r in res]},
-            "plain_fp64_sequential": {"value": round(pairs64 / t64, 3), "unit": UNIT, "seconds": round(t64, 2),
-                                      "converged": conv64},
-            "batched_fp64": {"value": round(pairsb64 / tb64, 3), "unit": UNIT, "seconds": round(tb64, 2),
-                             "converged": convb64},
-            "gpu_launches": int(launches), "clocks": clk.summary()}
+            "value": m["value"], "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
+            "ms_per_step": round(m["seconds"] * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 apply / f64 refine", "data": "synthetic (seeded generator)",
+            "config": {"workload": leg["workload"]}, "batch": leg, "gpu_launches": m["gpu_launches"],
+            "clocks": m["clocks"]}
 
 
-def run_serve(args, ws, rank, local):
-    """The Poisson request stream (first --requests requests) through the continuous-batching server."""
-    import torch
-
-    from paper_1806_08020_gb300 import pp
-
-    torch.cuda.set_device(local)
-    stream_spec = inputs.request_stream(count=args.requests)
-    reqs = []
-    for q in stream_spec:  # inputs are generated before the timed region
-        A = inputs.banded_random(q["n"], q["w"], q["seed"] + 7919 * rank)
-        reqs.append((q, A, inputs.start_vector(A.n, q["seed"], 0), inputs.start_vector(A.n, q["seed"], 1)))
-    prec = pp.PP_FP64 if args.serve_precision == "fp64" else pp.PP_FP32
-    S = pp.pp_server_create(precision=prec, max_cycles=args.serve_max_cycles)
+def _serve_once(pp, reqs, prec, max_cycles, local):
+    """Serve the requests at their arrival times; returns (results by index, wall seconds, clocks, launches)."""
+    S = pp.pp_server_create(precision=prec, max_cycles=max_cycles)
     pending, done = {}, {}
     i = 0
     t0 = time.perf_counter()
@@ -496,8 +585,8 @@ def run_serve(args, ws, rank, local):
             now = time.perf_counter() - t0
             while i < len(reqs) and reqs[i][0]["arrival"] <= now:
                 q, A, b, v = reqs[i]
-                rid = pp.pp_server_submit(S, A, q["d"], q["nev"], q["m"], q["k"], 1e-8, b, v)
-                pending[rid] = q
+                rid = pp.pp_server_submit(S, A, q["d"], q["nev"], q["m"], q["k"], q["rtol"], b, v)
+                pending[rid] = i
                 i += 1
             if pending:
                 pp.pp_server_step(S)
@@ -506,27 +595,68 @@ def run_serve(args, ws, rank, local):
             for rid in list(pending):
                 r = pp.pp_server_result(S, rid)
                 if r is not None:
-                    done[rid] = r
-                    del pending[rid]
+                    done[pending.pop(rid)] = r
         wall = time.perf_counter() - t0
-    lat = np.array([l for _, l in done.values()])
-    pairs = sum(int(np.sum(r.resid <= 1e-8)) for r, _ in done.values() if r.status == 0)
-    conv = sum(r.status == 0 for r, _ in done.values())
-    cont = sum(1 for r, _ in done.values() if prec == pp.PP_FP32 and r.stats["fp64_cycles"] > 0)
-    offered = len(reqs) / max(stream_spec[-1]["arrival"], 1e-9)
+    launches = int(pp.pp_server_launch_count(S))
+    S.close()
+    return done, wall, clk.summary(), launches
+
+
+def leg_serve(local: int, rank: int, requests: int, max_cycles: int = 300,
+              precisions=("fp32", "fp64")) -> dict:
+    """The first `requests` requests of the Poisson(50/s) stream of random banded
+    eigen-solves (n logU[1e4, 2e6], half-band U{5..25}, nev U{4..32}, d U{10..100},
+    k = nev + 5, m = max(30, 2k), smallest real part), submitted at their arrival
+    times to the continuous-batching server; latency from submission to result."""
+    from paper_1806_08020_gb300 import pp
+
+    spec = inputs.request_stream(count=requests)
+    reqs = []
+    for q in spec:  # inputs are generated before the timed region
+        A = inputs.banded_random(q["n"], q["w"], q["seed"] + 7919 * rank)
+        reqs.append((q, A, inputs.start_vector(A.n, q["seed"], 0), inputs.start_vector(A.n, q["seed"], 1)))
+    offered = len(reqs) / max(spec[-1]["arrival"], 1e-9)
+    out = {"workload": f"first {len(reqs)} requests of the Poisson(50/s) stream: banded n logU[1e4,2e6], "
+                       "half-band U{5..25}, nev U{4..32}, d U{10..100}, SR target, rtol 1e-8",
+           "requests": len(reqs), "sum_nev": int(sum(q["nev"] for q, *_ in reqs)),
+           "max_cycles_per_request": max_cycles}
+    got = {}
+    for name in precisions:
+        prec = pp.PP_FP64 if name == "fp64" else pp.PP_FP32
+        done, wall, clocks, launches = _serve_once(pp, reqs, prec, max_cycles, local)
+        lat = np.array([l for _, l in done.values()])
+        pairs = sum(count_pairs(r, reqs[i][0]["nev"], reqs[i][0]["rtol"]) for i, (r, _) in done.items())
+        out["served_" + name] = {
+            "value": round(pairs / wall, 3), "unit": UNIT, "seconds": round(wall, 2), "eigenpairs": pairs,
+            "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4), "p99": round(float(np.percentile(lat, 99)), 4),
+                          "max": round(float(lat.max()), 4)},
+            "load": {"offered_req_per_s": round(offered, 2), "achieved_req_per_s": round(len(done) / wall, 2)},
+            "converged": int(sum(r.status == 0 for r, _ in done.values())),
+            "fp64_continuations": int(sum(1 for r, _ in done.values() if prec == pp.PP_FP32 and r.stats["fp64_cycles"] > 0)),
+            "gpu_launches": launches, "clocks": clocks}
+        got[name] = done
+    if "fp32" in got and "fp64" in got:
+        errs = [_max_match_error(got["fp32"][i][0].lam, got["fp64"][i][0].lam) for i in got["fp32"] if i in got["fp64"]]
+        errs = [e for e in errs if e is not None]
+        out["rel_err_fp32_vs_fp64"] = {"max": max(errs) if errs else None,
+                                       "median": float("%.3g" % statistics.median(errs)) if errs else None,
+                                       "note": "per request, largest |lam_fp32 - lam_fp64| / |lam_fp64|; both meet "
+                                               "residual <= 1e-8 ||A||_1 on A in FP64"}
+    return out
+
+
+def run_serve(args, ws, rank, local):
+    """The request stream (first --requests requests) on its own line."""
+    leg = leg_serve(local, rank, args.requests, args.serve_max_cycles,
+                    precisions=(args.serve_precision,) if args.serve_precision != "both" else ("fp32", "fp64"))
+    first = leg["served_" + ("fp32" if args.serve_precision != "fp64" else "fp64")]
     return {"metric": "eigenpairs/s at residual 1e-8 and p50/p99 latency, served request stream",
-            "value": round(pairs / wall, 3), "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
-            "ms_per_step": round(wall * 1e3, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == pp.PP_FP64 else "f32 apply / f64 refine", "data": "synthetic (seeded generator)",
-            "config": {"workload": f"first {len(reqs)} requests of the Poisson(50/s) stream: banded n logU[1e4,2e6], "
-                                   "half-band U{5..25}, nev U{4..32}, d U{10..100}",
-                       "max_cycles_per_request": args.serve_max_cycles, "precision": args.serve_precision,
-                       "fp64_continuations": cont},
-            "latency_s": {"p50": round(float(np.percentile(lat, 50)), 4),
-                          "p99": round(float(np.percentile(lat, 99)), 4)},
-            "load": {"offered_req_per_s": round(offered, 2), "achieved_req_per_s": round(len(done) / wall, 2),
-                     "converged": conv, "requests": len(done)},
-            "gpu_launches": int(pp.pp_server_launch_count(S)), "clocks": clk.summary()}
+            "value": first["value"], "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
+            "ms_per_step": round(first["seconds"] * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.serve_precision == "fp64" else "f32 apply / f64 refine",
+            "data": "synthetic (seeded generator)", "config": {"workload": leg["workload"]},
+            "latency_s": first["latency_s"], "load": first["load"], "serve": leg,
+            "gpu_launches": first["gpu_launches"], "clocks": first["clocks"]}
 
 
 def _oracle_errors(lam: np.ndarray) -> list[float] | None:
@@ -557,63 +687,158 @@ def _match_errors(lam_a: np.ndarray, lam_b: np.ndarray) -> list[float]:
     return out
 
 
-def run_precision3d(args, ws, rank, local):
-    """n = 160^3 3-D CD, double polynomial 10 x 20 (Section 8): mixed precision vs FP64."""
+def _double_apply_bytes(n: int, stored: int, vbytes: int, inner, outer) -> tuple[int, int]:
+    """Algorithmic bytes and passes of one pi_2(tau(A)) x apply on DIA storage, following
+    the library's schedule: every pass reads the stored values (zeros included) and x;
+    inner passes write their output except the last; the running sum is read (not by
+    the first pass) and written (the last pass writes it only for the first tau of a
+    conjugate outer pair); a pair's first pass writes the temporary t and its second
+    reads t and p; the last inner pass of each tau reads the outer base (and t for an
+    outer pair) and writes the outer result."""
+    def tau_bytes(write_r: bool, outer_pair_second: bool, epilogue: bool) -> tuple[int, int]:
+        tot, passes, j = 0, 0, 0
+        steps = []
+        i = 0
+        while i < len(inner):
+            steps.append(inner[i].imag != 0)
+            i += 2 if inner[i].imag != 0 else 1
+        for s, pair in enumerate(steps):
+            last = s == len(steps) - 1
+            if pair:  # plain pass t = A p
+                tot += stored * vbytes + 2 * n * vbytes
+                passes += 1
+            b = stored * vbytes + n * vbytes * (2 if pair else 1)  # values, x (and p for a pair)
+            b += 0 if s == 0 else n * vbytes                       # r read
+            b += n * vbytes if (not last or write_r) else 0        # r write
+            b += 0 if last else n * vbytes                         # y write
+            if last and epilogue:
+                b += n * vbytes * (3 if outer_pair_second else 2)  # obase (+ ox) read, oy write
+            tot += b
+            passes += 1
+        return tot, passes
+    tot, passes = 0, 0
+    i = 0
+    while i < len(outer):
+        if outer[i].imag == 0:
+            b, p = tau_bytes(False, False, True)
+            tot, passes, i = tot + b, passes + p, i + 1
+        else:
+            b1, p1 = tau_bytes(True, False, False)
+            b2, p2 = tau_bytes(False, True, True)
+            tot, passes, i = tot + b1 + b2, passes + p1 + p2, i + 2
+    return tot, passes
+
+
+def leg_precision3d(local: int, rank: int, fmt_name: str = "auto", steps: int = 2, warmup: int = 1,
+                    sell_loop: int = 0, sell_c: int = 0) -> dict:
+    """n = 160^3 3-D CD (beta = 50), double polynomial 10 x 20 (Section 8), Arnoldi(40, 21),
+    nev 16: mixed precision (FP32 apply and basis, FP64 test and refinement on A) against
+    the FP64 method and the BF16-basis variant; per-eigenpair errors against FP64 and the
+    closed form; and the fused pi_2(tau(A)) v apply on its own, event-timed, against the
+    measured HBM bandwidth."""
     import torch
 
     from paper_1806_08020_gb300 import pp
 
-    torch.cuda.set_device(local)
     cfg = inputs.precision_3d()
     A = cfg["A"]
     seed = rank_seed(cfg["seed"], rank)
     b = inputs.start_vector(A.n, seed, 0)
     v0 = inputs.start_vector(A.n, seed, 1)
     stream = torch.cuda.Stream()
-    out = {}
-    for name, prec in (("mixed_fp32", pp.PP_FP32), ("mixed_bf16_basis", pp.PP_FP32_BF16), ("fp64", pp.PP_FP64)):
-        fmt = {"auto": pp.PP_FMT_AUTO, "sell": pp.PP_FMT_SELL, "dia": pp.PP_FMT_DIA, "csr": pp.PP_FMT_CSR}[args.format]
-        ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, max_cycles=60, sell_loop=args.sell_loop,
-                           sell_c=args.sell_c, format=fmt)
+    fmt = {"auto": pp.PP_FMT_AUTO, "sell": pp.PP_FMT_SELL, "dia": pp.PP_FMT_DIA, "csr": pp.PP_FMT_CSR}[fmt_name]
+    out, lams, apply_roof = {}, {}, None
+    for name, prec, st, wu in (("mixed_fp32", pp.PP_FP32, steps, warmup), ("fp64", pp.PP_FP64, 1, 1),
+                               ("mixed_bf16_basis", pp.PP_FP32_BF16, 1, 1)):
+        ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, max_cycles=60, sell_loop=sell_loop,
+                           sell_c=sell_c, format=fmt)
+        poly = None
 
         def solve():
+            nonlocal poly
             poly = pp.pp_build_poly2(ctx, cfg["d1"], cfg["d2"], b)
             return pp.pp_eigs(ctx, poly, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=False)
-        steps = max(1, args.steps if name == "mixed_fp32" else 1)
-        for _ in range(max(1, args.warmup if name == "mixed_fp32" else 1)):  # the others: one warm-up, one step
+        for _ in range(max(1, wu)):
             solve()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         pairs, res = 0, None
         with ClockSampler(local) as clk:
             e0.record(stream)
-            for _ in range(steps):
+            for _ in range(st):
                 res = solve()
-                pairs += int(np.sum(res.resid <= cfg["rtol"])) if res.status == 0 else 0
+                pairs += count_pairs(res, cfg["nev"], cfg["rtol"])
             e1.record(stream)
             torch.cuda.synchronize()
         t = e0.elapsed_time(e1) * 1e-3
-        out[name] = {"value": round(pairs / t, 3), "ms_per_step": round(t / steps * 1e3, 1), "steps": steps,
-                     "cycles": res.stats["cycles"], "fp64_cycles": res.stats["fp64_cycles"],
-                     "max_resid": float(np.max(res.resid)), "lam": res.lam, "clocks": clk.summary(),
-                     "launches": res.stats["kernel_launches"], "format": pp.pp_format_info(ctx),
-                     "t_apply_s": round(res.stats["t_apply"], 4), "t_orth_s": round(res.stats["t_orth"], 4),
-                     "t_restart_s": round(res.stats["t_restart"], 4)}
+        f = pp.pp_format_info(ctx)
+        out[name] = {"value": round(pairs / t, 3), "unit": UNIT, "ms_per_step": round(t / st * 1e3, 1), "steps": st,
+                     "cycles": int(res.stats["cycles"]), "fp64_cycles": int(res.stats["fp64_cycles"]),
+                     "max_resid": float(np.max(res.resid)), "clocks": clk.summary(),
+                     "launches": int(res.stats["kernel_launches"]), "format": f,
+                     "phases_ms": {k: round(res.stats[k] * 1e3, 1) for k in ("t_total", "t_apply", "t_orth", "t_restart")}}
+        lams[name] = res.lam
+        if name == "mixed_fp32":
+            # the fused apply alone: K applies of pi_2(tau(A)) on device vectors, events on the context's stream
+            x = torch.from_numpy(v0.astype(np.float32)).to(f"cuda:{local}")
+            y = torch.empty_like(x)
+            torch.cuda.synchronize()
+            for _ in range(3):
+                pp.pp_apply(poly, x.data_ptr(), y.data_ptr())
+            reps = 5
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(reps):
+                pp.pp_apply(poly, x.data_ptr(), y.data_ptr())
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ta = a0.elapsed_time(a1) * 1e-3 / reps
+            nbytes, passes = _double_apply_bytes(A.n, f["stored"], 4, pp.pp_poly_inner_roots(poly),
+                                                 pp.pp_poly_roots(poly))
+            peaks = _peaks()
+            hbm = peaks.get("hbm_gbs") or 6800.0
+            apply_roof = {"bound": "hbm", "achieved": round(nbytes / ta / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                          "frac": round(nbytes / ta / 1e9 / hbm, 4),
+                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback",
+                          "kernel": _format_name(f) + " general pass (running sum of tau, outer step fused)",
+                          "bytes_per_apply": int(nbytes), "passes_per_apply": passes,
+                          "ms_per_apply": round(ta * 1e3, 3), "avg_pass_us": round(ta / passes * 1e6, 2),
+                          "l2": "per pass: 115 MB of values + 16 MB vectors, above the 129 MB L2"}
         ctx.close()
-    err = _match_errors(out["mixed_fp32"]["lam"], out["fp64"]["lam"])
-    err16 = _match_errors(out["mixed_bf16_basis"]["lam"], out["fp64"]["lam"])
-    out["mixed_bf16_basis"]["rel_err_vs_fp64_per_eigenpair"] = [float("%.3g" % e) for e in err16]
-    for v in out.values():
-        del v["lam"]
-    m = out["mixed_fp32"]
+    lam_cf, kap_cf = _closed_form_3d_smallest(160, 50.0, 64)
+    for name in ("mixed_fp32", "mixed_bf16_basis"):
+        out[name]["rel_err_vs_fp64_per_eigenpair"] = [float("%.3g" % e) for e in _match_errors(lams[name], lams["fp64"])]
+    for name in out:
+        out[name]["rel_err_vs_closed_form_per_eigenpair"] = [float("%.3g" % e) for e in _match_errors(lams[name], lam_cf)]
+    out["note"] = ("eigenvalue condition numbers of this operator are ~1e7 (x-modes of D S D^-1), so residual <= 1e-8 "
+                   "||A||_1 bounds the eigenvalue errors only to ~10 kappa rtol ||A||_1; rel_err columns are reported")
+    out["apply_roofline"] = apply_roof
+    out["workload"] = cfg["name"]
+    return out
+
+
+def _closed_form_3d_smallest(N: int, beta: float, count: int):
+    """Smallest eigenvalues of the 7-point 3-D CD operator in closed form (Kronecker sum
+    of the tridiagonal factors: lam_x(i) + lam_y(j) + lam_z(k))."""
+    h = 1.0 / (N + 1)
+    c = np.cos(np.arange(1, N + 1) * np.pi / (N + 1))
+    lx = (2 - 2 * np.sqrt(1 - (beta * h / 2) ** 2) * c) / h**2
+    ly = (2 - 2 * c) / h**2
+    m = min(N, 12)
+    lam = np.sort((lx[:m, None, None] + ly[None, :m, None] + ly[None, None, :m]).ravel())[:count]
+    return lam.astype(complex), None
+
+
+def run_precision3d(args, ws, rank, local):
+    """The 3-D precision workload on its own line."""
+    leg = leg_precision3d(local, rank, args.format, max(1, args.steps), max(1, args.warmup), args.sell_loop,
+                          args.sell_c)
+    m = leg["mixed_fp32"]
     return {"metric": "eigenpairs/s at residual 1e-8, mixed precision vs FP64 (n=160^3 3-D CD, double polynomial)",
-            "value": m["value"], "unit": UNIT, "n_gpus": ws, "steps": m["steps"], "warmup": args.warmup,
+            "value": m["value"], "unit": UNIT, "n_gpus": ws, "steps": m["steps"], "warmup": max(1, args.warmup),
             "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 apply/basis, f64 refine", "data": "synthetic (seeded generator)",
-            "config": {"workload": cfg["name"], "n": A.n, "nnz": A.nnz, "d1": cfg["d1"], "d2": cfg["d2"],
-                       "m": cfg["m"], "k": cfg["k"], "nev": cfg["nev"], "rtol": cfg["rtol"]},
-            "mixed_fp32": m, "mixed_bf16_basis": out["mixed_bf16_basis"], "fp64": out["fp64"],
-            "rel_err_vs_fp64_per_eigenpair": [float("%.3g" % e) for e in err],
+            "config": {"workload": leg["workload"]}, "precision_3d": leg, "roofline": leg["apply_roofline"],
             "gpu_launches": m["launches"], "clocks": m["clocks"]}
 
 
@@ -739,7 +964,11 @@ def main():
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--serve-max-cycles", type=int, default=300)
-    ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--serve-precision", default="fp32", choices=["fp32", "fp64", "both"])
+    ap.add_argument("--serve-sample", type=int, default=32,
+                    help="requests of the serving stream in the default line's serve_sample leg")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="default line without the precision_3d, batch and serve_sample legs")
     ap.add_argument("--format", default="auto", choices=["auto", "sell", "dia", "csr"],
                     help="device format of the precision_3d arm (pp_opts.format); auto lets the tuner pick")
     ap.add_argument("--sell-c", type=int, default=0, choices=[0, 16, 32],

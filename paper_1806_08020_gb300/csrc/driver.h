@@ -312,6 +312,9 @@ struct Driver {
             sl = ns;
             CKS(ritz_test(Z, ppk::F64, nz, Sw, sl, rtol, R, S));
             S.vops += (int64_t)nz * nw;
+            if (std::getenv("PP_TRACE"))
+                std::fprintf(stderr, "[pp] refine %p round %d space %d max_resid %.3e nconv %d\n", (void *)this,
+                             round, nz, *std::max_element(R.res.begin(), R.res.end()), R.nconv);
             if (R.all) return PP_OK;
             const double mx = *std::max_element(R.res.begin(), R.res.end());
             if (!(mx < best)) break;
