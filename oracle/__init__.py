@@ -16,6 +16,7 @@ from .ppa import (  # noqa: F401
     Poly,
     add_stability_roots,
     apply_poly,
+    balance,
     build_double_poly,
     build_poly,
     build_poly_two,

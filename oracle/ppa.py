@@ -491,7 +491,8 @@ def thick_restart(V: np.ndarray, H: np.ndarray, m: int, Q: np.ndarray,
 def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: int, k: int,
          rtol: float, v0: np.ndarray, c: Counters, target_point: float = 1.0,
          target: str = "SM", max_cycles: int = 2000, sigma: float = 0.0,
-         log: Callable[[int, float], None] | None = None, restart: str = "ritz") -> EigResult:
+         log: Callable[[int, float], None] | None = None, restart: str = "ritz",
+         scale: np.ndarray | None = None) -> EigResult:
     """Thick-restarted Arnoldi(m, k) on ``op`` (Section 2 box step 2; Section 4).
 
     * Build V_{m+1}, H_{m+1,m} with CGS2 (one reorthogonalisation pass).
@@ -509,6 +510,9 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
     ``sigma`` is the shift of ``op``'s matrix; Rayleigh quotients use A itself.
     ``log`` (optional) is called as log(cycle, max relative residual) after
     each convergence test; it does not affect the arithmetic.
+    ``scale`` (balancing, see ``balance``): ``op`` acts on S = D^-1 A D with
+    D = diag(scale); each Ritz vector y of the operator is mapped to x = D y
+    before the test on A, which stays on A itself.
     ``restart="harmonic"``: the harmonic Arnoldi variant (Example 2): harmonic
     Ritz values (w.r.t. ``target_point``) and vectors replace the Ritz ones in
     the ordering, the convergence test and the restart, which keeps
@@ -552,6 +556,8 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
         while slot < nw:
             i = want[slot]
             y = V[:, :m] @ S[:, i]
+            if scale is not None:
+                y = scale * y
             y = y / np.linalg.norm(y)
             Ay = A @ y
             c.mvps += 1 if nu[i].imag == 0 else 2
@@ -590,6 +596,62 @@ def eigs(A: sp.csr_matrix, op: Callable[[np.ndarray], np.ndarray], nev: int, m: 
         j0 = kk
     srt = _target_sort(lam, target)
     return EigResult(lam[srt], X[:, srt], res[srt], False, max_cycles, c, nu[want][srt], hist)
+
+
+# ----------------------------------------------------------------------------
+# Balancing: a diagonal similarity (not in the paper; an opt-in transformation)
+# ----------------------------------------------------------------------------
+
+def balance(A: sp.csr_matrix, max_log_range: float = 600.0) -> tuple[np.ndarray, sp.csr_matrix]:
+    """The diagonal similarity S = D^-1 A D that makes A symmetric, when one exists.
+
+    Not part of the paper's method: a problem transformation for the strongly
+    non-normal convection-diffusion operators of Section 4, whose eigenvalue
+    condition numbers grow like e^(beta/2).  S symmetric means
+    a_ij d_j / d_i = a_ji d_i / d_j for every off-diagonal pair, i.e.
+    d_j / d_i = sqrt(a_ji / a_ij): this needs a_ij and a_ji nonzero together and
+    of the same sign, and the ratios multiplied around every cycle of the
+    graph to give 1.  D is found by walking the graph breadth first from each
+    component's first row (log d_root = 0), in log form, then every edge is
+    checked.  Returns (d, S) with d = exp(log d - max log d) (largest entry 1);
+    ValueError when no such D exists or its range exceeds e^max_log_range.
+    """
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    At = sp.csr_matrix(A.T)
+    logd = np.zeros(n)
+    seen = np.zeros(n, dtype=bool)
+    for root in range(n):
+        if seen[root]:
+            continue
+        seen[root] = True
+        queue = [root]
+        head = 0
+        while head < len(queue):
+            i = queue[head]
+            head += 1
+            cols = A.indices[A.indptr[i]:A.indptr[i + 1]]
+            vals = A.data[A.indptr[i]:A.indptr[i + 1]]
+            for j, aij in zip(cols, vals):
+                if j == i or aij == 0.0 or seen[j]:
+                    continue
+                aji = A[j, i]
+                if aji == 0.0 or (aji > 0) != (aij > 0):
+                    raise ValueError(f"balance: entries ({i},{j}) and ({j},{i}) are not nonzero with one sign")
+                logd[j] = logd[i] + 0.5 * (np.log(abs(aji)) - np.log(abs(aij)))
+                seen[j] = True
+                queue.append(j)
+    if logd.max() - logd.min() > max_log_range:
+        raise ValueError("balance: the scaling range exceeds e^%g" % max_log_range)
+    logd = logd - logd.max()
+    d = np.exp(logd)
+    coo = A.tocoo()
+    S = sp.csr_matrix((coo.data * np.exp(logd[coo.col] - logd[coo.row]), (coo.row, coo.col)), shape=A.shape)
+    S.sort_indices()
+    asym = abs(S - S.T)
+    if asym.nnz and asym.max() > 1e-12 * abs(S).max():
+        raise ValueError("balance: no diagonal similarity makes A symmetric (cycle condition fails)")
+    return d, S
 
 
 # ----------------------------------------------------------------------------
