@@ -92,6 +92,17 @@ typedef struct {
     int restart;        /* pp_eigs restart: PP_RESTART_RITZ (default) keeps Ritz vectors;
                            PP_RESTART_HARMONIC keeps harmonic Ritz vectors (the harmonic
                            Arnoldi variant of Example 2, for interior targets) */
+    int balance;        /* 0 (default): A as given.  1: balancing (not in the paper; an opt-in
+                           problem transformation): run the method on S = D^-1 A D, the diagonal
+                           similarity that makes A symmetric (d_j/d_i = sqrt(a_ji/a_ij) on every
+                           off-diagonal pair; needs a_ij, a_ji nonzero together with one sign and
+                           consistent cycles, as for central-difference convection-diffusion
+                           with cell Peclet number < 1; else pp_create returns PP_EINVAL; 2: the
+                           same where such a D exists, else A as given).  S has
+                           the eigenvalues of A with condition numbers 1.  Eigenvectors are
+                           returned for A (x = D y, unit norm) and the convergence test stays on
+                           A itself; start vectors, pp_apply and pp_orthogonalize act in the
+                           coordinates of S, and sigma is S's Gershgorin shift. */
     int dia_loop;       /* DIA row loop: 0 (default) = the tuner picks; 1 = one row per thread;
                            2 = four or 3 = two consecutive rows per thread with 16- or 8-byte
                            loads (FP32 contexts; taken only when the vectors are so aligned,
@@ -159,6 +170,10 @@ pp_status pp_debug_stall_sweeps(pp_ctx *ctx, int count);
 
 /* Number of library kernels launched on this context since pp_create. */
 int64_t pp_launch_count(const pp_ctx *ctx);
+
+/* Whether the context runs on the balanced matrix S = D^-1 A D (pp_opts.balance)
+ * and the range of its scaling, log(max d / min d).  Outputs may be NULL. */
+pp_status pp_balance_info(const pp_ctx *ctx, int *balanced, double *log_range);
 
 /* ||A||_1 (maximum absolute column sum) and the shift sigma used for the target. */
 pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);

@@ -92,6 +92,26 @@ struct Req {
     }
 };
 
+// A context for one instance of the batched engine: diagonal storage when the
+// matrix fits it (stencil and banded matrices; opts.format AUTO or DIA), else
+// SELL-32.  The batched kernels tune their own block shape, so the per-matrix
+// tuner is kept to a minimum (fixed chunk height, row loop and DIA row loop).
+static pp_status create_member(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                               const double *vals, const pp_opts &base, cudaStream_t stream, int make_twin) {
+    pp_opts o = base;
+    o.stream = stream;
+    if (!o.sell_c) o.sell_c = 32;
+    if (!o.sell_loop) o.sell_loop = 1;
+    if (!o.dia_loop) o.dia_loop = 1;
+    if (base.format == PP_FMT_AUTO || base.format == PP_FMT_DIA) {
+        o.format = PP_FMT_DIA;
+        pp_status st = pp_create_internal(out, n, rowptr, colind, vals, &o, make_twin);
+        if (st != PP_EINVAL || base.format == PP_FMT_DIA) return st;
+    }
+    o.format = PP_FMT_SELL;
+    return pp_create_internal(out, n, rowptr, colind, vals, &o, make_twin);
+}
+
 // Device bytes a request holds while admitted (matrix with SELL padding
 // headroom, FP64 residual operator, scratch, two basis slabs, Hessenberg,
 // FP64 test buffers, reduction scratch).
@@ -103,7 +123,8 @@ int64_t request_bytes(int64_t n, int64_t nnz, int m, int nev, int esz) {
     int64_t small = (int64_t)(m + 1) * m * 8 + 128 * 128 * 8 + 1300000 * 8;
     int64_t twin = 0;  // FP64 copy of an FP32 request and its basis (if FP32 cannot reach rtol)
     if (esz != 8)
-        twin = nnz * 12 * 13 / 10 + nnz * 12 + 8 * n + 8 * ldv * 8 + 1300000 * 8 + 2 * (int64_t)(m + 1) * ldv * (8 - esz);
+        twin = nnz * 12 * 13 / 10 + nnz * 12 + 8 * n + 8 * ldv * 8 + 1300000 * 8 + 2 * (int64_t)(m + 1) * ldv * (8 - esz) +
+               (int64_t)32 * ldv * 8 + 128 * 128 * 8;  // the refinement's extra Ritz vectors
     return mat + vecs + test + small + twin;
 }
 
@@ -183,6 +204,8 @@ class Engine {
         CKS(download_vecs(c, r->D->Y64, c->ldv(), r->cy.sl.nw, Yh, ppk::F64));
         for (int q = 0; q < r->cy.sl.nw; ++q)
             for (int64_t x = 0; x < c->n; ++x) w0[x] += Yh[(size_t)q * c->n + x];
+        if (!c->h_bal.empty())  // balanced: back to S's coordinates
+            for (int64_t x = 0; x < c->n; ++x) w0[x] /= c->h_bal[x];
         r->D.reset();
         r->dfree(r->V);
         r->dfree(r->V2);
@@ -324,9 +347,11 @@ class Engine {
         for (int i = 0; i < count; ++i) {
             Req *r = act[i];
             pp_ctx *c = r->c;
-            if (c->A.prec != pr || c->A.fmt != 2) return pp_fail(PP_EINVAL, "engine: mixed precisions or non-SELL matrix");
+            if (c->A.prec != pr || (c->A.fmt != 2 && c->A.fmt != 3))
+                return pp_fail(PP_EINVAL, "engine: mixed precisions or a matrix neither SELL nor DIA");
             const auto &A = c->A.sell;
-            pinst[i] = {A, c->sigma, r->V, c->ldv(), c->vec[6], c->vec[0], c->vec[1], c->vec[2]};
+            pinst[i] = {A, c->sigma, r->V, c->ldv(), c->vec[6], c->vec[0], c->vec[1], c->vec[2], c->A.dia,
+                        c->A.fmt == 3 ? 1 : 0};
             r->nblk = ppk::cgs_batch_blocks((int)c->n);
             r->blk0 = blocks;
             blocks += r->nblk;
@@ -499,8 +524,21 @@ class Engine {
         }
         const bool last = r->S.cycles >= max_cycles;
         if (c->A.prec != ppk::F64 && r->sw.should_refine(r->R, last)) {
+            // Far from rtol (more than ten times it) the FP64 refinement rarely
+            // finishes the job, and it runs outside the batched launches: such a
+            // request joins the batched FP64 engine at once, from its FP32 Ritz
+            // vectors.  Within ten times rtol the refinement is tried first.
+            const double mx = *std::max_element(r->R.res.begin(), r->R.res.end());
+            if (mx > 10 * r->rtol && c->twin && !last) {
+                trace_cycle("req", r, r->S.cycles, 32, r->R, "to fp64");
+                r->status = PP_OK;
+                r->to64 = true;
+                r->done = true;
+                return PP_OK;
+            }
             CKS(shared_refinement_basis(r));
-            s = r->D->refine(r->poly, r->cy.sl, r->nev, r->R, r->rtol, refine_steps, 3, r->S);
+            s = r->D->refine(r->poly, r->cy.sl, r->nev, r->R, r->rtol, refine_steps, 3, r->S, &r->cy, r->V, c->A.prec,
+                             r->m);
             trace_cycle("req", r, r->S.cycles, 64, r->R, r->R.all ? "refined: converged" : "refined");
             r->conv = s >= 0 && r->R.all;
             r->status = s < 0 ? s : (r->conv ? PP_OK : PP_ENOTCONV);
@@ -612,15 +650,9 @@ pp_status pp_batch_create(pp_batch **out, int count, const int64_t *n, const int
         }
         b->own_stream = true;
     }
-    pp_opts o = b->opts;
-    o.stream = b->stream;
-    o.format = PP_FMT_SELL;  // the batched pass kernel reads SELL
-    // the batched kernels have their own block-shape tuner; no per-matrix tuning
-    if (!o.sell_c) o.sell_c = 32;
-    if (!o.sell_loop) o.sell_loop = 1;
     b->ctx.assign(count, nullptr);
     for (int i = 0; i < count; ++i) {
-        pp_status st = pp_create(&b->ctx[i], n[i], rowptr[i], colind[i], vals[i], &o);
+        pp_status st = create_member(&b->ctx[i], n[i], rowptr[i], colind[i], vals[i], b->opts, b->stream, 1);
         if (st < 0) {
             delete b;
             return st;
@@ -774,13 +806,8 @@ pp_status pp_server_step(pp_server *s, int *active, int *queued) {
             r = std::move(s->queue.front());
             s->queue.pop_front();
         }
-        pp_opts o = s->opts;
-        o.stream = s->stream;
-        o.format = PP_FMT_SELL;
-        if (!o.sell_c) o.sell_c = 32;  // the batched kernels tune their own block shape
-        if (!o.sell_loop) o.sell_loop = 1;
-        pp_status st = pp_create_internal(&r->c, r->n, r->rowptr.data(), r->colind.data(), r->vals.data(), &o,
-                                          o.precision != PP_FP64);
+        pp_status st = create_member(&r->c, r->n, r->rowptr.data(), r->colind.data(), r->vals.data(), s->opts,
+                                     s->stream, s->opts.precision != PP_FP64);
         r->own_ctx = st >= 0;
         if (st >= 0) st = s->eng.start(r.get(), r->b.data(), r->v0.empty() ? nullptr : r->v0.data());
         std::vector<int64_t>().swap(r->rowptr);

@@ -793,6 +793,36 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
         }
         gl = std::min(gl, diag - off);
     }
+    // balancing (opts.balance): the operator's matrix becomes S = D^-1 A D, the
+    // diagonal similarity that makes A symmetric; ||A||_1 and the residual test
+    // stay on A, the shift is S's Gershgorin bound
+    int balance = opts ? opts->balance : 0;
+    if (balance < 0 || balance > 2) return pp_fail(PP_EINVAL, "pp_create: balance must be 0, 1 or 2");
+    std::vector<double> logd, svals;
+    const double *kvals = vals;  // values of the operator's matrix
+    if (balance) {
+        std::string why;
+        if (!ppd::symmetrizing_scale(n, rowptr, colind, vals, logd, why)) {
+            if (balance == 1) return pp_fail(PP_EINVAL, "pp_create: balance: %s", why.c_str());
+            balance = 0;  // 2: where a symmetrising D exists, else A as given
+        }
+    }
+    if (balance) {
+        svals.resize(nnz);
+        gl = INFINITY;
+        for (int64_t i = 0; i < n; ++i) {
+            double diag = 0, off = 0;
+            for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                svals[k] = vals[k] * std::exp(logd[colind[k]] - logd[i]);
+                if (colind[k] == i)
+                    diag += svals[k];
+                else
+                    off += std::fabs(svals[k]);
+            }
+            gl = std::min(gl, diag - off);
+        }
+        kvals = svals.data();
+    }
     pp_ctx *c = new pp_ctx();
     pp_opts_default(&c->opts);
     if (opts) c->opts = *opts;
@@ -842,8 +872,18 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     // stream-ordered uploads: the context's stream does not synchronise with the legacy stream
     if (cudaMemcpyAsync(d_rowptr, rp32.data(), (n + 1) * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
         cudaMemcpyAsync(d_col, colind, nnz * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(d_val, vals, nnz * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        cudaMemcpyAsync(d_val, kvals, nnz * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return fail(pp_fail(PP_ECUDA, "pp_create: upload failed"));
+    double *d_aval = nullptr;  // balanced: A's own values for the residual test
+    if (balance) {
+        c->h_bal.resize(n);
+        for (int64_t i = 0; i < n; ++i) c->h_bal[i] = std::exp(logd[i]);
+        if ((st = dmalloc(c, (void **)&d_aval, nnz * 8)) < 0 || (st = dmalloc(c, (void **)&c->d_bal, n * 8)) < 0)
+            return fail(st);
+        if (cudaMemcpyAsync(d_aval, vals, nnz * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(c->d_bal, c->h_bal.data(), n * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return fail(pp_fail(PP_ECUDA, "pp_create: upload failed"));
+    }
     // format: SELL-C unless its padding exceeds 30 % (then CSR); C and the
     // block size of the product kernels from the tuner unless opts fix C
     if (c->opts.sell_c != 0 && c->opts.sell_c != 16 && c->opts.sell_c != 32)
@@ -1055,6 +1095,12 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     c->A64.fmt = 1;
     c->A64.csr = {(int)n, d_rowptr, d_col, d_val};
     if (pr == ppk::F64) c->A64 = M;
+    c->S64 = c->A64;
+    if (balance) {  // the test on A itself; S64 (the refinement's projections) stays S
+        c->A64.prec = ppk::F64;
+        c->A64.fmt = 1;
+        c->A64.csr = {(int)n, d_rowptr, d_col, d_aval};
+    }
     if ((st = ensure_part(c, ppk::cgs_part_doubles(ppk::cgs_grid((int)n)))) < 0) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: setup kernels failed"));
     if (c->bprec != ppk::F64 && make_twin) {
@@ -1119,6 +1165,17 @@ pp_status pp_orthogonalize(pp_ctx *c, const void *V, int64_t ldv, int j, void *w
     CK(cudaMemcpyAsync(h_host, dh, (size_t)(j + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return check_sweeps(c);
+}
+
+pp_status pp_balance_info(const pp_ctx *c, int *balanced, double *log_range) {
+    if (!c) return pp_fail(PP_EINVAL, "pp_balance_info: null context");
+    if (balanced) *balanced = c->d_bal ? 1 : 0;
+    if (log_range) {
+        double lo = 0;
+        for (double d : c->h_bal) lo = std::min(lo, std::log(d));
+        *log_range = -lo;
+    }
+    return PP_OK;
 }
 
 pp_status pp_matrix_info(const pp_ctx *c, double *norm1, double *sigma) {

@@ -73,6 +73,11 @@ struct pp_ctx {
     bool own_stream = false;
     ppk::Matrix A;     // storage precision (shifted operator uses sigma)
     ppk::Matrix A64;   // FP64 copy for residuals on A (same as A in FP64 mode)
+    ppk::Matrix S64;   // FP64 copy of the operator's matrix: S = D^-1 A D when balanced, else A64
+    // balancing (opts.balance): the diagonal d of D (largest entry 1) on the device
+    // and the host; null / empty when A is used as given
+    double *d_bal = nullptr;
+    std::vector<double> h_bal;
     size_t esz = 8;    // bytes per stored vector element
     ppk::Prec bprec = ppk::F64;  // Arnoldi basis storage (BF16 for PP_FP32_BF16, else as the vectors)
     size_t besz = 8;             // bytes per basis element

@@ -52,7 +52,8 @@ pp_status first_cycle_ideal(pp_ctx *c, const pp_poly *p, const double *b, int m,
     return PP_OK;
 }
 
-// y = (A - sigma I) b in FP64 on the device (the residual operator, exact values).
+// y = (A - sigma I) b in FP64 on the device (the operator's matrix with its exact
+// values: S = D^-1 A D when balanced).
 pp_status damp_start(pp_ctx *c, const double *b, std::vector<double> &out) {
     const int64_t n = c->n;
     void *x = nullptr, *y = nullptr;
@@ -70,7 +71,7 @@ pp_status damp_start(pp_ctx *c, const double *b, std::vector<double> &out) {
     out.assign(n, 0.0);
     cudaError_t e = cudaMemcpyAsync(x, b, (size_t)n * 8, cudaMemcpyDefault, c->stream);  // b: host or device
     if (e == cudaSuccess) {
-        ppk::launch_step(c->A64, a, c->stream);
+        ppk::launch_step(c->S64, a, c->stream);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), y, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);

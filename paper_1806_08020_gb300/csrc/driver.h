@@ -30,6 +30,18 @@ struct RitzOut {
     bool all = false;
 };
 
+// Ritz values of H_m (host FP64), the wanted set (nev slots, one more when a
+// conjugate pair would split) and its Ritz vectors' coefficients (Section 4).
+struct Cycle {
+    int m = 0;
+    std::vector<double> Hm, wr, wi, Sv, Sw;
+    std::vector<cd> nu;
+    std::vector<int> order;
+    Slots sl;
+    bool harmonic = false;
+    std::vector<double> cvec;  // harmonic: [-h f; 1], the direction of every harmonic residual
+};
+
 struct Driver {
     pp_ctx *c;
     int64_t n, ldv;
@@ -41,6 +53,7 @@ struct Driver {
     int *dpartner = nullptr;
     // refinement
     double *Z = nullptr, *dG = nullptr, *Yb = nullptr;
+    double *Ye = nullptr, *dQe = nullptr;  // extra Ritz vectors of the refinement and their coefficients
     static constexpr int kZcap = 128;
 
     ~Driver() {
@@ -77,6 +90,10 @@ struct Driver {
         // FP64 arithmetic and output whatever the basis precision
         ppk::launch_rotate64(pb, (int)n, B, ldv, mcols, dQ, nw, Y64, ldv, c->stream);
         CKS(check_launch(c));
+        if (c->d_bal) {  // balanced: Ritz vectors of S mapped to A's coordinates, x = D y
+            ppk::launch_scale_rows((int)n, nw, Y64, ldv, Y64, ldv, c->d_bal, false, c->stream);
+            CKS(check_launch(c));
+        }
         for (int s = 0; s < nw; ++s) {
             ppk::StepArgs a;
             a.x = Y64 + (size_t)s * ldv;
@@ -158,19 +175,48 @@ struct Driver {
         return PP_OK;
     }
 
+    // Value of the Arnoldi operator's polynomial at an eigenvalue estimate mu of
+    // A: pi(mu - sigma), pi_2(1 - pi_1(mu - sigma)) for a double polynomial, or
+    // mu - sigma without one (the operator is then A - sigma I itself).
+    cd op_value(const pp_poly *p, cd mu) const {
+        const cd z = mu - c->sigma;
+        if (!p) return z;
+        auto prod = [](const std::vector<cd> &roots, cd x) {
+            cd v = 1.0;
+            for (const cd &t : roots) v *= 1.0 - x / t;
+            return v;
+        };
+        if (p->inner) return prod(p->roots, 1.0 - prod(p->inner->roots, z));
+        return prod(p->roots, z);
+    }
+
+    // Extra Ritz vectors carried by the refinement besides the wanted ones: the
+    // next ones in the Arnoldi's order.  When the boundary of the wanted set
+    // falls inside a cluster that FP32 cannot resolve (eigenvalues closer than
+    // u_32 ||A||), only a space holding the whole cluster lets Rayleigh-Ritz
+    // separate the wanted members from their neighbours.
+    static int refine_extra(int nev, int m, int nw) { return std::max(0, std::min(std::min(nev + 2, m - nw - 1), 32)); }
+
     // FP64 refinement on A (mixed precision): Rayleigh-Ritz of A itself on a
-    // search space built in FP64 from the wanted Ritz vectors Y.  With an FP64
-    // copy of the operator the space is span{pi(A) Y} (pi_1(A) Y for a double
-    // polynomial): the polynomial keeps the wanted part of Y and damps the FP32
+    // search space built in FP64 from the wanted Ritz vectors Y and, from the
+    // second round on (with the polynomial), `extra` further Ritz vectors of the
+    // cycle.  With an FP64 copy of the operator the space is span{pi(A) Y}, then
+    // span{pi(A) [Y, Y_e]} (pi_1(A) for a double
+    // polynomial): the polynomial keeps the wanted part and damps the FP32
     // rounding noise in the unwanted part of the spectrum (one step of subspace
-    // iteration).  Without
-    // one it is the block Krylov space span{Y, A Y, ..., A^s Y}.  The Ritz
-    // pairs nearest the current estimates replace them, for up to `rounds`
-    // rounds; a round that does not lower the largest residual is undone and
-    // ends the refinement, so the estimates never get worse.  A failed dense
-    // eigensolve or too few candidates also end it.
+    // iteration).  Without one it is the block Krylov space span{Y, A Y, ...,
+    // A^s Y}.  The refined Ritz pairs are ranked as the Arnoldi ranks its Ritz
+    // values (distance of the operator's value to its target), the first nev
+    // slots replace the wanted ones and the next ones the extras, for up to
+    // `rounds` rounds; a round that does not lower the largest residual is
+    // undone and ends the refinement (the first one only when no extras
+    // follow), so the estimates never get worse.  A
+    // failed dense eigensolve or too few candidates also end it.
+    // cy, V (mcols columns of precision pb): the cycle the extras come from
+    // (may be null: no extras).
     pp_status refine(const pp_poly *p, Slots &sl, int nev, RitzOut &R, double rtol, int steps, int rounds,
-                     pp_stats &S) {
+                     pp_stats &S, const Cycle *cy = nullptr, const void *V = nullptr, ppk::Prec pb = ppk::F64,
+                     int mcols = 0) {
         if (!Z) CKS(alloc((void **)&Z, (size_t)ldv * (kZcap + 1) * 8));
         if (!dG) CKS(alloc((void **)&dG, (size_t)(kZcap + 1) * kZcap * 8));
         if (!Yb) CKS(alloc((void **)&Yb, (size_t)ldv * (wcap + 1) * 8));
@@ -182,12 +228,54 @@ struct Driver {
         steps = std::max(1, std::min(steps, kZcap / (nev + 1) - 1));
         const int ldg = kZcap + 1;
         double *W = AY64 + (size_t)(nev + 1) * ldv;  // spare FP64 column (context vectors are FP32 here)
-        auto project = [&](int col, int nz) -> pp_status {  // G[:, col] = Z^T A z_col
+        // extra Ritz vectors of the cycle (with the polynomial and its FP64 copy)
+        // extra Ritz vectors of the cycle (with the polynomial and its FP64 copy);
+        // the first round goes without them (they double its cost and the wanted
+        // vectors alone usually suffice), the following rounds carry them
+        int ne = 0;
+        const int extra = (tw && cy && V) ? refine_extra(nev, cy->m, sl.nw) : 0;
+        auto cycle_extras = [&]() -> pp_status {
+            ne = 0;
+            if (!Ye) CKS(alloc((void **)&Ye, (size_t)ldv * 32 * 8));
+            if (!dQe) CKS(alloc((void **)&dQe, (size_t)kZcap * kZcap * 8));
+            std::vector<double> Se;
+            const int m = cy->m;
+            for (int q = sl.nw; q < m && ne < extra;) {
+                const int i = cy->order[q];
+                if (cy->wi[i] == 0.0) {
+                    Se.insert(Se.end(), &cy->Sv[(size_t)i * m], &cy->Sv[(size_t)i * m] + m);
+                    ne += 1;
+                    q += 1;
+                } else {
+                    if (ne + 2 > extra) break;
+                    const int base = cy->wi[i] > 0 ? i : i - 1;
+                    Se.insert(Se.end(), &cy->Sv[(size_t)base * m], &cy->Sv[(size_t)base * m] + 2 * m);
+                    ne += 2;
+                    q += 2;
+                }
+            }
+            if (ne) {
+                CK(cudaMemcpyAsync(dQe, Se.data(), Se.size() * 8, cudaMemcpyHostToDevice, c->stream));
+                ppk::launch_rotate64(pb, (int)n, V, ldv, mcols, dQe, ne, Ye, ldv, c->stream);
+                CKS(check_launch(c));
+                S.vops += (int64_t)mcols * ne;
+            }
+            return PP_OK;
+        };
+        // Y64 holds vectors of A's coordinates (x = D y when balanced): the search
+        // space lives in the coordinates of the operator's matrix S (= A unbalanced)
+        double *U = AY64;  // spare FP64 column while the space is built
+        auto to_operator = [&](const double *y) -> const double * {
+            if (!c->d_bal) return y;
+            ppk::launch_scale_rows((int)n, 1, y, ldv, U, ldv, c->d_bal, true, c->stream);
+            return U;
+        };
+        auto project = [&](int col, int nz) -> pp_status {  // G[:, col] = Z^T S z_col
             ppk::StepArgs a;
             a.x = Z + (size_t)col * ldv;
             a.y = W;
             a.plain = 1;
-            ppk::launch_step(c->A64, a, c->stream);
+            ppk::launch_step(c->S64, a, c->stream);
             CKS(check_launch(c));
             ppk::CgsArgs ca;
             ca.mode = 0;
@@ -217,18 +305,21 @@ struct Driver {
             int nz = 0;
             CK(cudaMemsetAsync(dG, 0, (size_t)ldg * kZcap * 8, c->stream));
             if (tw) {
-                for (int s = 0; s < nw; ++s) {
-                    CKS(op_apply(tw, pf, Y64 + (size_t)s * ldv, W));
+                for (int s = 0; s < nw + ne; ++s) {
+                    const double *y = s < nw ? to_operator(Y64 + (size_t)s * ldv) : Ye + (size_t)(s - nw) * ldv;
+                    CKS(check_launch(c));
+                    CKS(op_apply(tw, pf, y, W));
                     CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, c->d_small + 2048));
                     S.dots += 2 * nz + 1;
                     S.vops += 4 * nz + 2;
                     nz++;
                 }
-                S.mvps += op_mvps(pf) * nw;
+                S.mvps += op_mvps(pf) * (nw + ne);
                 for (int col = 0; col < nz; ++col) CKS(project(col, nz));
             } else {
                 for (int s = 0; s < nw; ++s) {
-                    CK(cudaMemcpyAsync(W, Y64 + (size_t)s * ldv, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+                    const double *y = to_operator(Y64 + (size_t)s * ldv);
+                    CK(cudaMemcpyAsync(W, y, n * 8, cudaMemcpyDeviceToDevice, c->stream));
                     CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, c->d_small + 2048));
                     nz++;
                 }
@@ -239,7 +330,7 @@ struct Driver {
                         a.x = Z + (size_t)col * ldv;
                         a.y = W;
                         a.plain = 1;
-                        ppk::launch_step(c->A64, a, c->stream);
+                        ppk::launch_step(c->S64, a, c->stream);
                         CKS(check_launch(c));
                         CKS(cgs2_step(c, ppk::F64, Z, ldv, nz, W, dG + (size_t)col * ldg));
                         S.dots += 2 * nz + 1;
@@ -263,37 +354,38 @@ struct Driver {
                 if (!std::isfinite(v)) return PP_OK;
             std::vector<double> wr(nz), wi(nz), Sv((size_t)nz * nz);
             if (!ppd::dense_eig(nz, G.data(), nz, wr.data(), wi.data(), Sv.data(), nz)) return PP_OK;
-            // the refined wanted set: the Ritz values of G nearest the current
-            // estimates, a conjugate pair as one unit, until nev slots are filled
-            // (one more when the last unit is a pair); FP32 may have shown a pair
-            // where FP64 resolves two real values, so the slot layout is rebuilt
-            std::vector<cd> est;
-            for (int q = 0; q < sl.nw; ++q)
-                if (sl.partner[q] == q || sl.sg[q] > 0) est.push_back(cd(R.lre[q], std::fabs(R.lim[q])));
+            // the refined Ritz values (a conjugate pair as one unit, its Im > 0
+            // member) ranked as the Arnoldi ranks its Ritz values: by the
+            // distance of the operator's value at them to its target (FP32 may
+            // have shown a pair where FP64 resolves two real values, so the slot
+            // layout is rebuilt); the first nev slots are the wanted set, the
+            // next ones (up to ne columns) the extras of the next round
             std::vector<int> units;
-            std::vector<double> dist;
+            std::vector<cd> nuv;
             for (int i = 0; i < nz; ++i) {
                 if (wi[i] < 0) continue;
-                double dmin = INFINITY;
-                for (const cd &e : est) dmin = std::min(dmin, std::abs(cd(wr[i], wi[i]) - e));
                 units.push_back(i);
-                dist.push_back(dmin);
+                nuv.push_back(op_value(p, cd(wr[i], wi[i])));
             }
-            std::vector<int> ord(units.size());
-            for (size_t q = 0; q < ord.size(); ++q) ord[q] = (int)q;
-            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return dist[a] < dist[b]; });
+            const std::vector<int> ord = ppd::ritz_order(nuv, p ? 1.0 : 0.0);
             Slots ns;
-            std::vector<int> pick;
+            std::vector<int> pick, pick_e;
+            int nxe = 0;
             for (int q : ord) {
-                if (ns.nw >= nev) break;
-                int i = units[q];
-                pick.push_back(i);
-                ns.nw += wi[i] != 0.0 ? 2 : 1;
+                const int i = units[q];
+                const int w = wi[i] != 0.0 ? 2 : 1;
+                if (ns.nw < nev) {
+                    pick.push_back(i);
+                    ns.nw += w;
+                } else if (nxe + w <= ne) {
+                    pick_e.push_back(i);
+                    nxe += w;
+                }
             }
             if (ns.nw < nev) return PP_OK;
             ns.partner.assign(ns.nw, 0);
             ns.sg.assign(ns.nw, 0.0);
-            std::vector<double> Sw((size_t)nz * ns.nw);
+            std::vector<double> Sw((size_t)nz * ns.nw), Swe;
             int s = 0;
             for (int i : pick) {
                 std::copy(&Sv[(size_t)i * nz], &Sv[(size_t)i * nz] + nz, &Sw[(size_t)s * nz]);
@@ -309,19 +401,43 @@ struct Driver {
                     s += 2;
                 }
             }
+            for (int i : pick_e) Swe.insert(Swe.end(), &Sv[(size_t)i * nz], &Sv[(size_t)i * nz] + (size_t)nz * (wi[i] != 0.0 ? 2 : 1));
             sl = ns;
             CKS(ritz_test(Z, ppk::F64, nz, Sw, sl, rtol, R, S));
             S.vops += (int64_t)nz * nw;
-            if (std::getenv("PP_TRACE"))
-                std::fprintf(stderr, "[pp] refine %p round %d space %d max_resid %.3e nconv %d\n", (void *)this,
-                             round, nz, *std::max_element(R.res.begin(), R.res.end()), R.nconv);
+            if (trace_refine())
+                std::fprintf(stderr, "[pp] refine %p round %d space %d max_resid %.3e nconv %d\n", (void *)this, round,
+                             nz, *std::max_element(R.res.begin(), R.res.end()), R.nconv);
             if (R.all) return PP_OK;
             const double mx = *std::max_element(R.res.begin(), R.res.end());
+            if (round == 0 && extra > 0) {
+                // the second round adds the cycle's next Ritz vectors to the best wanted ones
+                if (mx < best) {
+                    best = mx;
+                    sl_best = sl;
+                    R_best = R;
+                    CK(cudaMemcpyAsync(Yb, Y64, (size_t)ldv * sl.nw * 8, cudaMemcpyDeviceToDevice, c->stream));
+                } else {
+                    sl = sl_best;
+                    R = R_best;
+                    CK(cudaMemcpyAsync(Y64, Yb, (size_t)ldv * sl.nw * 8, cudaMemcpyDeviceToDevice, c->stream));
+                }
+                CKS(cycle_extras());
+                continue;
+            }
             if (!(mx < best)) break;
             best = mx;
             sl_best = sl;
             R_best = R;
             CK(cudaMemcpyAsync(Yb, Y64, (size_t)ldv * sl.nw * 8, cudaMemcpyDeviceToDevice, c->stream));
+            // the next round's extras: the following refined Ritz vectors
+            ne = nxe;
+            if (ne) {
+                CK(cudaMemcpyAsync(dQe, Swe.data(), Swe.size() * 8, cudaMemcpyHostToDevice, c->stream));
+                ppk::launch_rotate64(ppk::F64, (int)n, Z, ldv, nz, dQe, ne, Ye, ldv, c->stream);
+                CKS(check_launch(c));
+                S.vops += (int64_t)nz * ne;
+            }
         }
         // undo the last round if it did not improve
         const double mx = R.res.empty() ? INFINITY : *std::max_element(R.res.begin(), R.res.end());
@@ -331,6 +447,10 @@ struct Driver {
             CK(cudaMemcpyAsync(Y64, Yb, (size_t)ldv * sl.nw * 8, cudaMemcpyDeviceToDevice, c->stream));
         }
         return PP_OK;
+    }
+    static bool trace_refine() {
+        static const bool on = std::getenv("PP_TRACE") != nullptr;
+        return on;
     }
 };
 
@@ -350,8 +470,9 @@ inline void trace_cycle(const char *who, const void *id, int64_t cycle, int prec
 }
 
 // When the FP32 cycles of the mixed mode hand over to the FP64 refinement:
-// within 10 rtol; at the FP32 floor (below 1e-6 and no longer halving per
-// cycle); after three cycles without halving at any level (an operator too
+// within 50 rtol (the refinement with its extra Ritz vectors gains one to two
+// orders of magnitude); at the FP32 floor (below 1e-6 and no longer halving
+// per cycle); after two cycles without halving at any level (an operator too
 // non-normal for FP32, or an FP32 apply swamped by the growth of the partial
 // products of a high-degree polynomial); or at the last cycle.
 struct MixedSwitch {
@@ -362,9 +483,9 @@ struct MixedSwitch {
         double mx = *std::max_element(R.res.begin(), R.res.end());
         stall = (mx < 0.5 * best) ? 0 : stall + 1;
         best = std::min(best, mx);
-        if (last_cycle || mx <= 10 * rtol) return true;
+        if (last_cycle || mx <= 50 * rtol) return true;
         if (mx <= std::max(rtol, 1e-6) && stall >= 1) return true;
-        return stall >= 3;
+        return stall >= 2;
     }
     // after a refinement that missed rtol, keep cycling in FP32 from here
     void reset() {
@@ -373,17 +494,6 @@ struct MixedSwitch {
     }
 };
 
-// Ritz values of H_m (host FP64), the wanted set (nev slots, one more when a
-// conjugate pair would split) and its Ritz vectors' coefficients (Section 4).
-struct Cycle {
-    int m = 0;
-    std::vector<double> Hm, wr, wi, Sv, Sw;
-    std::vector<cd> nu;
-    std::vector<int> order;
-    Slots sl;
-    bool harmonic = false;
-    std::vector<double> cvec;  // harmonic: [-h f; 1], the direction of every harmonic residual
-};
 
 // With harmonic set, the values are the harmonic Ritz values with respect to
 // the target t: eigenvalues of K = H_m + h^2 f e_m^T, f = (H_m - t I)^{-T} e_m,

@@ -89,7 +89,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
             break;
         }
         if (mixed && sw.should_refine(R, cycle == c->opts.max_cycles)) {
-            CKS(D.refine(p, cy.sl, nev, R, rtol, c->opts.refine_steps, 3, S));
+            CKS(D.refine(p, cy.sl, nev, R, rtol, c->opts.refine_steps, 3, S, &cy, V, bpr, m));
             S.nconv = R.nconv;
             trace_cycle("eigs", c, cycle, 64, R, R.all ? "refined: converged" : "refined");
             converged = R.all;
@@ -105,6 +105,8 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
                 CKS(download_vecs(c, D.Y64, ldv, cy.sl.nw, Yh, ppk::F64));
                 for (int s = 0; s < cy.sl.nw; ++s)
                     for (int64_t i = 0; i < n; ++i) w0[i] += Yh[(size_t)s * n + i];
+                if (!c->h_bal.empty())  // the twin's Krylov space is in S's coordinates (y = D^-1 x)
+                    for (int64_t i = 0; i < n; ++i) w0[i] /= c->h_bal[i];
                 pp_ctx *tw = c->twin;
                 const int max_c = tw->opts.max_cycles;
                 tw->opts.max_cycles = (int)std::max<int64_t>(1, c->opts.max_cycles - cycle);

@@ -91,10 +91,40 @@ __device__ void reduce_partials(const double *part, int nblocks, int nout, doubl
 constexpr int kRows = 64;
 constexpr int kQ = kRows / 32;
 
-// Per-block partial sums of a sweep, then the last block's reduction and (mode
-// 2) the Hessenberg column.  acc[cc] is the block-local projection on column
-// warp + NW cc (NW warps per block); nrm the squared norm of the updated
-// vector's rows.
+// The grid reduction of a sweep once every block has written its `nout`
+// partials part[bid * nout + o]: the last block of each group of 32 sums the
+// group's partials (block order), the last group sums the group sums (group
+// order) into a.out, and in mode 2 writes the Hessenberg column.
+template <int NW>
+__device__ __forceinline__ void cgs_reduce_tail(const CgsArgs &a, int bid, int nblk, int nout) {
+    const int tid = threadIdx.x;
+    const int j = a.j;
+    const int ng = (nblk + 31) / 32, g = bid / 32;
+    const int gsize = nblk - 32 * g < 32 ? nblk - 32 * g : 32;
+    double *gpart = a.part + (size_t)nblk * nout;
+    if (!last_block(a.ticket + 1 + g, gsize)) return;
+    reduce_partials(a.part + (size_t)g * 32 * nout, gsize, nout, gpart + (size_t)g * nout);
+    __syncthreads();
+    if (tid == 0) a.ticket[1 + g] = 0;
+    if (!last_block(a.ticket, ng)) return;
+    reduce_partials(gpart, ng, nout, a.out);
+    __syncthreads();
+    if (tid == 0) *a.ticket = 0;
+    if (a.mode == 2) {
+        __threadfence_block();
+        __syncthreads();
+        double nn = sqrt(a.out[0]);
+        for (int c = tid; c < j; c += NW * 32) a.hcol[c] = a.h1[c] + a.h[c];
+        if (tid == 0) {
+            a.hcol[j] = nn;
+            a.scal[0] = nn > 0 ? 1.0 / nn : 0.0;
+        }
+    }
+}
+
+// Per-block partial sums of an FP64 sweep, then the grid reduction.  acc[cc]
+// is the block-local projection on column warp + NW cc (NW warps per block);
+// nrm the squared norm of the updated vector's rows.
 template <int CPW, int NW = kWarps>
 __device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, const double (&acc)[CPW],
                                            double nrm) {
@@ -124,29 +154,54 @@ __device__ __forceinline__ void cgs_finish(const CgsArgs &a, int bid, int nblk, 
             part[a.mode == 1 ? j : 0] = s;
         }
     }
-    // two-level reduction: the last block of each group of 32 sums the group's
-    // partials (block order), the last group sums the group sums (group order)
-    const int ng = (nblk + 31) / 32, g = bid / 32;
-    const int gsize = nblk - 32 * g < 32 ? nblk - 32 * g : 32;
-    double *gpart = a.part + (size_t)nblk * nout;
-    if (!last_block(a.ticket + 1 + g, gsize)) return;
-    reduce_partials(a.part + (size_t)g * 32 * nout, gsize, nout, gpart + (size_t)g * nout);
-    __syncthreads();
-    if (tid == 0) a.ticket[1 + g] = 0;
-    if (!last_block(a.ticket, ng)) return;
-    reduce_partials(gpart, ng, nout, a.out);
-    __syncthreads();
-    if (tid == 0) *a.ticket = 0;
-    if (a.mode == 2) {
-        __threadfence_block();
-        __syncthreads();
-        double nn = sqrt(a.out[0]);
-        for (int c = tid; c < j; c += NW * 32) a.hcol[c] = a.h1[c] + a.h[c];
-        if (tid == 0) {
-            a.hcol[j] = nn;
-            a.scal[0] = nn > 0 ? 1.0 / nn : 0.0;
+    cgs_reduce_tail<NW>(a, bid, nblk, nout);
+}
+
+// (h, l) += (bh, bl) for compensated FP32 sums: Knuth's TwoSum of the leading
+// parts, the error added to the trailing parts.
+__device__ __forceinline__ void pair_add(float &h, float &l, float bh, float bl) {
+    const float t = __fadd_rn(h, bh);
+    const float z = __fsub_rn(t, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(t, z)), __fsub_rn(bh, z));
+    h = t;
+    l = __fadd_rn(__fadd_rn(l, bl), e);
+}
+
+// The same for an FP32 sweep whose projections are compensated pairs (hi +
+// lo): their warp sums stay compensated FP32 pairs (on this part an FP64
+// instruction costs as much as a few dozen FP32 ones), lane 0 hands hi + lo
+// to the FP64 partials; the squared norm nrm is FP64.
+template <int CPW>
+__device__ __forceinline__ void cgs_finish_f32(const CgsArgs &a, int bid, int nblk, float (&hi)[CPW],
+                                               float (&lo)[CPW], double nrm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int j = a.j;
+    __shared__ double nrm_sh[kWarps];
+    const int nout = (a.mode == 0) ? j : (a.mode == 1 ? j + 1 : 1);
+    double *part = a.part + (size_t)bid * nout;
+    if (a.mode != 2) {
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+            float h = hi[cc], l = lo[cc];
+#pragma unroll
+            for (int off = 16; off; off >>= 1)
+                pair_add(h, l, __shfl_xor_sync(0xffffffffu, h, off), __shfl_xor_sync(0xffffffffu, l, off));
+            int c = warp + kWarps * cc;
+            if (lane == 0 && c < j) part[c] = (double)h + (double)l;
         }
     }
+    if (a.mode != 0) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+        if (lane == 0) nrm_sh[warp] = nrm;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0;
+            for (int ww = 0; ww < kWarps; ++ww) s += nrm_sh[ww];
+            part[a.mode == 1 ? j : 0] = s;
+        }
+    }
+    cgs_reduce_tail<kWarps>(a, bid, nblk, nout);
 }
 
 // The sweep of block `bid` out of `nblk` blocks working on an FP64 basis:
@@ -255,8 +310,8 @@ __device__ __forceinline__ void dot2_term(float x, float y, float &s, float &c) 
 // load; w is FP32).  The first projection h1 = V^T w and both updates w - V h
 // run in FP32 (FP32 FMAs are many times faster than FP64 ones on this part);
 // the reorthogonalising projection h2 = V^T w1 uses Dot2, so the second
-// Gram-Schmidt pass is accurate to about twice FP32 precision.  Squared norms
-// accumulate in FP64.
+// Gram-Schmidt pass is accurate to about twice FP32 precision; their warp
+// sums are compensated FP32 pairs.  Squared norms accumulate in FP64.
 template <typename TV, int CPW>
 __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
@@ -277,6 +332,8 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
     float hi[CPW], lo[CPW];
 #pragma unroll
     for (int cc = 0; cc < CPW; ++cc) hi[cc] = lo[cc] = 0.f;
+    // the squared norm in FP64: the entries of pi(A) v_j can exceed sqrt of the
+    // FP32 range (high-degree polynomials), where an FP32 square overflows
     double nrm = 0;
     const int ntiles = (n + RT - 1) / RT;
     for (int tile = bid; tile < ntiles; tile += nblk) {
@@ -338,10 +395,7 @@ __device__ __forceinline__ void cgs_body_f32(const CgsArgs &a, int bid, int nblk
                     for (int q = 0; q < QT; ++q) dot2_term(vv[cc][q], wsh[lane + 32 * q], hi[cc], lo[cc]);
         }
     }
-    double acc[CPW];
-#pragma unroll
-    for (int cc = 0; cc < CPW; ++cc) acc[cc] = (double)hi[cc] + (double)lo[cc];
-    cgs_finish<CPW>(a, bid, nblk, acc, nrm);
+    cgs_finish_f32<CPW>(a, bid, nblk, hi, lo, nrm);
 }
 
 template <typename T, int CPW, int NW>
@@ -648,6 +702,18 @@ __global__ void k_unit_into(int n, const double *x, const double *nrm2, T *dst) 
             dst[i] = (float)v;
         else
             dst[i] = __float2bfloat16_rn((float)v);
+    }
+}
+
+// Y[:, c] = X[:, c] * d (or / d), c < cols: the diagonal similarity of balancing
+// applied to (or removed from) a block of FP64 vectors, elementwise.
+__global__ void k_scale_rows(int n, int cols, const double *X, int64_t ldx, double *Y, int64_t ldy, const double *d,
+                             int divide) {
+    const int64_t total = (int64_t)n * cols;
+    for (int64_t t = blockIdx.x * (int64_t)kThreads + threadIdx.x; t < total; t += (int64_t)gridDim.x * kThreads) {
+        const int64_t c = t / n, r = t - c * n;
+        const double x = X[c * ldx + r], dr = __ldg(d + r);
+        Y[c * ldy + r] = divide ? x / dr : x * dr;
     }
 }
 
@@ -959,6 +1025,11 @@ void launch_norm2(int n, const double *x, double *part, unsigned *ticket, double
     if (g > num_sms() * 4) g = num_sms() * 4;
     if (g < 1) g = 1;
     k_norm2<<<g, kThreads, 0, st>>>(n, x, part, ticket, out);
+}
+
+void launch_scale_rows(int n, int cols, const double *X, int64_t ldx, double *Y, int64_t ldy, const double *d,
+                       bool divide, cudaStream_t st) {
+    k_scale_rows<<<num_sms() * 4, kThreads, 0, st>>>(n, cols, X, ldx, Y, ldy, d, divide ? 1 : 0);
 }
 
 void launch_slot_scale(int n, const double *src, const double *nrm2, double sgn, double *dst, cudaStream_t st) {

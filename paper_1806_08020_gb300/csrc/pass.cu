@@ -597,7 +597,8 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_step(SellView S, CsrView R,
 
 // One polynomial pass for every active instance: warp = 32 consecutive rows
 // of one instance; a block takes blockDim/32 such groups of one instance
-// (a work item) and blocks stride over the work items.
+// (a work item) and blocks stride over the work items.  Each instance's matrix
+// is SELL or DIA (its 32-row value blocks match the warp's rows).
 template <typename T>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassInst *pi, const BatchPassEntry *tab,
                                                                 const int2 *items, int nitems, const int *lo,
@@ -611,12 +612,14 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassI
         if (e.kind < 0 || jj < lo[itm.x] || jj >= hi[itm.x]) continue;
         const BatchPassInst &I = pi[itm.x];
         const int row = (itm.y + warp) * 32 + lane;
-        if (row >= I.A.n) continue;
+        if (row >= (I.dia ? I.D.n : I.A.n)) continue;
         const T *bufs[5] = {(const T *)I.V + (size_t)jj * I.ldv, (const T *)I.W, (const T *)I.P0, (const T *)I.P1,
                             (const T *)I.T};
         const T *x = bufs[e.src];
         T *y = (T *)bufs[e.dst];
-        T u = I.A.off ? sell_row<T, T, T, true>(I.A, x, row) : sell_row<T, T, T, false>(I.A, x, row);
+        // DIA: the diagonal offsets are read through the cache (the instances differ)
+        T u = I.dia ? dia_row<T, T, T>(I.D, I.D.off, x, row)
+                    : (I.A.off ? sell_row<T, T, T, true>(I.A, x, row) : sell_row<T, T, T, false>(I.A, x, row));
         if (I.sigma != 0.0) u = fma(-(T)I.sigma, x[row], u);
         if (e.kind == 0)
             y[row] = u;

@@ -5,6 +5,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 // Record a failure message for pp_last_error() and return the status.
@@ -21,6 +22,11 @@ double pof_log10(const std::vector<cd> &roots, size_t j);
 int extra_copies(double lp);
 bool add_stability_roots(const std::vector<cd> &ordered, std::vector<cd> &out, int &added);
 std::vector<int> ritz_order(const std::vector<cd> &nu, double target);
+// log d of the diagonal similarity D^-1 A D that makes A symmetric (largest
+// entry 0); false with a reason when none exists or its range exceeds
+// e^max_log_range (balance.cpp).
+bool symmetrizing_scale(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals,
+                        std::vector<double> &logd, std::string &why, double max_log_range = 600.0);
 }  // namespace ppd
 
 #ifdef __CUDACC__
@@ -148,6 +154,9 @@ void launch_scale(Prec p, int n, void *x, const double *scal, cudaStream_t st);
 // out[0] = ||x||^2 (FP64 x on the device; part holds one double per block, at
 // most 4 blocks per SM; ticket is zero before and after).
 void launch_norm2(int n, const double *x, double *part, unsigned *ticket, double *out, cudaStream_t st);
+// Y[:, c] = X[:, c] * d (divide: / d) elementwise, c < cols (FP64; X may be Y).
+void launch_scale_rows(int n, int cols, const double *X, int64_t ldx, double *Y, int64_t ldy, const double *d,
+                       bool divide, cudaStream_t st);
 // dst = src * sgn / sqrt(nrm2[0] + nrm2[1]) (FP64 device vectors).
 void launch_slot_scale(int n, const double *src, const double *nrm2, double sgn, double *dst, cudaStream_t st);
 // dst = x / sqrt(nrm2[0]) stored in precision p.
@@ -180,6 +189,8 @@ struct BatchPassInst {
     const void *V;
     int64_t ldv;
     void *W, *P0, *P1, *T;
+    DiaView D;  // the instance's matrix in diagonal storage when dia != 0 (else A, SELL)
+    int dia;
 };
 // One pass of one instance: kind -1 none, 0 y = u, 1 y = x - a2 u, 2 y = aux - a1 x - a2 u.
 struct BatchPassEntry {

@@ -28,7 +28,7 @@ class pp_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("format", C.c_int), ("target", C.c_int), ("sigma", C.c_double),
                 ("add_roots", C.c_int), ("max_cycles", C.c_int), ("refine_steps", C.c_int),
                 ("sell_c", C.c_int), ("sell_sigma", C.c_int), ("sell_index", C.c_int), ("sell_loop", C.c_int),
-                ("stream", C.c_void_p), ("restart", C.c_int), ("dia_loop", C.c_int)]
+                ("stream", C.c_void_p), ("restart", C.c_int), ("balance", C.c_int), ("dia_loop", C.c_int)]
 
 
 class pp_stats(C.Structure):
@@ -59,6 +59,7 @@ _SIGS = {
     "pp_destroy": (None, [_P]),
     "pp_trim": (C.c_int, [_P]),
     "pp_matrix_info": (C.c_int, [_P, _D, _D]),
+    "pp_balance_info": (C.c_int, [_P, _I, _D]),
     "pp_debug_stall_sweeps": (C.c_int, [_P, C.c_int]),
     "pp_format_info": (C.c_int, [_P, _I, _I, _I, _I, _I, _I64]),
     "pp_launch_count": (C.c_int64, [_P]),
@@ -213,6 +214,13 @@ def pp_create(A, **opts) -> Context:
     _check(LIB.pp_create(C.byref(h), int(A.n), rp.ctypes.data_as(_I64), ci.ctypes.data_as(C.POINTER(C.c_int32)),
                          _dp(va), C.byref(o)))
     return Context(h.value, int(A.n), o.precision)
+
+
+def pp_balance_info(ctx: Context) -> tuple[bool, float]:
+    """(balanced, log of the scaling range) of a context (pp_opts.balance)."""
+    b, r = C.c_int(), C.c_double()
+    _check(LIB.pp_balance_info(ctx.handle, C.byref(b), C.byref(r)))
+    return bool(b.value), r.value
 
 
 def pp_matrix_info(ctx: Context) -> tuple[float, float]:

@@ -1,0 +1,137 @@
+"""Balancing (pp_opts.balance; not in the paper, an opt-in transformation):
+the method runs on S = D^-1 A D, the diagonal similarity that makes A
+symmetric, and returns A's eigenpairs with the residual test on A itself.
+
+For the convection-diffusion operators the eigenvalues then meet the closed
+form (condition numbers 1 instead of ~e^(beta/2)), and the GPU matches the
+oracle's balanced solve of the same inputs (`oracle.balance`, `eigs(scale=)`).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.ppa import make_operator
+from paper_1806_08020_gb300 import inputs
+from test_gpu_eigs import cpu_residuals
+
+pytestmark = pytest.mark.gpu
+
+
+def closed_form_2d(N, beta, count):
+    h = 1.0 / (N + 1)
+    c = np.cos(np.arange(1, N + 1) * np.pi / (N + 1))
+    lx = (2 - 2 * np.sqrt(1 - (beta * h / 2) ** 2) * c) / h**2
+    ly = (2 - 2 * c) / h**2
+    m = min(N, 40)
+    return np.sort((lx[:m, None] + ly[None, :m]).ravel())[:count]
+
+
+def symmetric_bound(A, lam, X):
+    """Per slot, ||S y - mu y|| / ||y|| with y = D^-1 x the returned vector in S's
+    coordinates (S = D^-1 A D symmetric): some eigenvalue lies within this of mu."""
+    dd, S = O.balance(A)
+    out = []
+    for mu, x in zip(lam, X.T):
+        y = x / dd
+        out.append(np.linalg.norm(S @ y - mu.real * y) / np.linalg.norm(y))
+    return np.array(out)
+
+
+def check_values(A, lam, X, want):
+    """Every value within 10x the symmetric residual bound of a closed-form eigenvalue."""
+    bnd = symmetric_bound(A, lam, X)
+    err = np.array([np.min(np.abs(want - mu.real)) for mu in lam])
+    assert np.all(err <= 10 * bnd + 1e-12 * np.abs(lam.real)), (err, bnd)
+    return err, bnd
+
+
+def gpu_balanced(Acsr, d, nev, m, k, seed, precision, balance=1, max_cycles=2000):
+    from paper_1806_08020_gb300 import pp
+    ctx = pp.pp_create(Acsr, precision=precision, balance=balance, max_cycles=max_cycles)
+    poly = pp.pp_build_poly(ctx, d, inputs.start_vector(Acsr.n, seed, 0))
+    return ctx, pp.pp_eigs(ctx, poly, nev, m, k, 1e-8, inputs.start_vector(Acsr.n, seed, 1))
+
+
+def oracle_balanced(Acsr, d, nev, m, k, seed):
+    A = O.to_scipy(Acsr)
+    dd, S = O.balance(A)
+    c = O.Counters()
+    op = O.Operator(S, O.gershgorin_shift(S), c)
+    P = O.build_poly(op, inputs.start_vector(Acsr.n, seed, 0), d, c)
+    R = O.eigs(A, make_operator(op, P, c), nev, m, k, 1e-8, inputs.start_vector(Acsr.n, seed, 1), c, target="SR",
+               scale=dd)
+    return A, R
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("N,beta", [(50, 20.0), (60, 110.0)])
+def test_balanced_matches_oracle_and_closed_form(N, beta, precision):
+    """n = 2,500 (kappa ~ 1e2 unbalanced) and n = 3,600 with beta h / 2 = 0.90
+    (kappa ~ 1e34 unbalanced): every eigenvalue, the GPU's and the oracle's
+    balanced solve's, within ten times the symmetric residual bound
+    ||S y - mu y|| / ||y|| (y = D^-1 x) of the closed form, the two sets equal
+    within those bounds, and every residual on A recomputed on the CPU from the
+    returned vectors."""
+    from paper_1806_08020_gb300 import pp
+    prec = pp.PP_FP64 if precision == "fp64" else pp.PP_FP32
+    nev = 10 if N == 50 else 6
+    m, k = (30, 15) if N == 50 else (30, 11)
+    Acsr = inputs.convection_diffusion_2d(N, beta)
+    ctx, res = gpu_balanced(Acsr, 10, nev, m, k, 20181806, prec)
+    balanced, rng = pp.pp_balance_info(ctx)
+    h = 1.0 / (N + 1)
+    assert balanced and rng == pytest.approx((N - 1) * 0.5 * np.log((1 + beta * h / 2) / (1 - beta * h / 2)),
+                                             rel=1e-10)
+    A, R = oracle_balanced(Acsr, 10, nev, m, k, 20181806)
+    assert res.status == pp.PP_OK and R.converged
+    assert res.lam.size == R.lam.size
+    assert np.all(res.lam.imag == 0)
+    want = closed_form_2d(N, beta, 4 * res.lam.size)
+    check_values(A, res.lam, res.X, want)
+    check_values(A, R.lam, R.X, want)
+    # same wanted set as the oracle: the sorted values agree within both bounds
+    bg, bo = symmetric_bound(A, res.lam, res.X), symmetric_bound(A, R.lam, R.X)
+    assert np.all(np.abs(np.sort(res.lam.real) - np.sort(R.lam.real)) <= 10 * (bg.max() + bo.max()) + 1e-12 * np.abs(R.lam.real).max())
+    assert np.all(res.resid <= 1e-8)
+    rc = cpu_residuals(A, res.lam, res.X)
+    assert np.all(rc <= 1.01e-8), rc
+    assert np.allclose(np.linalg.norm(res.X, axis=0), 1.0, rtol=1e-10)
+
+
+def test_balance_refused_and_optional():
+    """beta h / 2 > 1 (opposite-sign neighbours, a complex spectrum): balance = 1 is
+    refused with PP_EINVAL; balance = 2 runs on A as given."""
+    from paper_1806_08020_gb300 import pp
+    Acsr = inputs.convection_diffusion_2d(12, 60.0)
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_create(Acsr, balance=1)
+    assert e.value.status == pp.PP_EINVAL
+    ctx = pp.pp_create(Acsr, balance=2)
+    assert pp.pp_balance_info(ctx)[0] is False
+    with pytest.raises(pp.PPError):
+        pp.pp_create(Acsr, balance=3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_balanced_plain_large_full_size(precision):
+    """The n = 10^6 workload (N = 1000, beta = 100, d = 50, Arnoldi(50, 25), nev = 20)
+    balanced: the true eigenvalues (closed form, 2521.29 upward) within the
+    symmetric residual bound (S has condition numbers 1; near-degenerate pairs
+    (i, j), (j, i) split by ~0.04 let a converged vector mix them) instead of
+    the unbalanced solve's pseudospectral curve, every residual on A
+    <= 1e-8 ||A||_1 recomputed on the CPU.  The oracle's balanced solve of these
+    inputs takes 9 cycles (~5 minutes on host cores), so it is not rerun here."""
+    from paper_1806_08020_gb300 import pp
+    cfg = inputs.plain_large()
+    prec = pp.PP_FP64 if precision == "fp64" else pp.PP_FP32
+    ctx, res = gpu_balanced(cfg["A"], cfg["d"], cfg["nev"], cfg["m"], cfg["k"], cfg["seed"], prec, max_cycles=40)
+    print("balanced n = 1e6", precision, {k: res.stats[k] for k in ("cycles", "fp64_cycles", "t_total", "max_resid")})
+    assert res.status == pp.PP_OK
+    want = closed_form_2d(1000, 100.0, 4 * res.lam.size)
+    assert want[0] == pytest.approx(2521.29, abs=0.01)
+    assert np.all(res.lam.imag == 0)
+    A = O.to_scipy(cfg["A"])
+    assert np.all(cpu_residuals(A, res.lam, res.X) <= 1.01e-8)
+    err, bnd = check_values(A, res.lam, res.X, want)
+    print("max relative distance to the closed form", np.max(err / res.lam.real), "bound", bnd.max())
+    assert np.min(res.lam.real) == pytest.approx(want[0], rel=1e-8)
