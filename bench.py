@@ -291,12 +291,16 @@ def run_ours(args, ws, rank, local):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp64_derived = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
     fp64_peak, dgemm = fp64_peaks(stream, dev, local)
+    # the larger of the two measured FP64 rates is the denominator (the smaller fraction)
+    peak_fp64 = max(fp64_peak["tflops"], dgemm or 0.0)
     traffic = _profile_traffic("sell_root_step_fp64_n1e6.txt")
     # the FP64 pipe is the most utilised unit of this kernel (ncu: FP64 pipe ~73 %, DRAM ~45 % cold)
-    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(fp64_peak["tflops"], 4),
-                "unit": "TFLOP/s", "frac": round(achieved_tflops / fp64_peak["tflops"], 4), "traffic": traffic,
-                "peak_source": "measured: FP64 FMA-throughput kernel (pp_measure_fp64_rate), clocks " +
-                               json.dumps(fp64_peak["clocks"]),
+    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(peak_fp64, 4),
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / peak_fp64, 4), "traffic": traffic,
+                "peak_source": ("measured: the larger of cuBLAS DGEMM 4096^3 (%.4f) and the FP64 FMA-throughput "
+                                "kernel pp_measure_fp64_rate (%.4f); clocks during the kernel %s"
+                                % (dgemm or 0.0, fp64_peak["tflops"], json.dumps(fp64_peak["clocks"]))),
+                "fma_kernel_tflops": round(fp64_peak["tflops"], 4),
                 "peak_derived": round(fp64_derived, 4),
                 "peak_derived_source": "152 SMs x 2 FP64 FMA/clk x 2 flops x %.0f MHz" % sm_mhz,
                 "dgemm_tflops": dgemm,
@@ -343,6 +347,7 @@ def run_ours(args, ws, rank, local):
     legs = {}
     if not args.no_legs:
         t_leg = time.perf_counter()
+        legs["balanced"] = leg_balanced(local, rank)
         legs["precision_3d"] = leg_precision3d(local, rank)
         legs["batch"] = leg_batch(local, rank)
         legs["serve_sample"] = leg_serve(local, rank, args.serve_sample)
@@ -687,6 +692,60 @@ def _match_errors(lam_a: np.ndarray, lam_b: np.ndarray) -> list[float]:
     return out
 
 
+def _closed_form_2d_smallest(N: int, beta: float, count: int) -> np.ndarray:
+    """Smallest eigenvalues of the 5-point 2-D CD operator in closed form (Kronecker sum)."""
+    h = 1.0 / (N + 1)
+    c = np.cos(np.arange(1, N + 1) * np.pi / (N + 1))
+    lx = (2 - 2 * np.sqrt(1 - (beta * h / 2) ** 2) * c) / h**2
+    ly = (2 - 2 * c) / h**2
+    m = min(N, 40)
+    return np.sort((lx[:m, None] + ly[None, :m]).ravel())[:count]
+
+
+def leg_balanced(local: int, rank: int, steps: int = 2) -> dict:
+    """The n = 1e6 workload with balancing (pp_opts.balance = 1; not in the paper): the
+    method on S = D^-1 A D (symmetric), residuals on A, in FP64 and in mixed precision;
+    per-eigenpair distance to the closed-form eigenvalues (2521.29 upward), which the
+    unbalanced solve misses by far (eigenvalue condition numbers ~1e17)."""
+    import torch
+
+    from paper_1806_08020_gb300 import pp
+
+    cfg = inputs.plain_large()
+    A = cfg["A"]
+    seed = rank_seed(cfg["seed"], rank)
+    b = torch.from_numpy(inputs.start_vector(A.n, seed, 0)).to(f"cuda:{local}")
+    v0 = torch.from_numpy(inputs.start_vector(A.n, seed, 1)).to(f"cuda:{local}")
+    stream = torch.cuda.Stream()
+    want = _closed_form_2d_smallest(1000, 100.0, 4 * cfg["nev"])
+    out = {"workload": cfg["name"] + " balanced (S = D^-1 A D)"}
+    for name, prec in (("fp64", pp.PP_FP64), ("mixed_fp32", pp.PP_FP32)):
+        ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, balance=1, max_cycles=100)
+
+        def solve():
+            poly = pp.pp_build_poly(ctx, cfg["d"], b)
+            return pp.pp_eigs(ctx, poly, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=False)
+        solve()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pairs = 0
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                res = solve()
+                pairs += count_pairs(res, cfg["nev"], cfg["rtol"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        err = [float("%.3g" % (np.min(np.abs(want - z.real)) / z.real)) for z in res.lam]
+        out[name] = {"value": round(pairs / t, 3), "unit": UNIT, "ms_per_step": round(t / steps * 1e3, 1),
+                     "steps": steps, "cycles": int(res.stats["cycles"]), "fp64_cycles": int(res.stats["fp64_cycles"]),
+                     "max_resid": float(np.max(res.resid)), "lam_min": float(np.min(res.lam.real)),
+                     "rel_err_vs_closed_form_per_eigenpair": err, "clocks": clk.summary()}
+        ctx.close()
+    return out
+
+
 def _double_apply_bytes(n: int, stored: int, vbytes: int, inner, outer) -> tuple[int, int]:
     """Algorithmic bytes and passes of one pi_2(tau(A)) x apply on DIA storage, following
     the library's schedule: every pass reads the stored values (zeros included) and x;
@@ -730,7 +789,7 @@ def _double_apply_bytes(n: int, stored: int, vbytes: int, inner, outer) -> tuple
 
 
 def leg_precision3d(local: int, rank: int, fmt_name: str = "auto", steps: int = 2, warmup: int = 1,
-                    sell_loop: int = 0, sell_c: int = 0) -> dict:
+                    sell_loop: int = 0, sell_c: int = 0, dia_loop: int = 0) -> dict:
     """n = 160^3 3-D CD (beta = 50), double polynomial 10 x 20 (Section 8), Arnoldi(40, 21),
     nev 16: mixed precision (FP32 apply and basis, FP64 test and refinement on A) against
     the FP64 method and the BF16-basis variant; per-eigenpair errors against FP64 and the
@@ -751,7 +810,7 @@ def leg_precision3d(local: int, rank: int, fmt_name: str = "auto", steps: int = 
     for name, prec, st, wu in (("mixed_fp32", pp.PP_FP32, steps, warmup), ("fp64", pp.PP_FP64, 1, 1),
                                ("mixed_bf16_basis", pp.PP_FP32_BF16, 1, 1)):
         ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=prec, max_cycles=60, sell_loop=sell_loop,
-                           sell_c=sell_c, format=fmt)
+                           sell_c=sell_c, format=fmt, dia_loop=dia_loop)
         poly = None
 
         def solve():
@@ -832,7 +891,7 @@ def _closed_form_3d_smallest(N: int, beta: float, count: int):
 def run_precision3d(args, ws, rank, local):
     """The 3-D precision workload on its own line."""
     leg = leg_precision3d(local, rank, args.format, max(1, args.steps), max(1, args.warmup), args.sell_loop,
-                          args.sell_c)
+                          args.sell_c, args.dia_loop)
     m = leg["mixed_fp32"]
     return {"metric": "eigenpairs/s at residual 1e-8, mixed precision vs FP64 (n=160^3 3-D CD, double polynomial)",
             "value": m["value"], "unit": UNIT, "n_gpus": ws, "steps": m["steps"], "warmup": max(1, args.warmup),
@@ -840,6 +899,97 @@ def run_precision3d(args, ws, rank, local):
             "dtype": "f32 apply/basis, f64 refine", "data": "synthetic (seeded generator)",
             "config": {"workload": leg["workload"]}, "precision_3d": leg, "roofline": leg["apply_roofline"],
             "gpu_launches": m["launches"], "clocks": m["clocks"]}
+
+
+def run_apply3d(args, ws, rank, local):
+    """The fused pi_2(tau(A)) v apply alone on the n = 160^3 3-D workload (FP32 values and
+    vectors in the format --format/--dia-loop fix, else the tuner's): the double polynomial
+    10 x 20 built once, then --steps applies timed with CUDA events on the context's stream
+    after --warmup; value = algorithmic GB/s (the pass schedule's bytes, as in the default
+    line's precision_3d.apply_roofline).  The ncu captures of the DIA passes use this."""
+    import torch
+
+    from paper_1806_08020_gb300 import pp
+
+    torch.cuda.set_device(local)
+    cfg = inputs.precision_3d()
+    A = cfg["A"]
+    stream = torch.cuda.Stream()
+    fmt = {"auto": pp.PP_FMT_AUTO, "sell": pp.PP_FMT_SELL, "dia": pp.PP_FMT_DIA, "csr": pp.PP_FMT_CSR}[args.format]
+    ctx = pp.pp_create(A, stream=stream.cuda_stream, precision=pp.PP_FP32, format=fmt, dia_loop=args.dia_loop,
+                       sell_loop=args.sell_loop, sell_c=args.sell_c)
+    poly = pp.pp_build_poly2(ctx, cfg["d1"], cfg["d2"], inputs.start_vector(A.n, rank_seed(cfg["seed"], rank), 0))
+    x = torch.from_numpy(inputs.start_vector(A.n, cfg["seed"], 1).astype(np.float32)).to(f"cuda:{local}")
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    for _ in range(max(1, args.warmup)):
+        pp.pp_apply(poly, x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            pp.pp_apply(poly, x.data_ptr(), y.data_ptr())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / args.steps
+    f = pp.pp_format_info(ctx)
+    nbytes, passes = _double_apply_bytes(A.n, f["stored"], 4, pp.pp_poly_inner_roots(poly), pp.pp_poly_roots(poly))
+    hbm = _peaks().get("hbm_gbs") or 6800.0
+    return {"metric": "pi(A)v HBM GB/s, fused double-polynomial apply (n=160^3 3-D CD, FP32)",
+            "value": round(nbytes / t / 1e9, 1), "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
+            "config": {"workload": cfg["name"] + " apply", "format": _format_name(f), "passes_per_apply": passes,
+                       "bytes_per_apply": int(nbytes), "avg_pass_us": round(t / passes * 1e6, 2)},
+            "roofline": {"bound": "hbm", "achieved": round(nbytes / t / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(nbytes / t / 1e9 / hbm, 4)},
+            "gpu_launches": passes * args.steps, "clocks": clk.summary()}
+
+
+def run_cgs2(args, ws, rank, local):
+    """One CGS2 step (pp_orthogonalize: three sweeps and the scaling) at n = 1e6 against
+    j = 22 and j = 50 orthonormal columns, in the context precision --cgs-precision;
+    --steps steps timed per j (host-synchronised calls: the step returns the H column).
+    The ncu captures of the sweeps use this."""
+    import torch
+
+    from paper_1806_08020_gb300 import pp
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 1000000
+    prec = pp.PP_FP32 if args.cgs_precision == "fp32" else pp.PP_FP64
+    tdt = torch.float32 if prec == pp.PP_FP32 else torch.float64
+    ctx = pp.pp_create(inputs.diagonal(np.ones(n)), precision=prec)
+    ldv = (n + 31) // 32 * 32
+    out = {}
+    for j in (22, 50):
+        q, _ = np.linalg.qr(np.random.default_rng(j).standard_normal((n, j)))
+        V = torch.zeros((j, ldv), dtype=tdt, device=dev)
+        V[:, :n] = torch.from_numpy(q.T.copy()).to(dev, tdt)
+        w0 = torch.from_numpy(inputs.start_vector(n, j, 0)).to(dev, tdt)
+        w, v = w0.clone(), torch.empty_like(w0)
+        torch.cuda.synchronize()
+        for _ in range(max(1, args.warmup)):
+            w.copy_(w0)
+            pp.pp_orthogonalize(ctx, V.data_ptr(), ldv, j, w.data_ptr(), v.data_ptr())
+        t = 0.0
+        for _ in range(args.steps):
+            w.copy_(w0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pp.pp_orthogonalize(ctx, V.data_ptr(), ldv, j, w.data_ptr(), v.data_ptr())
+            t += time.perf_counter() - t0
+        esz = 4 if prec == pp.PP_FP32 else 8
+        nbytes = (3 * j + 7) * n * esz  # sweeps: mode 0 reads V and w (j+1), 1 and 2 also write (j+2 each); scaling 2
+        out[f"j{j}"] = {"ms_per_step": round(t / args.steps * 1e3, 4), "bytes_per_step": nbytes,
+                        "gbs": round(nbytes / (t / args.steps) / 1e9, 1)}
+    return {"metric": "CGS2 step GB/s (pp_orthogonalize, n=1e6)", "value": out["j50"]["gbs"], "unit": "GB/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["j50"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.cgs_precision,
+            "data": "synthetic (seeded generator)", "config": {"workload": "cgs2 n=1e6 j=22,50", **out},
+            "gpu_launches": 4 * 2 * args.steps}
 
 
 def run_damping(args, ws, rank, local):
@@ -960,7 +1110,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="plain_large",
-                    choices=["plain_large", "batch", "serve", "precision_3d", "damping", "harmonic"])
+                    choices=["plain_large", "batch", "serve", "precision_3d", "damping", "harmonic", "apply3d",
+                             "cgs2"])
+    ap.add_argument("--dia-loop", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="DIA row loop (pp_opts.dia_loop): 0 tuner, 1 one row, 2 four rows, 3 two rows per thread")
+    ap.add_argument("--cgs-precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--serve-max-cycles", type=int, default=300)
@@ -987,6 +1141,10 @@ def main():
         out = run_precision3d(args, ws, rank, local)
     elif args.workload == "damping":
         out = run_damping(args, ws, rank, local)
+    elif args.workload == "apply3d":
+        out = run_apply3d(args, ws, rank, local)
+    elif args.workload == "cgs2":
+        out = run_cgs2(args, ws, rank, local)
     elif args.workload == "harmonic":
         out = run_harmonic(args, ws, rank, local)
     else:
