@@ -138,10 +138,10 @@ std::vector<ppk::BatchPassEntry> pass_schedule(const pp_poly *p) {
         bool last = i + 1 == st.size();
         int dst = last ? 1 : (cur == 2 ? 3 : 2);
         if (!st[i].pair) {
-            out.push_back({1, cur, dst, 0, 0.0, st[i].c});
+            out.push_back({1, cur, dst, 0, 0.0, st[i].c, 0.f, (float)st[i].c});
         } else {
-            out.push_back({0, cur, 4, 0, 0.0, 0.0});
-            out.push_back({2, 4, dst, cur, st[i].c1, -st[i].c2});
+            out.push_back({0, cur, 4, 0, 0.0, 0.0, 0.f, 0.f});
+            out.push_back({2, 4, dst, cur, st[i].c1, -st[i].c2, (float)st[i].c1, (float)-st[i].c2});
         }
         cur = dst;
     }
@@ -350,8 +350,8 @@ class Engine {
             if (c->A.prec != pr || (c->A.fmt != 2 && c->A.fmt != 3))
                 return pp_fail(PP_EINVAL, "engine: mixed precisions or a matrix neither SELL nor DIA");
             const auto &A = c->A.sell;
-            pinst[i] = {A, c->sigma, r->V, c->ldv(), c->vec[6], c->vec[0], c->vec[1], c->vec[2], c->A.dia,
-                        c->A.fmt == 3 ? 1 : 0};
+            pinst[i] = {A, c->sigma, (float)c->sigma, r->V, c->ldv(), c->vec[6], c->vec[0], c->vec[1], c->vec[2],
+                        c->A.dia, c->A.fmt == 3 ? 1 : 0};
             r->nblk = ppk::cgs_batch_blocks((int)c->n);
             r->blk0 = blocks;
             blocks += r->nblk;
@@ -359,7 +359,7 @@ class Engine {
                         c->d_small + 513, c->d_small + 512, c->d_part, c->d_ticket, r->nblk, r->blk0};
             for (int t = 0; t < Pmax; ++t)
                 tab[(size_t)t * count + i] =
-                    t < (int)r->passes.size() ? r->passes[t] : ppk::BatchPassEntry{-1, 0, 0, 0, 0, 0};
+                    t < (int)r->passes.size() ? r->passes[t] : ppk::BatchPassEntry{-1, 0, 0, 0, 0, 0, 0.f, 0.f};
         }
         CKS(d_pinst.ensure(count));
         CKS(d_cinst.ensure(count));
@@ -402,7 +402,7 @@ class Engine {
     // Re-run when the set's total size changes by more than 2x.
     pp_status tune_pass() {
         const int count = (int)act.size();
-        std::vector<ppk::BatchPassEntry> tab(count, ppk::BatchPassEntry{0, 0, 1, 0, 0.0, 0.0});
+        std::vector<ppk::BatchPassEntry> tab(count, ppk::BatchPassEntry{0, 0, 1, 0, 0.0, 0.0, 0.f, 0.f});
         std::vector<int> lo(count, 0), hi(count, 1);
         CKS(d_tune_tab.ensure(count));
         CK(cudaMemcpyAsync(d_tune_tab.p, tab.data(), sizeof(tab[0]) * count, cudaMemcpyHostToDevice, st));
@@ -419,7 +419,7 @@ class Engine {
                 cudaEventDestroy(e1);
                 return s;
             }
-            for (int gps : {4, 8, 16}) {
+            for (int gps : {4, 8, 16, 32}) {
                 double t = INFINITY;
                 for (int it = 0; it < 7; ++it) {
                     cudaEventRecord(e0, st);
@@ -432,6 +432,9 @@ class Engine {
                     if (it >= 2) t = std::min(t, (double)ms);
                 }
                 launches += 7;
+                if (trace_on())
+                    std::fprintf(stderr, "[pp] batch pass tuner: %d instances, %d threads/block, %d blocks/SM: %.1f us\n",
+                                 count, 32 * g, gps, t * 1e3);
                 if (t < best) {
                     best = t;
                     groups = g;
@@ -523,11 +526,15 @@ class Engine {
             return PP_OK;
         }
         const bool last = r->S.cycles >= max_cycles;
-        if (c->A.prec != ppk::F64 && r->sw.should_refine(r->R, last)) {
+        const bool refine_now = c->A.prec != ppk::F64 && r->sw.should_refine(r->R, last);
+        if (c->A.prec != ppk::F64 && (refine_now || r->sw.stall >= 1)) {
             // Far from rtol (more than ten times it) the FP64 refinement rarely
             // finishes the job, and it runs outside the batched launches: such a
             // request joins the batched FP64 engine at once, from its FP32 Ritz
-            // vectors.  Within ten times rtol the refinement is tried first.
+            // vectors, as soon as its FP32 residuals stop halving (on the
+            // batched workloads the FP32 floor is reached within a cycle or two
+            // and further FP32 cycles only delay the FP64 ones).  Within ten
+            // times rtol the refinement is tried first.
             const double mx = *std::max_element(r->R.res.begin(), r->R.res.end());
             if (mx > 10 * r->rtol && c->twin && !last) {
                 trace_cycle("req", r, r->S.cycles, 32, r->R, "to fp64");
@@ -536,6 +543,8 @@ class Engine {
                 r->done = true;
                 return PP_OK;
             }
+        }
+        if (refine_now) {
             CKS(shared_refinement_basis(r));
             s = r->D->refine(r->poly, r->cy.sl, r->nev, r->R, r->rtol, refine_steps, 3, r->S, &r->cy, r->V, c->A.prec,
                              r->m);

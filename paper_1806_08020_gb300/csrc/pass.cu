@@ -17,6 +17,16 @@ namespace ppk {
 
 namespace {
 
+// A coefficient in the accumulation type: the FP32 copy for FP32 kernels (set
+// on the host), the double itself for FP64 ones.
+template <typename Acc>
+__device__ __forceinline__ Acc cf(double d, float f) {
+    if constexpr (sizeof(Acc) == 4)
+        return f;
+    else
+        return (Acc)d;
+}
+
 // ---------------------------------------------------------------------------
 // Fused root step
 // ---------------------------------------------------------------------------
@@ -24,12 +34,12 @@ template <typename T, typename Acc>
 __device__ __forceinline__ void step_epilogue(int row, Acc u, const StepArgs &s) {
     const T *x = (const T *)s.x;
     Acc xi = (Acc)x[row];
-    if (s.sigma != 0.0) u = u - (Acc)s.sigma * xi;
+    if (s.has_sigma) u = u - cf<Acc>(s.sigma, s.fsigma) * xi;
     if (s.plain) {
         ((T *)s.y)[row] = (T)u;
         return;
     }
-    Acc delta = (Acc)s.a1 * xi + (Acc)s.a2 * u;
+    Acc delta = cf<Acc>(s.a1, s.fa1) * xi + cf<Acc>(s.a2, s.fa2) * u;
     if (s.y) {
         Acc base = s.aux ? (Acc)((const T *)s.aux)[row] : xi;
         ((T *)s.y)[row] = (T)(base - delta);
@@ -39,8 +49,8 @@ __device__ __forceinline__ void step_epilogue(int row, Acc u, const StepArgs &s)
         Acc rv = s.r_init ? delta : (Acc)r[row] + delta;
         if (s.r_write) r[row] = (T)rv;
         if (s.oy) {
-            Acc od = (Acc)s.b2 * rv;
-            if (s.ox) od += (Acc)s.b1 * (Acc)((const T *)s.ox)[row];
+            Acc od = cf<Acc>(s.b2, s.fb2) * rv;
+            if (s.ox) od += cf<Acc>(s.b1, s.fb1) * (Acc)((const T *)s.ox)[row];
             ((T *)s.oy)[row] = (T)((Acc)((const T *)s.obase)[row] - od);
         }
     }
@@ -228,14 +238,14 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_dia(DiaView D, StepArg
     const T *x = (const T *)s.x;
     T *y = (T *)s.y;
     Acc u = dia_row<T, V, Acc>(D, off_s, x, row);
-    if (SIGMA) u = fma(-(Acc)s.sigma, (Acc)x[row], u);
+    if (SIGMA) u = fma(-cf<Acc>(s.sigma, s.fsigma), (Acc)x[row], u);
     if (KIND == 0) {
         y[row] = (T)u;
     } else if (KIND == 1) {
-        y[row] = (T)fma(-(Acc)s.a2, u, (Acc)x[row]);
+        y[row] = (T)fma(-cf<Acc>(s.a2, s.fa2), u, (Acc)x[row]);
     } else {
-        Acc v = fma(-(Acc)s.a1, (Acc)x[row], (Acc)((const T *)s.aux)[row]);
-        y[row] = (T)fma(-(Acc)s.a2, u, v);
+        Acc v = fma(-cf<Acc>(s.a1, s.fa1), (Acc)x[row], (Acc)((const T *)s.aux)[row]);
+        y[row] = (T)fma(-cf<Acc>(s.a2, s.fa2), u, v);
     }
 }
 
@@ -324,9 +334,9 @@ template <int R>
 __device__ __forceinline__ void step_epilogue_rows(int r0, float (&u)[R], const StepArgs &s) {
     float xi[R];
     VecR<R>::ld((const float *)s.x + r0, xi);
-    if (s.sigma != 0.0) {
+    if (s.has_sigma) {
 #pragma unroll
-        for (int q = 0; q < R; ++q) u[q] = u[q] - (float)s.sigma * xi[q];
+        for (int q = 0; q < R; ++q) u[q] = u[q] - s.fsigma * xi[q];
     }
     if (s.plain) {
         VecR<R>::st((float *)s.y + r0, u);
@@ -334,7 +344,7 @@ __device__ __forceinline__ void step_epilogue_rows(int r0, float (&u)[R], const 
     }
     float delta[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) delta[q] = (float)s.a1 * xi[q] + (float)s.a2 * u[q];
+    for (int q = 0; q < R; ++q) delta[q] = s.fa1 * xi[q] + s.fa2 * u[q];
     if (s.y) {
         float base[R];
         if (s.aux) {
@@ -362,12 +372,12 @@ __device__ __forceinline__ void step_epilogue_rows(int r0, float (&u)[R], const 
             float ob[R], od[R];
             VecR<R>::ld((const float *)s.obase + r0, ob);
 #pragma unroll
-            for (int q = 0; q < R; ++q) od[q] = (float)s.b2 * rv[q];
+            for (int q = 0; q < R; ++q) od[q] = s.fb2 * rv[q];
             if (s.ox) {
                 float ox[R];
                 VecR<R>::ld((const float *)s.ox + r0, ox);
 #pragma unroll
-                for (int q = 0; q < R; ++q) od[q] += (float)s.b1 * ox[q];
+                for (int q = 0; q < R; ++q) od[q] += s.fb1 * ox[q];
             }
 #pragma unroll
             for (int q = 0; q < R; ++q) ob[q] = ob[q] - od[q];
@@ -395,14 +405,14 @@ __global__ void __launch_bounds__(256) k_dia_rows(DiaView D, StepArgs s) {
             if (GENERAL) {
                 step_epilogue<float, float>(row, u, s);
             } else {
-                if (SIGMA) u = fmaf(-(float)s.sigma, x[row], u);
+                if (SIGMA) u = fmaf(-s.fsigma, x[row], u);
                 float *y = (float *)s.y;
                 if (KIND == 0)
                     y[row] = u;
                 else if (KIND == 1)
-                    y[row] = fmaf(-(float)s.a2, u, x[row]);
+                    y[row] = fmaf(-s.fa2, u, x[row]);
                 else
-                    y[row] = fmaf(-(float)s.a2, u, fmaf(-(float)s.a1, x[row], ((const float *)s.aux)[row]));
+                    y[row] = fmaf(-s.fa2, u, fmaf(-s.fa1, x[row], ((const float *)s.aux)[row]));
             }
         }
         return;
@@ -417,19 +427,19 @@ __global__ void __launch_bounds__(256) k_dia_rows(DiaView D, StepArgs s) {
     VecR<R>::ld(x + r0, xi);
     if (SIGMA) {
 #pragma unroll
-        for (int q = 0; q < R; ++q) u[q] = fmaf(-(float)s.sigma, xi[q], u[q]);
+        for (int q = 0; q < R; ++q) u[q] = fmaf(-s.fsigma, xi[q], u[q]);
     }
     if (KIND == 0) {
         VecR<R>::st((float *)s.y + r0, u);
     } else if (KIND == 1) {
 #pragma unroll
-        for (int q = 0; q < R; ++q) out[q] = fmaf(-(float)s.a2, u[q], xi[q]);
+        for (int q = 0; q < R; ++q) out[q] = fmaf(-s.fa2, u[q], xi[q]);
         VecR<R>::st((float *)s.y + r0, out);
     } else {
         float ax[R];
         VecR<R>::ld((const float *)s.aux + r0, ax);
 #pragma unroll
-        for (int q = 0; q < R; ++q) out[q] = fmaf(-(float)s.a2, u[q], fmaf(-(float)s.a1, xi[q], ax[q]));
+        for (int q = 0; q < R; ++q) out[q] = fmaf(-s.fa2, u[q], fmaf(-s.fa1, xi[q], ax[q]));
         VecR<R>::st((float *)s.y + r0, out);
     }
 }
@@ -441,14 +451,14 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass(SellView S, CsrView R,
     const T *x = (const T *)s.x;
     T *y = (T *)s.y;
     auto finish = [&](int row, Acc u) {
-        if (SIGMA) u = fma(-(Acc)s.sigma, (Acc)x[row], u);
+        if (SIGMA) u = fma(-cf<Acc>(s.sigma, s.fsigma), (Acc)x[row], u);
         if (KIND == 0) {
             y[row] = (T)u;
         } else if (KIND == 1) {
-            y[row] = (T)fma(-(Acc)s.a2, u, (Acc)x[row]);
+            y[row] = (T)fma(-cf<Acc>(s.a2, s.fa2), u, (Acc)x[row]);
         } else {
-            Acc v = fma(-(Acc)s.a1, (Acc)x[row], (Acc)((const T *)s.aux)[row]);
-            y[row] = (T)fma(-(Acc)s.a2, u, v);
+            Acc v = fma(-cf<Acc>(s.a1, s.fa1), (Acc)x[row], (Acc)((const T *)s.aux)[row]);
+            y[row] = (T)fma(-cf<Acc>(s.a2, s.fa2), u, v);
         }
     };
     if constexpr (FMT >= 5) {  // two rows per thread
@@ -550,14 +560,14 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_tma(SellView A, StepAr
 #pragma unroll 4
                 for (int q = 0; q < len; ++q) u = fma(vs[32 * q], __ldg(x + (int)is[32 * q]), u);
             }
-            if (SIGMA) u = fma(-(T)s.sigma, x[row], u);
+            if (SIGMA) u = fma(-cf<T>(s.sigma, s.fsigma), x[row], u);
             if (KIND == 0) {
                 y[row] = u;
             } else if (KIND == 1) {
-                y[row] = fma(-(T)s.a2, u, x[row]);
+                y[row] = fma(-cf<T>(s.a2, s.fa2), u, x[row]);
             } else {
-                T v = fma(-(T)s.a1, x[row], ((const T *)s.aux)[row]);
-                y[row] = fma(-(T)s.a2, u, v);
+                T v = fma(-cf<T>(s.a1, s.fa1), x[row], ((const T *)s.aux)[row]);
+                y[row] = fma(-cf<T>(s.a2, s.fa2), u, v);
             }
         }
         __syncwarp();
@@ -620,13 +630,13 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassI
         // DIA: the diagonal offsets are read through the cache (the instances differ)
         T u = I.dia ? dia_row<T, T, T>(I.D, I.D.off, x, row)
                     : (I.A.off ? sell_row<T, T, T, true>(I.A, x, row) : sell_row<T, T, T, false>(I.A, x, row));
-        if (I.sigma != 0.0) u = fma(-(T)I.sigma, x[row], u);
+        if (cf<T>(I.sigma, I.fsigma) != (T)0) u = fma(-cf<T>(I.sigma, I.fsigma), x[row], u);
         if (e.kind == 0)
             y[row] = u;
         else if (e.kind == 1)
-            y[row] = fma(-(T)e.a2, u, x[row]);
+            y[row] = fma(-cf<T>(e.a2, e.fa2), u, x[row]);
         else
-            y[row] = fma(-(T)e.a2, u, fma(-(T)e.a1, x[row], bufs[e.aux][row]));
+            y[row] = fma(-cf<T>(e.a2, e.fa2), u, fma(-cf<T>(e.a1, e.fa1), x[row], bufs[e.aux][row]));
     }
 }
 
@@ -836,10 +846,17 @@ static void pass_format(const Matrix &A, const StepArgs &s, cudaStream_t st) {
 }
 
 void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st) {
+    StepArgs t = s;
+    t.fa1 = (float)s.a1;
+    t.fa2 = (float)s.a2;
+    t.fb1 = (float)s.b1;
+    t.fb2 = (float)s.b2;
+    t.fsigma = (float)s.sigma;
+    t.has_sigma = s.sigma != 0.0;
     if (A.prec == F64)
-        pass_format<double>(A, s, st);
+        pass_format<double>(A, t, st);
     else
-        pass_format<float>(A, s, st);
+        pass_format<float>(A, t, st);
 }
 
 void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *tab, const int2 *items, int nitems,

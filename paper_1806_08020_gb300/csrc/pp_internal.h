@@ -97,6 +97,10 @@ struct StepArgs {
     const void *ox = nullptr;
     void *oy = nullptr;
     double b1 = 0, b2 = 0;
+    // FP32 copies of the coefficients (set by launch_step): FP32 kernels read them
+    // instead of converting the doubles per thread (an FP64 instruction each)
+    float fa1 = 0, fa2 = 0, fb1 = 0, fb2 = 0, fsigma = 0;
+    int has_sigma = 0;
 };
 
 struct Matrix {
@@ -186,6 +190,7 @@ struct BatchCgsInst {
 struct BatchPassInst {
     SellView A;
     double sigma;
+    float fsigma;  // sigma rounded to FP32 (the FP32 kernel reads it)
     const void *V;
     int64_t ldv;
     void *W, *P0, *P1, *T;
@@ -196,6 +201,7 @@ struct BatchPassInst {
 struct BatchPassEntry {
     int kind, src, dst, aux;
     double a1, a2;
+    float fa1, fa2;  // a1, a2 rounded to FP32
 };
 int cgs_batch_blocks(int n);
 // Instance i takes part in step jj when lo[i] <= jj < hi[i] (device arrays).
