@@ -300,9 +300,11 @@ pp_status pp_apply_host(const pp_poly *p, const double *x, double *y);
  *      pair (lam, conj(lam)) the columns (Re x, Im x) of the unit vector x;
  *   resid: ||A x - lam x|| / ||A||_1 per slot;  *nout: slots written.
  * PP_FP32 contexts (mixed precision): the cycles run in FP32 storage; the
- * convergence test is always FP64 on A; at the FP32 floor the Ritz vectors are
- * refined in FP64 (block Krylov space of A, Rayleigh-Ritz); if that does not
- * reach rtol the solve continues in FP64 from the refined vectors.
+ * convergence test is always FP64 on A; within 50 rtol or at the FP32 floor
+ * the Ritz vectors are refined in FP64 (Rayleigh-Ritz of A on span{pi(A) Y},
+ * pi applied in FP64 by the context's FP64 copy; from the second round the
+ * cycle's next Ritz vectors join Y); if that does not reach rtol the solve
+ * continues in FP64 from the refined vectors.
  * Requires 1 <= nev < k < m, m < n.  Returns PP_ENOTCONV with the best pairs
  * when max_cycles is reached.
  */

@@ -9,15 +9,15 @@
 // (k - 1 when a conjugate pair would split) through V_k = V_m Q_k.
 //
 // Mixed precision (context precision PP_FP32): the Arnoldi cycles run with
-// FP32 matrix values, vectors and basis (the CGS2 sums accumulate in FP64).
-// When the FP64 residuals reach the FP32 floor the wanted Ritz vectors are
-// refined in FP64 on A: a block Krylov space span{Y, AY, ..., A^s Y} is built
-// with FP64 SpMVs and FP64 CGS2, A is projected onto it (Rayleigh-Ritz), and
-// the Ritz pairs nearest the current estimates replace them.  When that does
-// not reach rtol (an operator so non-normal that u_32 times the eigenvalue
-// condition number is near 1: the FP32 Krylov space does not hold the
-// eigenvectors), the solve continues with FP64 cycles on the context's FP64
-// twin, started from the sum of the refined Ritz vectors.
+// FP32 matrix values, vectors and basis.  Within 50 rtol, or when the FP64
+// residuals reach the FP32 floor, the wanted Ritz vectors are refined in FP64
+// on A (Driver::refine): pi(A) applied in FP64 by the context's FP64 twin to
+// them (and, from the second round, to the cycle's next Ritz vectors), FP64
+// CGS2, A projected onto that space (Rayleigh-Ritz), the refined pairs ranked
+// as the Arnoldi ranks its Ritz values.  When that does not reach rtol (the
+// FP32 Krylov space does not hold the eigenvectors well enough), the solve
+// continues with FP64 cycles on the twin, started from the sum of the refined
+// Ritz vectors.
 #include "driver.h"
 
 using namespace ppi;
