@@ -18,6 +18,9 @@
 // soon as it converges.
 #include "driver.h"
 
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <deque>
 #include <map>
 #include <memory>
@@ -312,6 +315,8 @@ class Engine {
     std::vector<ppk::BatchCgsInst> cinst;
     std::vector<cudaGraphExec_t> graphs;
     int Pmax = 0, blocks = 0, nitems = 0;
+    std::vector<int> item_end;    // work items through instance i (upload_items)
+    std::vector<int> pass_items;  // work items of the instances that take pass t (a prefix)
     int groups = 8, grid_per_sm = 8;  // batched-pass block shape (tuned)
     bool dirty = true;
     ppk::Prec pr = ppk::F32;
@@ -327,8 +332,8 @@ class Engine {
     void launch_step(int jj) {
         const int count = (int)act.size();
         for (int t = 0; t < Pmax; ++t)
-            ppk::launch_pass_batch(pr, d_pinst.p, d_tab.p + (size_t)t * count, d_items.p, nitems, d_lo.p, d_hi.p, jj,
-                                   groups, grid_per_sm, st);
+            ppk::launch_pass_batch(pr, d_pinst.p, d_tab.p + (size_t)t * count, d_items.p, pass_items[t], d_lo.p,
+                                   d_hi.p, jj, groups, grid_per_sm, st);
         for (int mode = 0; mode < 3; ++mode)
             ppk::launch_cgs_batch(pr, d_cinst.p, count, blocks, d_lo.p, d_hi.p, mode, jj, st);
         ppk::launch_scale_batch(pr, d_cinst.p, count, blocks, d_lo.p, d_hi.p, jj, st);
@@ -336,6 +341,10 @@ class Engine {
 
     pp_status build_tables() {
         free_graphs();
+        // most passes first: the instances that take pass t are then a prefix of
+        // the set, and so are their work items (the pass launches cover only those)
+        std::stable_sort(act.begin(), act.end(),
+                         [](const Req *a, const Req *b) { return a->passes.size() > b->passes.size(); });
         const int count = (int)act.size();
         pr = act[0]->c->A.prec;
         Pmax = 0;
@@ -376,17 +385,28 @@ class Engine {
             tuned_rows = rows;
         }
         CKS(upload_items(groups));
+        pass_items.assign(Pmax, 0);
+        for (int t = 0; t < Pmax; ++t) {
+            int L = 0;
+            while (L < count && (int)act[L]->passes.size() > t) ++L;
+            pass_items[t] = L > 0 ? item_end[L - 1] : 0;
+        }
         CK(cudaStreamSynchronize(st));
         dirty = false;
         return PP_OK;
     }
 
-    // Work items (instance, first 32-row group), `g` groups per block.
+    // Work items (instance, first 32-row group), `g` warps per block (a warp takes
+    // one 32-row group, two for a DIA instance).
     pp_status upload_items(int g) {
         std::vector<int2> items;
+        item_end.assign(act.size(), 0);
         for (int i = 0; i < (int)act.size(); ++i) {
             const int ngroups = (int)((act[i]->c->n + 31) / 32);
-            for (int g0 = 0; g0 < ngroups; g0 += g) items.push_back(make_int2(i, g0));
+            // a DIA instance's warps take two 32-row groups each (two rows per lane)
+            const int step = act[i]->c->A.fmt == 3 ? 2 * g : g;
+            for (int g0 = 0; g0 < ngroups; g0 += step) items.push_back(make_int2(i, g0));
+            item_end[i] = (int)items.size();
         }
         nitems = (int)items.size();
         CKS(d_items.ensure(items.size()));
@@ -399,8 +419,19 @@ class Engine {
     // every instance fastest, timed with CUDA events on the engine's stream
     // (fastest of five launches after two warm-up ones).  The timed pass reads
     // v_1 and writes the operator output, which the first real step overwrites.
-    // Re-run when the set's total size changes by more than 2x.
+    // Re-run when the set's total size changes by more than 2x.  PP_BATCH_SHAPE
+    // = "g,b" fixes g warps per block and b blocks per SM instead (for
+    // profiling: under a profiler the timings mislead the tuner).
     pp_status tune_pass() {
+        if (const char *fix = std::getenv("PP_BATCH_SHAPE")) {
+            int g = 0, b = 0;
+            if (std::sscanf(fix, "%d,%d", &g, &b) == 2 && (g == 2 || g == 4 || g == 8 || g == 16) && b >= 1 &&
+                b <= 32) {
+                groups = g;
+                grid_per_sm = b;
+                return PP_OK;
+            }
+        }
         const int count = (int)act.size();
         std::vector<ppk::BatchPassEntry> tab(count, ppk::BatchPassEntry{0, 0, 1, 0, 0.0, 0.0, 0.f, 0.f});
         std::vector<int> lo(count, 0), hi(count, 1);

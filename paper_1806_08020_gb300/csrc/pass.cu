@@ -605,10 +605,136 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_step(SellView S, CsrView R,
     }
 }
 
-// One polynomial pass for every active instance: warp = 32 consecutive rows
-// of one instance; a block takes blockDim/32 such groups of one instance
-// (a work item) and blocks stride over the work items.  Each instance's matrix
-// is SELL or DIA (its 32-row value blocks match the warp's rows).
+// Two consecutive DIA rows r0, r0 + 1 (r0 even, both < n) of a batched
+// instance in type T: each diagonal's two values and, for an even offset, the
+// two x values are one 8- or 16-byte load; the offsets come through the cache.
+// Products in increasing diagonal order per row, as dia_row.
+template <typename T>
+struct Pair2;
+template <>
+struct Pair2<float> {
+    using V = float2;
+};
+template <>
+struct Pair2<double> {
+    using V = double2;
+};
+template <typename T>
+__device__ __forceinline__ void ld2(const T *p, T (&o)[2]) {
+    const typename Pair2<T>::V v = __ldg((const typename Pair2<T>::V *)p);
+    o[0] = v.x;
+    o[1] = v.y;
+}
+template <typename T>
+__device__ __forceinline__ void st2(T *p, T a, T b) {
+    typename Pair2<T>::V v;
+    v.x = a;
+    v.y = b;
+    *(typename Pair2<T>::V *)p = v;
+}
+
+template <typename T>
+__device__ __forceinline__ void dia_pair(const DiaView &D, const T *__restrict__ x, int r0, T (&u)[2]) {
+    const T *val = (const T *)D.val + (size_t)(r0 >> 5) * ((size_t)D.ndiag * 32) + (r0 & 31);
+    u[0] = u[1] = (T)0;
+    for (int d0 = 0; d0 < D.ndiag; d0 += 8) {
+        T a[8][2], xv[8][2];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int d = d0 + t;
+            a[t][0] = a[t][1] = xv[t][0] = xv[t][1] = (T)0;
+            if (d < D.ndiag) {
+                ld2<T>(val + d * 32, a[t]);
+                const int o = __ldg(D.off + d), c = r0 + o;
+                if ((o & 1) == 0 && c >= 0 && c + 1 < D.n) {
+                    ld2<T>(x + c, xv[t]);
+                } else {
+                    if (c >= 0 && c < D.n) xv[t][0] = __ldg(x + c);
+                    if (c + 1 >= 0 && c + 1 < D.n) xv[t][1] = __ldg(x + c + 1);
+                }
+            }
+        }
+        const int cnt = D.ndiag - d0 < 8 ? D.ndiag - d0 : 8;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (t < cnt) {
+                u[0] = fma(a[t][0], xv[t][0], u[0]);
+                u[1] = fma(a[t][1], xv[t][1], u[1]);
+            }
+    }
+}
+
+// Two consecutive DIA rows as dia_pair, for an instance with at most eight
+// diagonals whose offsets the caller holds in registers: every load of the
+// rows is issued at once (no offset load ahead of the x gathers).
+template <typename T>
+__device__ __forceinline__ void dia_pair8(const T *__restrict__ val, int n, int ndiag, const int (&off)[8],
+                                          const T *__restrict__ x, int r0, T (&u)[2]) {
+    T a[8][2], xv[8][2];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        a[t][0] = a[t][1] = xv[t][0] = xv[t][1] = (T)0;
+        if (t < ndiag) {
+            ld2<T>(val + t * 32, a[t]);
+            const int c = r0 + off[t];
+            if ((off[t] & 1) == 0 && c >= 0 && c + 1 < n) {
+                ld2<T>(x + c, xv[t]);
+            } else {
+                if (c >= 0 && c < n) xv[t][0] = __ldg(x + c);
+                if (c + 1 >= 0 && c + 1 < n) xv[t][1] = __ldg(x + c + 1);
+            }
+        }
+    }
+    u[0] = u[1] = (T)0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (t < ndiag) {
+            u[0] = fma(a[t][0], xv[t][0], u[0]);
+            u[1] = fma(a[t][1], xv[t][1], u[1]);
+        }
+}
+
+// The operands of one instance's pass at step jj, resolved once per run of
+// work items in that instance and then held in registers.
+template <typename T>
+struct BatchOperands {
+    const T *x, *aux;
+    T *y;
+    T a1, a2, sg;
+    int kind;  // -1: the instance takes no pass at this step
+};
+
+template <typename T>
+__device__ __forceinline__ T *batch_buf(const BatchPassInst &I, int k, int jj) {
+    switch (k) {
+        case 0: return (T *)I.V + (size_t)jj * I.ldv;
+        case 1: return (T *)I.W;
+        case 2: return (T *)I.P0;
+        case 3: return (T *)I.P1;
+        default: return (T *)I.T;
+    }
+}
+
+// y from u = (A - sigma I) x at one row (kind 0: u; 1: x - a2 u; 2: aux - a1 x - a2 u).
+template <typename T>
+__device__ __forceinline__ T batch_out(const BatchOperands<T> &o, T u, T xi, T ai) {
+    if (o.sg != (T)0) u = fma(-o.sg, xi, u);
+    if (o.kind == 0) return u;
+    if (o.kind == 1) return fma(-o.a2, u, xi);
+    return fma(-o.a2, u, fma(-o.a1, xi, ai));
+}
+
+// One polynomial pass for every active instance in one launch.  A work item
+// is g warps' rows of one instance: 32 consecutive rows per warp (SELL), or 64
+// with two consecutive rows per lane (DIA: the lane's two values of a diagonal
+// sit side by side in its 32-row block).  Blocks take chunks of kBatchChunk
+// consecutive work items, strided over the grid (so that the instances that
+// take no pass at a step spread over all blocks).  Consecutive items mostly
+// stay in one instance: its operands, and in FP32 for up to eight diagonals
+// its offsets, are loaded once and kept in registers, and the next item's
+// index is read while this one computes.
+constexpr int kBatchChunk = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassInst *pi, const BatchPassEntry *tab,
                                                                 const int2 *items, int nitems, const int *lo,
@@ -616,27 +742,76 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassI
     grid_trigger();
     grid_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const int2 itm = items[it];
-        const BatchPassEntry e = tab[itm.x];
-        if (e.kind < 0 || jj < lo[itm.x] || jj >= hi[itm.x]) continue;
-        const BatchPassInst &I = pi[itm.x];
-        const int row = (itm.y + warp) * 32 + lane;
-        if (row >= (I.dia ? I.D.n : I.A.n)) continue;
-        const T *bufs[5] = {(const T *)I.V + (size_t)jj * I.ldv, (const T *)I.W, (const T *)I.P0, (const T *)I.P1,
-                            (const T *)I.T};
-        const T *x = bufs[e.src];
-        T *y = (T *)bufs[e.dst];
-        // DIA: the diagonal offsets are read through the cache (the instances differ)
-        T u = I.dia ? dia_row<T, T, T>(I.D, I.D.off, x, row)
-                    : (I.A.off ? sell_row<T, T, T, true>(I.A, x, row) : sell_row<T, T, T, false>(I.A, x, row));
-        if (cf<T>(I.sigma, I.fsigma) != (T)0) u = fma(-cf<T>(I.sigma, I.fsigma), x[row], u);
-        if (e.kind == 0)
-            y[row] = u;
-        else if (e.kind == 1)
-            y[row] = fma(-cf<T>(e.a2, e.fa2), u, x[row]);
-        else
-            y[row] = fma(-cf<T>(e.a2, e.fa2), u, fma(-cf<T>(e.a1, e.fa1), x[row], bufs[e.aux][row]));
+    int cur = -1, dia = 0, n = 0, ndiag = 0;
+    const T *val = nullptr;
+    const int *offp = nullptr;
+    int off[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) off[t] = 0;
+    BatchOperands<T> o{};
+    for (int c0 = blockIdx.x * kBatchChunk; c0 < nitems; c0 += gridDim.x * kBatchChunk) {
+        const int c1 = min(nitems, c0 + kBatchChunk);
+        int2 nxt = items[c0];
+        for (int it = c0; it < c1; ++it) {
+            const int2 itm = nxt;
+            if (it + 1 < c1) nxt = items[it + 1];  // the next index is in flight during this item
+            if (itm.x != cur) {
+                cur = itm.x;
+                const BatchPassInst &I = pi[cur];
+                const BatchPassEntry e = tab[cur];
+                o.kind = (e.kind < 0 || jj < lo[cur] || jj >= hi[cur]) ? -1 : e.kind;
+                o.x = batch_buf<T>(I, e.src, jj);
+                o.y = batch_buf<T>(I, e.dst, jj);
+                o.aux = batch_buf<T>(I, e.aux, jj);
+                o.a1 = cf<T>(e.a1, e.fa1);
+                o.a2 = cf<T>(e.a2, e.fa2);
+                o.sg = cf<T>(I.sigma, I.fsigma);
+                dia = I.dia;
+                n = dia ? I.D.n : I.A.n;
+                ndiag = dia ? I.D.ndiag : 0;
+                val = (const T *)I.D.val;
+                offp = I.D.off;
+                if (sizeof(T) == 4 && dia && ndiag <= 8) {
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) off[t] = t < ndiag ? __ldg(offp + t) : 0;
+                }
+            }
+            if (o.kind >= 0) {
+                if (dia) {
+                    const int r0 = (itm.y + 2 * warp) * 32 + 2 * lane;
+                    if (r0 + 1 < n) {
+                        T u[2], xi[2], ax[2] = {(T)0, (T)0};
+                        if (sizeof(T) == 4 && ndiag <= 8) {
+                            dia_pair8<T>(val + (size_t)(r0 >> 5) * ((size_t)ndiag * 32) + (r0 & 31), n, ndiag, off, o.x,
+                                         r0, u);
+                        } else {
+                            const DiaView D{n, ndiag, 0, offp, val};
+                            if (sizeof(T) == 4) {
+                                dia_pair<T>(D, o.x, r0, u);
+                            } else {  // FP64: one row at a time keeps the registers of eight diagonals
+                                u[0] = dia_row<T, T, T>(D, offp, o.x, r0);
+                                u[1] = dia_row<T, T, T>(D, offp, o.x, r0 + 1);
+                            }
+                        }
+                        ld2<T>(o.x + r0, xi);
+                        if (o.kind == 2) ld2<T>(o.aux + r0, ax);
+                        st2<T>(o.y + r0, batch_out<T>(o, u[0], xi[0], ax[0]), batch_out<T>(o, u[1], xi[1], ax[1]));
+                    } else if (r0 < n) {  // the last row of an odd n
+                        const DiaView D{n, ndiag, 0, offp, val};
+                        const T u = dia_row<T, T, T>(D, offp, o.x, r0);
+                        o.y[r0] = batch_out<T>(o, u, o.x[r0], o.kind == 2 ? o.aux[r0] : (T)0);
+                    }
+                } else {
+                    const int row = (itm.y + warp) * 32 + lane;
+                    if (row < n) {
+                        const SellView &A = pi[cur].A;
+                        const T u =
+                            A.off ? sell_row<T, T, T, true>(A, o.x, row) : sell_row<T, T, T, false>(A, o.x, row);
+                        o.y[row] = batch_out<T>(o, u, o.x[row], o.kind == 2 ? o.aux[row] : (T)0);
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -862,7 +1037,8 @@ void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st) {
 void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *tab, const int2 *items, int nitems,
                        const int *lo, const int *hi, int jj, int groups, int grid_per_sm, cudaStream_t st) {
     int g = num_sms() * grid_per_sm;
-    if (nitems < g) g = nitems;
+    const int chunks = (nitems + kBatchChunk - 1) / kBatchChunk;
+    if (chunks < g) g = chunks;
     if (g < 1) g = 1;
     const int threads = 32 * groups;
     if (p == F64)
