@@ -21,7 +21,6 @@
 #include <string>
 #include <map>
 #include <mutex>
-#include <set>
 #include <vector>
 
 
@@ -600,6 +599,18 @@ pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_
 
 }  // extern "C"
 
+// 64-bit row pointers to 32-bit on the device (pp_create checks nnz < 2^31).
+static __global__ void k_rowptr32(int64_t count, const int64_t *src, int *dst) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = (int)src[i];
+}
+
+static cudaError_t launch_rowptr32(int64_t count, const int64_t *src, int *dst, cudaStream_t st) {
+    const int threads = 256;
+    k_rowptr32<<<(unsigned)((count + threads - 1) / threads), threads, 0, st>>>(count, src, dst);
+    return cudaGetLastError();
+}
+
 // Stored entries of SELL-C (C = 1 << cs): each slice padded to its longest row.
 static int64_t sell_padded(int64_t n, const int64_t *rowptr, int cs) {
     const int64_t C = (int64_t)1 << cs;
@@ -610,31 +621,6 @@ static int64_t sell_padded(int64_t n, const int64_t *rowptr, int cs) {
         tot += w * C;
     }
     return tot;
-}
-
-// The distinct diagonals col - row of a CSR matrix in increasing order, when the
-// columns of every row increase strictly and there are at most kDiaMax of them.
-static bool dia_offsets(int64_t n, const int64_t *rowptr, const int32_t *colind, std::vector<int> &off) {
-    std::set<int> seen;
-    std::vector<int> prev;  // the previous row's offsets: stencil rows repeat them
-    for (int64_t i = 0; i < n; ++i) {
-        const int64_t k0 = rowptr[i], len = rowptr[i + 1] - k0;
-        bool same = (int64_t)prev.size() == len;
-        for (int64_t t = 0; t < len; ++t) {
-            const int64_t k = k0 + t;
-            if (t > 0 && colind[k] <= colind[k - 1]) return false;
-            same = same && prev[t] == (int)(colind[k] - i);
-        }
-        if (same) continue;
-        prev.resize(len);
-        for (int64_t t = 0; t < len; ++t) {
-            prev[t] = (int)(colind[k0 + t] - i);
-            seen.insert(prev[t]);
-        }
-        if ((int)seen.size() > ppk::kDiaMax) return false;
-    }
-    off.assign(seen.begin(), seen.end());
-    return true;
 }
 
 // Most stored entries of SELL-32 in any g consecutive slices (a staged tile).
@@ -770,29 +756,15 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     int64_t nnz = rowptr[n];
     if (rowptr[0] != 0 || nnz < 0 || nnz >= (int64_t)1 << 31 || n >= (int64_t)1 << 31)
         return pp_fail(PP_EINVAL, "pp_create: rowptr must start at 0 and nnz, n < 2^31");
-    // one pass over the entries: validation, the column sums of ||A||_1, the
-    // Gershgorin bound of the shift, and whether 16-bit column offsets fit
-    // (row pointers first: with them monotone and ending at nnz, every row stays inside the arrays)
-    for (int64_t i = 0; i < n; ++i)
-        if (rowptr[i + 1] < rowptr[i]) return pp_fail(PP_EINVAL, "pp_create: rowptr not monotone at %lld", (long long)i);
-    std::vector<double> colsum(n, 0.0);
-    double gl = INFINITY;
-    bool fits16 = true;
-    for (int64_t i = 0; i < n; ++i) {
-        double diag = 0, off = 0;
-        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-            const int64_t col = colind[k];
-            const double v = vals[k];
-            if (col < 0 || col >= n || !std::isfinite(v)) return pp_fail(PP_EINVAL, "pp_create: bad entry %lld", (long long)k);
-            colsum[col] += std::fabs(v);
-            if (col == i)
-                diag += v;
-            else
-                off += std::fabs(v);
-            fits16 = fits16 && std::llabs((long long)(col - i)) <= 32767;
-        }
-        gl = std::min(gl, diag - off);
+    // validation, ||A||_1, the Gershgorin bound of the shift and whether 16-bit
+    // column offsets fit, in one parallel pass over the entries
+    ppd::CsrScan scan;
+    {
+        std::string why;
+        if (!ppd::scan_csr(n, rowptr, colind, vals, scan, why)) return pp_fail(PP_EINVAL, "pp_create: %s", why.c_str());
     }
+    double gl = scan.gl;
+    const bool fits16 = scan.fits16;
     // balancing (opts.balance): the operator's matrix becomes S = D^-1 A D, the
     // diagonal similarity that makes A symmetric; ||A||_1 and the residual test
     // stay on A, the shift is S's Gershgorin bound
@@ -833,7 +805,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     c->n = n;
     c->nnz = nnz;
     // ||A||_1 and the Gershgorin shift on the host (exact, deterministic)
-    c->norm1 = *std::max_element(colsum.begin(), colsum.end());
+    c->norm1 = scan.norm1;
     if (std::isnan(c->opts.sigma)) {
         if (c->opts.target == PP_TARGET_SR)
             c->sigma = (gl >= -1e-12 * c->norm1) ? 0.0 : std::min(0.0, gl);
@@ -864,13 +836,13 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     // device CSR (int32 row pointers, FP64 values)
     int *d_rowptr = nullptr, *d_col = nullptr;
     double *d_val = nullptr;
-    std::vector<int> rp32(n + 1);
-    for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rowptr[i];
+    int64_t *d_rp64 = nullptr;  // the row pointers as given, made 32-bit on the device
     if ((st = dmalloc(c, (void **)&d_rowptr, (n + 1) * 4)) < 0 || (st = dmalloc(c, (void **)&d_col, nnz * 4)) < 0 ||
-        (st = dmalloc(c, (void **)&d_val, nnz * 8)) < 0)
+        (st = dmalloc(c, (void **)&d_val, nnz * 8)) < 0 || (st = dmalloc(c, (void **)&d_rp64, (n + 1) * 8)) < 0)
         return fail(st);
     // stream-ordered uploads: the context's stream does not synchronise with the legacy stream
-    if (cudaMemcpyAsync(d_rowptr, rp32.data(), (n + 1) * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(d_rp64, rowptr, (n + 1) * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        launch_rowptr32(n + 1, d_rp64, d_rowptr, c->stream) != cudaSuccess ||
         cudaMemcpyAsync(d_col, colind, nnz * 4, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
         cudaMemcpyAsync(d_val, kvals, nnz * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return fail(pp_fail(PP_ECUDA, "pp_create: upload failed"));
@@ -1028,13 +1000,15 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     // DIA for stencil and banded matrices (no column indices): when asked for,
     // or in auto mode when it times faster than the SELL choice
     std::vector<int> doff;
-    const bool dia_fits = dia_offsets(n, rowptr, colind, doff) &&
+    const bool auto_tuned = c->opts.format == PP_FMT_AUTO && !c->opts.sell_c && !c->opts.sell_loop && M.fmt == 2;
+    // (a cached SELL decision needs no DIA analysis)
+    const bool dia_wanted = c->opts.format == PP_FMT_DIA || (auto_tuned && (!cached || choice.dia));
+    const bool dia_fits = dia_wanted && ppd::dia_offsets(n, rowptr, colind, ppk::kDiaMax, doff) &&
                           (int64_t)doff.size() * n <= (int64_t)(1.3 * (double)nnz) + 32 * 8;
     if (c->opts.format == PP_FMT_DIA && !dia_fits)
         return fail(pp_fail(PP_EINVAL, "pp_create: DIA needs sorted columns, at most %d diagonals and <= 30 %% padding",
                             ppk::kDiaMax));
-    const bool auto_tuned = c->opts.format == PP_FMT_AUTO && !c->opts.sell_c && !c->opts.sell_loop && M.fmt == 2;
-    if (dia_fits && (c->opts.format == PP_FMT_DIA || (auto_tuned && (!cached || choice.dia)))) {
+    if (dia_fits) {
         const int nd = (int)doff.size();
         const int64_t ld = c->ldv();
         int *d_off = nullptr;
@@ -1103,6 +1077,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     }
     if ((st = ensure_part(c, ppk::cgs_part_doubles(ppk::cgs_grid((int)n)))) < 0) return fail(st);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: setup kernels failed"));
+    dfree(c, d_rp64);
     if (c->bprec != ppk::F64 && make_twin) {
         // FP64 twin on the same stream: the mixed-precision solve continues in FP64
         // when the FP32 cycles cannot resolve the eigenvectors (u_32 kappa ~ 1)

@@ -27,6 +27,19 @@ std::vector<int> ritz_order(const std::vector<cd> &nu, double target);
 // e^max_log_range (balance.cpp).
 bool symmetrizing_scale(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals,
                         std::vector<double> &logd, std::string &why, double max_log_range = 600.0);
+// Host analysis of a CSR matrix (csr_scan.cpp, parallel over row ranges).
+struct CsrScan {
+    double norm1 = 0;         // largest column sum of |a_ij|
+    double gl = 0;            // min_i (a_ii - sum_{j != i} |a_ij|)
+    bool fits16 = true;       // every |j - i| <= 32767
+};
+// false with a reason for non-monotone row pointers or an entry with a column
+// outside [0, n) or a value that is not finite.
+bool scan_csr(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals, CsrScan &out,
+              std::string &why);
+// The distinct diagonals col - row in increasing order; false when the columns
+// of some row do not increase strictly or there are more than max_diags.
+bool dia_offsets(int64_t n, const int64_t *rowptr, const int32_t *colind, int max_diags, std::vector<int> &off);
 }  // namespace ppd
 
 #ifdef __CUDACC__
