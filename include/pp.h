@@ -179,6 +179,19 @@ pp_status pp_balance_info(const pp_ctx *ctx, int *balanced, double *log_range);
 pp_status pp_matrix_info(const pp_ctx *ctx, double *norm1, double *sigma);
 
 /*
+ * pp_csr_info — the host analysis pp_create runs on a CSR matrix, without a
+ * device: ||A||_1 (maximum absolute column sum; the residual bound of Section
+ * 4 is rtol ||A||_1) and the shift of the smallest-real-part target (Section 2,
+ * footnote 1: sigma = min(0, min_i (a_ii - sum_{j != i} |a_ij|)), 0 when that
+ * bound is above -1e-12 ||A||_1).  Arguments as pp_create (host arrays, read
+ * only); either output may be NULL.  PP_EINVAL for the inputs pp_create
+ * refuses (row pointers not starting at 0 or not monotone, a column outside
+ * [0, n), a value that is not finite, nnz or n >= 2^31).
+ */
+pp_status pp_csr_info(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals, double *norm1,
+                      double *sigma_sr);
+
+/*
  * pp_format_info — the device format of A chosen at pp_create: fmt
  * (PP_FMT_CSR, PP_FMT_SELL or PP_FMT_DIA), the SELL chunk height (0 otherwise),
  * the column index width in bits (16 or 32; 0 for DIA), the block size of the product kernels, the

@@ -599,6 +599,11 @@ pp_status pp_create(pp_ctx **out, int64_t n, const int64_t *rowptr, const int32_
 
 }  // extern "C"
 
+// The shift of the smallest-real-part target (Section 2, footnote 1): the
+// leftmost Gershgorin point gl when it is negative beyond rounding
+// (below -1e-12 ||A||_1), else 0.
+static double sr_shift(double gl, double norm1) { return (gl >= -1e-12 * norm1) ? 0.0 : std::min(0.0, gl); }
+
 // 64-bit row pointers to 32-bit on the device (pp_create checks nnz < 2^31).
 static __global__ void k_rowptr32(int64_t count, const int64_t *src, int *dst) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -808,7 +813,7 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     c->norm1 = scan.norm1;
     if (std::isnan(c->opts.sigma)) {
         if (c->opts.target == PP_TARGET_SR)
-            c->sigma = (gl >= -1e-12 * c->norm1) ? 0.0 : std::min(0.0, gl);
+            c->sigma = sr_shift(gl, c->norm1);
         else
             c->sigma = 0.0;
     } else {
@@ -1150,6 +1155,20 @@ pp_status pp_balance_info(const pp_ctx *c, int *balanced, double *log_range) {
         for (double d : c->h_bal) lo = std::min(lo, std::log(d));
         *log_range = -lo;
     }
+    return PP_OK;
+}
+
+pp_status pp_csr_info(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals, double *norm1,
+                      double *sigma_sr) {
+    if (n <= 0 || !rowptr || !colind || !vals) return pp_fail(PP_EINVAL, "pp_csr_info: bad arguments");
+    const int64_t nnz = rowptr[n];
+    if (rowptr[0] != 0 || nnz < 0 || nnz >= (int64_t)1 << 31 || n >= (int64_t)1 << 31)
+        return pp_fail(PP_EINVAL, "pp_csr_info: rowptr must start at 0 and nnz, n < 2^31");
+    ppd::CsrScan scan;
+    std::string why;
+    if (!ppd::scan_csr(n, rowptr, colind, vals, scan, why)) return pp_fail(PP_EINVAL, "pp_csr_info: %s", why.c_str());
+    if (norm1) *norm1 = scan.norm1;
+    if (sigma_sr) *sigma_sr = sr_shift(scan.gl, scan.norm1);
     return PP_OK;
 }
 

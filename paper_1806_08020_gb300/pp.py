@@ -59,6 +59,7 @@ _SIGS = {
     "pp_destroy": (None, [_P]),
     "pp_trim": (C.c_int, [_P]),
     "pp_matrix_info": (C.c_int, [_P, _D, _D]),
+    "pp_csr_info": (C.c_int, [C.c_int64, _I64, C.POINTER(C.c_int32), _D, _D, _D]),
     "pp_balance_info": (C.c_int, [_P, _I, _D]),
     "pp_debug_stall_sweeps": (C.c_int, [_P, C.c_int]),
     "pp_format_info": (C.c_int, [_P, _I, _I, _I, _I, _I, _I64]),
@@ -221,6 +222,17 @@ def pp_balance_info(ctx: Context) -> tuple[bool, float]:
     b, r = C.c_int(), C.c_double()
     _check(LIB.pp_balance_info(ctx.handle, C.byref(b), C.byref(r)))
     return bool(b.value), r.value
+
+
+def pp_csr_info(A) -> tuple[float, float]:
+    """(||A||_1, the smallest-real-part shift) of a host CSR matrix, as pp_create computes them."""
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+    va = _f64(A.vals)
+    a, s = C.c_double(), C.c_double()
+    _check(LIB.pp_csr_info(int(A.n), rp.ctypes.data_as(_I64), ci.ctypes.data_as(C.POINTER(C.c_int32)), _dp(va),
+                           C.byref(a), C.byref(s)))
+    return a.value, s.value
 
 
 def pp_matrix_info(ctx: Context) -> tuple[float, float]:
