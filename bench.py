@@ -608,11 +608,13 @@ def _serve_once(pp, reqs, prec, max_cycles, local):
 
 
 def leg_serve(local: int, rank: int, requests: int, max_cycles: int = 300,
-              precisions=("fp32", "fp64")) -> dict:
+              precisions=("fp32", "fp64"), sequential: bool = True) -> dict:
     """The first `requests` requests of the Poisson(50/s) stream of random banded
     eigen-solves (n logU[1e4, 2e6], half-band U{5..25}, nev U{4..32}, d U{10..100},
     k = nev + 5, m = max(30, 2k), smallest real part), submitted at their arrival
-    times to the continuous-batching server; latency from submission to result."""
+    times to the continuous-batching server; latency from submission to result.
+    With `sequential`, also the plain FP64 method on the same requests one after
+    the other (the comparison the served mixed form is to beat)."""
     from paper_1806_08020_gb300 import pp
 
     spec = inputs.request_stream(count=requests)
@@ -647,13 +649,33 @@ def leg_serve(local: int, rank: int, requests: int, max_cycles: int = 300,
                                        "median": float("%.3g" % statistics.median(errs)) if errs else None,
                                        "note": "per request, largest |lam_fp32 - lam_fp64| / |lam_fp64|; both meet "
                                                "residual <= 1e-8 ||A||_1 on A in FP64"}
+    if sequential:
+        # the plain FP64 GPU method (pp_create, pp_build_poly, pp_eigs) on one request after
+        # the other, all available at once (no arrival times): wall clock, as the served arms
+        import torch
+        pairs64, conv64 = 0, 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with ClockSampler(local) as clk:
+            for q, A, b, v in reqs:
+                ctx = pp.pp_create(A, max_cycles=max_cycles)
+                r = pp.pp_eigs(ctx, pp.pp_build_poly(ctx, q["d"], b), q["nev"], q["m"], q["k"], q["rtol"], v,
+                               want_vectors=False)
+                pairs64 += count_pairs(r, q["nev"], q["rtol"])
+                conv64 += r.status == 0
+                ctx.close()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        out["plain_fp64_sequential"] = {"value": round(pairs64 / wall, 3), "unit": UNIT, "seconds": round(wall, 2),
+                                        "eigenpairs": pairs64, "converged": int(conv64), "clocks": clk.summary()}
     return out
 
 
 def run_serve(args, ws, rank, local):
     """The request stream (first --requests requests) on its own line."""
     leg = leg_serve(local, rank, args.requests, args.serve_max_cycles,
-                    precisions=(args.serve_precision,) if args.serve_precision != "both" else ("fp32", "fp64"))
+                    precisions=(args.serve_precision,) if args.serve_precision != "both" else ("fp32", "fp64"),
+                    sequential=args.requests <= 64)
     first = leg["served_" + ("fp32" if args.serve_precision != "fp64" else "fp64")]
     return {"metric": "eigenpairs/s at residual 1e-8 and p50/p99 latency, served request stream",
             "value": first["value"], "unit": UNIT, "n_gpus": ws, "steps": 1, "warmup": 0,
