@@ -397,14 +397,14 @@ class Engine {
     }
 
     // Work items (instance, first 32-row group), `g` warps per block (a warp takes
-    // one 32-row group, two for a DIA instance).
+    // one 32-row group, two for an FP32 DIA instance).
     pp_status upload_items(int g) {
         std::vector<int2> items;
         item_end.assign(act.size(), 0);
         for (int i = 0; i < (int)act.size(); ++i) {
             const int ngroups = (int)((act[i]->c->n + 31) / 32);
-            // a DIA instance's warps take two 32-row groups each (two rows per lane)
-            const int step = act[i]->c->A.fmt == 3 ? 2 * g : g;
+            // an FP32 DIA instance's warps take two 32-row groups each (two rows per lane)
+            const int step = act[i]->c->A.fmt == 3 && act[i]->c->A.prec == ppk::F32 ? 2 * g : g;
             for (int g0 = 0; g0 < ngroups; g0 += step) items.push_back(make_int2(i, g0));
             item_end[i] = (int)items.size();
         }

@@ -725,20 +725,21 @@ __device__ __forceinline__ T batch_out(const BatchOperands<T> &o, T u, T xi, T a
 }
 
 // One polynomial pass for every active instance in one launch.  A work item
-// is g warps' rows of one instance: 32 consecutive rows per warp (SELL), or 64
-// with two consecutive rows per lane (DIA: the lane's two values of a diagonal
-// sit side by side in its 32-row block).  Blocks take chunks of kBatchChunk
-// consecutive work items, strided over the grid (so that the instances that
-// take no pass at a step spread over all blocks).  Consecutive items mostly
-// stay in one instance: its operands, and in FP32 for up to eight diagonals
-// its offsets, are loaded once and kept in registers, and the next item's
-// index is read while this one computes.
+// is g warps' rows of one instance: 32 consecutive rows per warp (SELL, and
+// DIA in FP64), or 64 with two consecutive rows per lane (DIA in FP32: the
+// lane's two values of a diagonal sit side by side in its 32-row block, one
+// 8-byte load).  Blocks take chunks of `chunk` (at
+// most kBatchChunk) consecutive work items, strided over the grid.  Consecutive
+// items mostly stay in one instance: its operands, and in FP32 for up to eight
+// diagonal offsets, are loaded once and kept in registers, and the next
+// item's index is read while this one computes.  The launcher shortens the
+// chunks when there are few items, so that small sets still fill the GPU.
 constexpr int kBatchChunk = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassInst *pi, const BatchPassEntry *tab,
                                                                 const int2 *items, int nitems, const int *lo,
-                                                                const int *hi, int jj) {
+                                                                const int *hi, int jj, int chunk) {
     grid_trigger();
     grid_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -749,8 +750,8 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassI
 #pragma unroll
     for (int t = 0; t < 8; ++t) off[t] = 0;
     BatchOperands<T> o{};
-    for (int c0 = blockIdx.x * kBatchChunk; c0 < nitems; c0 += gridDim.x * kBatchChunk) {
-        const int c1 = min(nitems, c0 + kBatchChunk);
+    for (int c0 = blockIdx.x * chunk; c0 < nitems; c0 += gridDim.x * chunk) {
+        const int c1 = min(nitems, c0 + chunk);
         int2 nxt = items[c0];
         for (int it = c0; it < c1; ++it) {
             const int2 itm = nxt;
@@ -777,21 +778,15 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassI
                 }
             }
             if (o.kind >= 0) {
-                if (dia) {
+                if (dia && sizeof(T) == 4) {
                     const int r0 = (itm.y + 2 * warp) * 32 + 2 * lane;
                     if (r0 + 1 < n) {
                         T u[2], xi[2], ax[2] = {(T)0, (T)0};
-                        if (sizeof(T) == 4 && ndiag <= 8) {
+                        if (ndiag <= 8) {
                             dia_pair8<T>(val + (size_t)(r0 >> 5) * ((size_t)ndiag * 32) + (r0 & 31), n, ndiag, off, o.x,
                                          r0, u);
                         } else {
-                            const DiaView D{n, ndiag, 0, offp, val};
-                            if (sizeof(T) == 4) {
-                                dia_pair<T>(D, o.x, r0, u);
-                            } else {  // FP64: one row at a time keeps the registers of eight diagonals
-                                u[0] = dia_row<T, T, T>(D, offp, o.x, r0);
-                                u[1] = dia_row<T, T, T>(D, offp, o.x, r0 + 1);
-                            }
+                            dia_pair<T>(DiaView{n, ndiag, 0, offp, val}, o.x, r0, u);
                         }
                         ld2<T>(o.x + r0, xi);
                         if (o.kind == 2) ld2<T>(o.aux + r0, ax);
@@ -801,12 +796,16 @@ __global__ void __launch_bounds__(kPassMaxThreads) k_pass_batch(const BatchPassI
                         const T u = dia_row<T, T, T>(D, offp, o.x, r0);
                         o.y[r0] = batch_out<T>(o, u, o.x[r0], o.kind == 2 ? o.aux[r0] : (T)0);
                     }
-                } else {
+                } else {  // one row per lane: SELL, and DIA in FP64 (bound by FP64 arithmetic, not loads)
                     const int row = (itm.y + warp) * 32 + lane;
                     if (row < n) {
-                        const SellView &A = pi[cur].A;
-                        const T u =
-                            A.off ? sell_row<T, T, T, true>(A, o.x, row) : sell_row<T, T, T, false>(A, o.x, row);
+                        T u;
+                        if (dia) {
+                            u = dia_row<T, T, T>(DiaView{n, ndiag, 0, offp, val}, offp, o.x, row);
+                        } else {
+                            const SellView &A = pi[cur].A;
+                            u = A.off ? sell_row<T, T, T, true>(A, o.x, row) : sell_row<T, T, T, false>(A, o.x, row);
+                        }
                         o.y[row] = batch_out<T>(o, u, o.x[row], o.kind == 2 ? o.aux[row] : (T)0);
                     }
                 }
@@ -1037,14 +1036,18 @@ void launch_step(const Matrix &A, const StepArgs &s, cudaStream_t st) {
 void launch_pass_batch(Prec p, const BatchPassInst *pi, const BatchPassEntry *tab, const int2 *items, int nitems,
                        const int *lo, const int *hi, int jj, int groups, int grid_per_sm, cudaStream_t st) {
     int g = num_sms() * grid_per_sm;
-    const int chunks = (nitems + kBatchChunk - 1) / kBatchChunk;
+    // chunks of up to kBatchChunk items, shorter where that leaves fewer than
+    // four blocks per SM
+    int chunk = nitems / (num_sms() * 4);
+    chunk = chunk < 1 ? 1 : (chunk > kBatchChunk ? kBatchChunk : chunk);
+    const int chunks = (nitems + chunk - 1) / chunk;
     if (chunks < g) g = chunks;
     if (g < 1) g = 1;
     const int threads = 32 * groups;
     if (p == F64)
-        launch_dependent(k_pass_batch<double>, g, threads, 0, st, pi, tab, items, nitems, lo, hi, jj);
+        launch_dependent(k_pass_batch<double>, g, threads, 0, st, pi, tab, items, nitems, lo, hi, jj, chunk);
     else
-        launch_dependent(k_pass_batch<float>, g, threads, 0, st, pi, tab, items, nitems, lo, hi, jj);
+        launch_dependent(k_pass_batch<float>, g, threads, 0, st, pi, tab, items, nitems, lo, hi, jj, chunk);
 }
 
 void launch_sell_fill(Prec p, int n, int nslices, int cshift, const int *rowptr, const int *col, const double *val,
