@@ -67,6 +67,58 @@ def test_batch_equals_solo(precision):
                 assert abs(lb - ls) <= 10 * kj * (rsb + rss) * nA + 1e-12 * abs(ls)
 
 
+def _scattered(N, beta, seed, count=120):
+    """A CD operator plus `count` small entries at random positions: more than 64
+    distinct diagonals, so the batched engine stores it in SELL-32, not DIA."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng([seed, 2])
+    A = O.to_scipy(inputs.convection_diffusion_2d(N, beta))
+    n = A.shape[0]
+    E = sp.csr_matrix((rng.standard_normal(count), (rng.integers(0, n, count), rng.integers(0, n, count))),
+                      shape=(n, n))
+    M = (A + E).tocsr()
+    M.sum_duplicates()
+    M.sort_indices()
+    return inputs.CSR(n, M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("layout", ["dia_and_sell", "sell_only"])
+def test_batch_formats_equal_solo(precision, layout):
+    """One batched launch over instances in both layouts of the batched pass (DIA:
+    FP32 two rows per lane, FP64 one; SELL-32: one row per lane), odd and even n,
+    different degrees (so the pass launches cover different prefixes of the set);
+    or every instance forced to SELL-32.  Each result against the solo solve."""
+    from paper_1806_08020_gb300 import pp
+    prec = pp.PP_FP64 if precision == "fp64" else pp.PP_FP32
+    inst = [(inputs.convection_diffusion_2d(21, 12.0), 11, 301), (_scattered(23, 8.0, 5), 6, 302),
+            (inputs.convection_diffusion_2d(32, 20.0), 4, 303), (_scattered(17, 15.0, 6), 13, 304)]
+    nev, m, k = 5, 24, 10
+    opts = dict(precision=prec)
+    if layout == "sell_only":
+        opts["format"] = pp.PP_FMT_SELL
+    B = pp.pp_batch_create([A for A, _, _ in inst], **opts)
+    bs = [inputs.start_vector(A.n, s, 0) for A, _, s in inst]
+    vs = [inputs.start_vector(A.n, s, 1) for A, _, s in inst]
+    status, res = pp.pp_batch_solve(B, [d for _, d, _ in inst], bs, vs, nev, m, k, 1e-8)
+    assert status == 0
+    for (A, d, s), rb, b, v in zip(inst, res, bs, vs):
+        ctx = pp.pp_create(A, precision=prec)
+        solo = pp.pp_eigs(ctx, pp.pp_build_poly(ctx, d, b), nev, m, k, 1e-8, v)
+        assert rb.status == 0 and solo.status == 0
+        rc = cpu_residuals(O.to_scipy(A), rb.lam, rb.X)
+        assert np.all(rc <= 1.01e-8)
+        assert rb.lam.size == solo.lam.size
+        if precision == "fp64":
+            assert np.max(np.abs(rb.lam - solo.lam) / np.abs(solo.lam)) <= 1e-10
+        else:
+            w, kap = eig_condition(A.to_dense())
+            nA = O.norm1(O.to_scipy(A))
+            for lb, ls, rsb, rss in zip(rb.lam, solo.lam, rb.resid, solo.resid):
+                kj = kap[np.argmin(np.abs(w - ls))]
+                assert abs(lb - ls) <= 10 * kj * (rsb + rss) * nA + 1e-12 * abs(ls)
+
+
 def test_batch_matches_oracle():
     from paper_1806_08020_gb300 import pp
     inst = _instances(4, seed=5)
