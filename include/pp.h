@@ -317,7 +317,9 @@ pp_status pp_apply_host(const pp_poly *p, const double *x, double *y);
  * the Ritz vectors are refined in FP64 (Rayleigh-Ritz of A on span{pi(A) Y},
  * pi applied in FP64 by the context's FP64 copy; from the second round the
  * cycle's next Ritz vectors join Y); if that does not reach rtol the solve
- * continues in FP64 from the refined vectors.
+ * continues in FP64 from the refined vectors.  PP_FP32_BF16 contexts do the
+ * same with a BF16 basis and continue with an FP32 basis (which refines and
+ * continues in FP64 in turn).
  * Requires 1 <= nev < k < m, m < n.  Returns PP_ENOTCONV with the best pairs
  * when max_cycles is reached.
  */

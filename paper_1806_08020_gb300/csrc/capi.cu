@@ -578,8 +578,7 @@ void pp_opts_default(pp_opts *o) {
 
 pp_status pp_trim(pp_ctx *c) {
     if (!c) return pp_fail(PP_EINVAL, "pp_trim: null context");
-    ws_trim(c);
-    if (c->twin) ws_trim(c->twin);
+    for (pp_ctx *t = c; t; t = t->twin) ws_trim(t);
     return PP_OK;
 }
 
@@ -1084,10 +1083,13 @@ pp_status pp_create_internal(pp_ctx **out, int64_t n, const int64_t *rowptr, con
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(pp_fail(PP_ECUDA, "pp_create: setup kernels failed"));
     dfree(c, d_rp64);
     if (c->bprec != ppk::F64 && make_twin) {
-        // FP64 twin on the same stream: the mixed-precision solve continues in FP64
-        // when the FP32 cycles cannot resolve the eigenvectors (u_32 kappa ~ 1)
+        // twin on the same stream, one precision up: the mixed-precision solve
+        // continues there when its cycles cannot resolve the eigenvectors
+        // (u kappa ~ 1).  FP32 contexts get an FP64 twin; BF16-basis contexts an
+        // FP32 one, which has its own FP64 twin (a BF16 basis stalls near 1e-3,
+        // an FP32 one near 1e-7, where the FP64 refinement takes over)
         pp_opts o = c->opts;
-        o.precision = PP_FP64;
+        o.precision = c->bprec == ppk::BF16 ? PP_FP32 : PP_FP64;
         o.sigma = c->sigma;
         o.stream = c->stream;
         if ((st = pp_create(&c->twin, n, rowptr, colind, vals, &o)) < 0) return fail(st);

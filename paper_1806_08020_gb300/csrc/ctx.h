@@ -89,7 +89,9 @@ struct pp_ctx {
     unsigned *d_ticket = nullptr;
     double *d_small = nullptr;  // h1, h2, scal, misc (4 * 256 doubles)
     int64_t launches = 0;
-    pp_ctx *twin = nullptr;  // FP64 copy of an FP32 context (mixed-precision fallback)
+    // the next precision up for the mixed-precision fallback: the FP64 copy of an
+    // FP32 context, the FP32 copy (with its own FP64 twin) of a BF16-basis one
+    pp_ctx *twin = nullptr;
     int64_t stored = 0;      // matrix entries held on the device (with SELL padding)
     int stall_sweeps = 0;    // test hook: staged CGS2 sweeps left to run without copies
     // per-call device workspace (bases, test buffers) kept for the next call:
@@ -126,6 +128,17 @@ struct Timers {
     ~Timers();
 };
 
+// The FP64 context of c's twin chain (c itself when FP64; null without one).
+inline pp_ctx *fp64_context(pp_ctx *c) {
+    while (c && c->bprec != ppk::F64) c = c->twin;
+    return c;
+}
+// Kernel launches of c and its twins.
+inline int64_t chain_launches(const pp_ctx *c) {
+    int64_t l = 0;
+    for (; c; c = c->twin) l += c->launches;
+    return l;
+}
 pp_status dmalloc(pp_ctx *c, void **p, size_t bytes);
 void dfree(pp_ctx *c, void *p);
 // Workspace of one call: a spare block of the context that fits (at most a

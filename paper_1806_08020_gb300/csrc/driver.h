@@ -220,7 +220,7 @@ struct Driver {
         if (!Z) CKS(alloc((void **)&Z, (size_t)ldv * (kZcap + 1) * 8));
         if (!dG) CKS(alloc((void **)&dG, (size_t)(kZcap + 1) * kZcap * 8));
         if (!Yb) CKS(alloc((void **)&Yb, (size_t)ldv * (wcap + 1) * 8));
-        pp_ctx *tw = (p && c->twin) ? c->twin : nullptr;
+        pp_ctx *tw = p ? fp64_context(c->twin) : nullptr;
         // the filter: pi itself, or for a double polynomial its inner factor pi_1
         // (degree d1 instead of d1 d2: it damps the same unwanted part, less
         // sharply, at a d2-th of the FP64 passes)

@@ -11,13 +11,14 @@
 // Mixed precision (context precision PP_FP32): the Arnoldi cycles run with
 // FP32 matrix values, vectors and basis.  Within 50 rtol, or when the FP64
 // residuals reach the FP32 floor, the wanted Ritz vectors are refined in FP64
-// on A (Driver::refine): pi(A) applied in FP64 by the context's FP64 twin to
+// on A (Driver::refine): pi(A) applied in FP64 by the FP64 context of the twins to
 // them (and, from the second round, to the cycle's next Ritz vectors), FP64
 // CGS2, A projected onto that space (Rayleigh-Ritz), the refined pairs ranked
 // as the Arnoldi ranks its Ritz values.  When that does not reach rtol (the
 // FP32 Krylov space does not hold the eigenvectors well enough), the solve
-// continues with FP64 cycles on the twin, started from the sum of the refined
-// Ritz vectors.
+// continues on the twin, started from the sum of the refined Ritz vectors:
+// FP64 cycles for an FP32 context; for a BF16 basis (PP_FP32_BF16) FP32-basis
+// cycles, which refine and continue in turn.
 #include "driver.h"
 
 using namespace ppi;
@@ -34,7 +35,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
     const bool mixed = bpr != ppk::F64;
     const double target = p ? 1.0 : 0.0;
     pp_stats S{};
-    const int64_t launches0 = c->launches, twin0 = c->twin ? c->twin->launches : 0;
+    const int64_t launches0 = chain_launches(c);
     Driver D{c, n, ldv, nev + 1};
     void *V = nullptr, *V2 = nullptr, *W = (p && p->inner) ? c->vec[0] : c->vec[6];
     double *dH = nullptr;
@@ -88,6 +89,39 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
             S.t_restart += now() - th0;
             break;
         }
+        // continue on the twin (one precision up) from `start` (host or device
+        // vector, NULL: all ones), the cycle count carried on
+        auto continue_on_twin = [&](const double *start) -> pp_status {
+            const double t_here = now() - th0;  // this cycle's test and refinement
+            pp_ctx *tw = c->twin;
+            const int max_c = tw->opts.max_cycles;
+            tw->opts.max_cycles = (int)std::max<int64_t>(1, c->opts.max_cycles - cycle);
+            pp_stats S2{};
+            pp_status st2 = pp_eigs(tw, p, nev, m, k, rtol, start, lam_re, lam_im, X, resid, nout, &S2);
+            tw->opts.max_cycles = max_c;
+            if (st2 < 0) return st2;
+            if (tw->bprec == ppk::F64) S2.fp64_cycles = S2.cycles;  // else as the twin counted them
+            S2.cycles += S.cycles;
+            S2.mvps += S.mvps;
+            S2.dots += S.dots;
+            S2.vops += S.vops;
+            S2.t_apply += S.t_apply;
+            S2.t_orth += S.t_orth;
+            S2.t_restart += S.t_restart + t_here;
+            S2.kernel_launches = chain_launches(c) - launches0;
+            S2.t_total = now() - t_start;
+            if (stats) *stats = S2;
+            return st2;
+        };
+        if (bpr == ppk::BF16 && c->twin && cycle < c->opts.max_cycles &&
+            *std::max_element(R.res.begin(), R.res.end()) > 10 * rtol) {
+            // A BF16 basis stalls near 1e-3 (its unit roundoff), out of the
+            // refinement's reach, and a start from its Ritz vectors served the
+            // FP32 cycles worse than the original one (measured on the 3-D
+            // workload): after one cycle the solve restarts on the FP32 twin from
+            // the start vector.
+            return continue_on_twin(v0);
+        }
         if (mixed && sw.should_refine(R, cycle == c->opts.max_cycles)) {
             CKS(D.refine(p, cy.sl, nev, R, rtol, c->opts.refine_steps, 3, S, &cy, V, bpr, m));
             S.nconv = R.nconv;
@@ -98,36 +132,19 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
                 break;
             }
             if (c->twin) {
-                // The FP32 Krylov space does not hold the eigenvectors to rtol (the
-                // problem is too non-normal for FP32): continue in FP64 on the same
-                // polynomial, started from the sum of the refined Ritz vectors.
+                // The Krylov space does not hold the eigenvectors to rtol (the problem
+                // is too non-normal for the basis precision): continue on the twin,
+                // one precision up, with the same polynomial, started from the sum of
+                // the refined Ritz vectors.
                 std::vector<double> Yh, w0(n, 0.0);
                 CKS(download_vecs(c, D.Y64, ldv, cy.sl.nw, Yh, ppk::F64));
                 for (int s = 0; s < cy.sl.nw; ++s)
                     for (int64_t i = 0; i < n; ++i) w0[i] += Yh[(size_t)s * n + i];
                 if (!c->h_bal.empty())  // the twin's Krylov space is in S's coordinates (y = D^-1 x)
                     for (int64_t i = 0; i < n; ++i) w0[i] /= c->h_bal[i];
-                pp_ctx *tw = c->twin;
-                const int max_c = tw->opts.max_cycles;
-                tw->opts.max_cycles = (int)std::max<int64_t>(1, c->opts.max_cycles - cycle);
-                pp_stats S2{};
-                pp_status st2 = pp_eigs(tw, p, nev, m, k, rtol, w0.data(), lam_re, lam_im, X, resid, nout, &S2);
-                tw->opts.max_cycles = max_c;
-                if (st2 < 0) return st2;
-                S2.fp64_cycles = S2.cycles;
-                S2.cycles += S.cycles;
-                S2.mvps += S.mvps;
-                S2.dots += S.dots;
-                S2.vops += S.vops;
-                S2.t_apply += S.t_apply;
-                S2.t_orth += S.t_orth;
-                S2.t_restart += S.t_restart + (now() - th0);
-                S2.kernel_launches = (c->launches - launches0) + (tw->launches - twin0);
-                S2.t_total = now() - t_start;
-                if (stats) *stats = S2;
-                return st2;
+                return continue_on_twin(w0.data());
             }
-            sw.reset();  // no FP64 twin: keep cycling in FP32 (restart below)
+            sw.reset();  // no twin: keep cycling in this precision (restart below)
         }
         if (cycle == c->opts.max_cycles) {
             S.t_restart += now() - th0;
@@ -161,7 +178,7 @@ extern "C" pp_status pp_eigs(pp_ctx *c, const pp_poly *p, int nev, int m, int k,
     S.converged = converged ? 1 : 0;
     S.max_resid = maxres;
     S.fp64_cycles = mixed ? 0 : S.cycles;
-    S.kernel_launches = (c->launches - launches0) + (c->twin ? c->twin->launches - twin0 : 0);
+    S.kernel_launches = chain_launches(c) - launches0;
     S.t_total = now() - t_start;
     if (stats) *stats = S;
     if (!converged) return pp_fail(PP_ENOTCONV, "pp_eigs: not converged in %lld cycles", (long long)S.cycles);
