@@ -12,6 +12,9 @@
 // of requests does not change, each step is replayed from a CUDA graph
 // captured once.  The per-cycle host work (Ritz values, FP64 convergence test
 // on A, refinement, thick restart) is the single-instance code of driver.h.
+// Mixed precision: each FP32 request runs one FP32 cycle as a warm start; one
+// still more than 10 rtol from converging then moves to a second engine of
+// FP64 twins, nearer ones are refined in FP64 first.
 //
 // pp_batch_* solves a fixed set to completion; pp_server_* admits requests as
 // device memory and slots free up (continuous batching) and retires each as
@@ -197,10 +200,10 @@ class Engine {
         return begin(r, v0);
     }
 
-    // A request whose FP32 cycles and refinement could not reach rtol joins
-    // the FP64 engine: the FP32 basis is released and FP64 Arnoldi cycles on
-    // the FP64 twin start from the sum of the refined Ritz vectors (the same
-    // polynomial; the cycle count continues).
+    // A request whose FP32 cycle (and refinement, when it was near rtol) did
+    // not reach rtol joins the FP64 engine: the FP32 basis is released and
+    // FP64 Arnoldi cycles on the FP64 twin start from the sum of its Ritz
+    // vectors (the same polynomial; the cycle count continues).
     pp_status start64(Req *r) {
         pp_ctx *c = r->c;
         std::vector<double> Yh, w0(c->n, 0.0);
