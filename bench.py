@@ -256,16 +256,24 @@ def run_ours(args, ws, rank, local):
     t, pairs = merge_over_ranks(t, pairs, dev)
     value = pairs / t
 
-    # end to end through the C-ABI from host buffers: upload, solve, vectors back
+    # end to end through the C-ABI from host buffers: upload, solve, vectors back.  The
+    # inputs and the vector buffer are pinned host memory, allocated before the timed region
     e2e_steps = max(1, min(args.steps, 3))
+
+    def _pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    Ah = inputs.CSR(A.n, _pinned(A.rowptr), _pinned(A.colind), _pinned(A.vals))
+    bh, v0h = _pinned(b), _pinned(v0)
+    Xh = torch.empty((cfg["nev"] + 1, n), dtype=torch.float64).pin_memory().numpy()
     barrier()
     h2d = A.rowptr.nbytes + A.colind.nbytes + A.vals.nbytes + b.nbytes + v0.nbytes
     te0 = time.perf_counter()
     e2e_pairs, d2h = 0, 0
     for _ in range(e2e_steps):
-        c2 = pp.pp_create(A, stream=stream.cuda_stream)
-        p2 = pp.pp_build_poly(c2, cfg["d"], b)
-        r2 = pp.pp_eigs(c2, p2, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0, want_vectors=True)
+        c2 = pp.pp_create(Ah, stream=stream.cuda_stream)
+        p2 = pp.pp_build_poly(c2, cfg["d"], bh)
+        r2 = pp.pp_eigs(c2, p2, cfg["nev"], cfg["m"], cfg["k"], cfg["rtol"], v0h, want_vectors=True, X_out=Xh)
         d2h = r2.X.nbytes + r2.lam.nbytes * 2 + r2.resid.nbytes
         e2e_pairs += count_pairs(r2, cfg["nev"], cfg["rtol"])
         p2.close()

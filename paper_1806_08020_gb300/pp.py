@@ -384,11 +384,18 @@ class EigsResult:
 
 
 def pp_eigs(ctx: Context, p: Poly | None, nev: int, m: int, k: int, rtol: float, v0=None,
-            want_vectors: bool = True) -> EigsResult:
+            want_vectors: bool = True, X_out: np.ndarray | None = None) -> EigsResult:
+    """X_out: optional float64 C-contiguous (nev+1, n) host array the vectors are written
+    into (e.g. pinned memory reused across calls); the result's X is a view of it."""
     n = ctx.n
     cap = nev + 1
     lre, lim, res = np.zeros(cap), np.zeros(cap), np.zeros(cap)
-    X = np.empty((cap, n)) if want_vectors else None  # slot-major: the library writes column s at X[s]
+    if X_out is not None:
+        if X_out.dtype != np.float64 or X_out.shape != (cap, n) or not X_out.flags.c_contiguous:
+            raise ValueError("X_out must be a C-contiguous float64 array of shape (nev + 1, n)")
+        X = X_out
+    else:
+        X = np.empty((cap, n)) if want_vectors else None  # slot-major: the library writes column s at X[s]
     v0a, v0p = _vec_in(v0, n) if v0 is not None else (None, None)
     nout = C.c_int()
     st = pp_stats()
