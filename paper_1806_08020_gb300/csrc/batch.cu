@@ -269,7 +269,10 @@ class Engine {
     pp_status cycle() {
         if (act.empty()) return PP_OK;
         const bool changed = dirty;
+        const bool tr = trace_on();
+        const double t0 = tr ? now() : 0.0;
         if (dirty) CKS(build_tables());
+        const double t1 = tr ? now() : 0.0;
         const int count = (int)act.size();
         int jmin = 1 << 30, jmax = 0;
         std::vector<int> lo(count), hi(count);
@@ -302,7 +305,15 @@ class Engine {
             launches += Pmax + 4;
         }
         CK(cudaGetLastError());
+        double t2 = 0.0;
+        if (tr) {  // (trace only: the wait separates the steps' device time from the host steps)
+            CK(cudaStreamSynchronize(st));
+            t2 = now();
+        }
         for (int i = 0; i < count; ++i) CKS(host_step(i));
+        if (tr)
+            std::fprintf(stderr, "[pp] engine cycle: %d requests, steps %d..%d, tables %.1f ms, steps %.1f ms, host steps %.1f ms\n",
+                         count, jmin, jmax, (t1 - t0) * 1e3, (t2 - t1) * 1e3, (now() - t2) * 1e3);
         return PP_OK;
     }
 
