@@ -95,8 +95,8 @@ class Operator:
 def cgs2(V: np.ndarray, w: np.ndarray, c: Counters) -> tuple[np.ndarray, np.ndarray]:
     """Classical Gram-Schmidt of w against the orthonormal columns of V, done twice.
 
-    Section 4: "each orthogonalization step is followed by a pass of
-    reorthogonalization".  Returns (w orthogonalised, h = h1 + h2).
+    Section 4 runs one reorthogonalisation pass after every orthogonalisation
+    step.  Returns (w orthogonalised, h = h1 + h2).
     """
     j = V.shape[1]
     h1 = V.T @ w
