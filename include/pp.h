@@ -192,6 +192,20 @@ pp_status pp_csr_info(int64_t n, const int64_t *rowptr, const int32_t *colind, c
                       double *sigma_sr);
 
 /*
+ * pp_csr_balance — the balancing pp_create applies with pp_opts.balance, on
+ * the host and without a device (not in the paper: an opt-in problem
+ * transformation).  d (host, n doubles, caller-owned) receives the diagonal
+ * D of the similarity S = D^-1 A D that makes A symmetric (d_j / d_i =
+ * sqrt(a_ji / a_ij) on every off-diagonal pair, largest entry 1);
+ * *log_range (may be NULL) receives -min_i log d_i.  PP_EINVAL with a reason
+ * for the inputs pp_create refuses and when no such D exists (a pair of
+ * entries not nonzero together or of opposite signs, ratios that do not
+ * multiply to 1 around a cycle, a range beyond e^600); d is then unspecified.
+ */
+pp_status pp_csr_balance(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals, double *d,
+                         double *log_range);
+
+/*
  * pp_format_info — the device format of A chosen at pp_create: fmt
  * (PP_FMT_CSR, PP_FMT_SELL or PP_FMT_DIA), the SELL chunk height (0 otherwise),
  * the column index width in bits (16 or 32; 0 for DIA), the block size of the product kernels, the

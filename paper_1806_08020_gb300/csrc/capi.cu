@@ -1160,6 +1160,27 @@ pp_status pp_balance_info(const pp_ctx *c, int *balanced, double *log_range) {
     return PP_OK;
 }
 
+pp_status pp_csr_balance(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals, double *d,
+                         double *log_range) {
+    if (n <= 0 || !rowptr || !colind || !vals || !d) return pp_fail(PP_EINVAL, "pp_csr_balance: bad arguments");
+    const int64_t nnz = rowptr[n];
+    if (rowptr[0] != 0 || nnz < 0 || nnz >= (int64_t)1 << 31 || n >= (int64_t)1 << 31)
+        return pp_fail(PP_EINVAL, "pp_csr_balance: rowptr must start at 0 and nnz, n < 2^31");
+    ppd::CsrScan scan;  // the same validation as pp_create
+    std::string why;
+    if (!ppd::scan_csr(n, rowptr, colind, vals, scan, why)) return pp_fail(PP_EINVAL, "pp_csr_balance: %s", why.c_str());
+    std::vector<double> logd;
+    if (!ppd::symmetrizing_scale(n, rowptr, colind, vals, logd, why))
+        return pp_fail(PP_EINVAL, "pp_csr_balance: %s", why.c_str());
+    double lo = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        d[i] = std::exp(logd[i]);
+        lo = std::min(lo, logd[i]);
+    }
+    if (log_range) *log_range = -lo;
+    return PP_OK;
+}
+
 pp_status pp_csr_info(int64_t n, const int64_t *rowptr, const int32_t *colind, const double *vals, double *norm1,
                       double *sigma_sr) {
     if (n <= 0 || !rowptr || !colind || !vals) return pp_fail(PP_EINVAL, "pp_csr_info: bad arguments");

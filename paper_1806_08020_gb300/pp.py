@@ -60,6 +60,7 @@ _SIGS = {
     "pp_trim": (C.c_int, [_P]),
     "pp_matrix_info": (C.c_int, [_P, _D, _D]),
     "pp_csr_info": (C.c_int, [C.c_int64, _I64, C.POINTER(C.c_int32), _D, _D, _D]),
+    "pp_csr_balance": (C.c_int, [C.c_int64, _I64, C.POINTER(C.c_int32), _D, _D, _D]),
     "pp_balance_info": (C.c_int, [_P, _I, _D]),
     "pp_debug_stall_sweeps": (C.c_int, [_P, C.c_int]),
     "pp_format_info": (C.c_int, [_P, _I, _I, _I, _I, _I, _I64]),
@@ -233,6 +234,19 @@ def pp_csr_info(A) -> tuple[float, float]:
     _check(LIB.pp_csr_info(int(A.n), rp.ctypes.data_as(_I64), ci.ctypes.data_as(C.POINTER(C.c_int32)), _dp(va),
                            C.byref(a), C.byref(s)))
     return a.value, s.value
+
+
+def pp_csr_balance(A) -> tuple[np.ndarray, float]:
+    """(d, log range) of the symmetrising diagonal similarity of a host CSR matrix, as
+    pp_create(balance=1) computes it; PPError (PP_EINVAL) when none exists."""
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+    va = _f64(A.vals)
+    d = np.empty(int(A.n))
+    r = C.c_double()
+    _check(LIB.pp_csr_balance(int(A.n), rp.ctypes.data_as(_I64), ci.ctypes.data_as(C.POINTER(C.c_int32)), _dp(va),
+                              _dp(d), C.byref(r)))
+    return d, r.value
 
 
 def pp_matrix_info(ctx: Context) -> tuple[float, float]:

@@ -104,3 +104,37 @@ def test_refusals():
         rp = A.rowptr.copy()
         rp[0] = 1
         _refused(inputs.CSR(A.n, rp, A.colind, A.vals))
+
+
+# ---- the balancing of pp_create (pp_opts.balance) on the host: pp_csr_balance ----
+
+@pytest.mark.parametrize("N,beta", [(10, 15.0), (50, 20.0), (300, 60.0)])
+def test_balance_closed_form_and_oracle(N, beta):
+    """log d = (x index - (N - 1)) log rho with rho = sqrt((1 + P)/(1 - P)), P = beta h / 2
+    (the closed form the oracle is pinned to), and the oracle's d to rounding; N = 300 has
+    448,800 entries (the threaded scan in front of it)."""
+    A = inputs.convection_diffusion_2d(N, beta)
+    d, rng = pp.pp_csr_balance(A)
+    h = 1.0 / (N + 1)
+    P = beta * h / 2
+    lrho = 0.5 * np.log((1 + P) / (1 - P))
+    ix = np.arange(N * N) % N
+    assert np.allclose(np.log(d), (ix - (N - 1)) * lrho, rtol=0, atol=1e-11 * N)
+    assert d.max() == 1.0
+    assert rng == pytest.approx((N - 1) * lrho, rel=1e-10)
+    if N <= 50:
+        dd, _ = O.balance(O.to_scipy(A))
+        assert np.allclose(d, dd, rtol=1e-12, atol=0)
+
+
+def test_balance_path_and_refusals():
+    # a path (no cycle) is always balanced: d = (1, sqrt 2, sqrt 2) up to scale (as the oracle's pin)
+    P = _csr(np.array([[2.0, 1.0, 0.0], [2.0, 2.0, 3.0], [0.0, 3.0, 2.0]]))
+    d, _ = pp.pp_csr_balance(P)
+    assert np.allclose(d / d[0], [1.0, np.sqrt(2.0), np.sqrt(2.0)])
+    # ratios around 0 -> 1 -> 2 -> 0 that do not multiply to 1; opposite signs (P = beta h / 2 > 1)
+    for A in (_csr(np.array([[2.0, 1.0, 2.0], [1.0, 2.0, 1.0], [1.0, 1.0, 2.0]])),
+              inputs.convection_diffusion_2d(10, 30.0)):
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_csr_balance(A)
+        assert e.value.status == pp.PP_EINVAL
