@@ -82,6 +82,7 @@ def test_balanced_matches_oracle_and_closed_form(N, beta, precision):
     h = 1.0 / (N + 1)
     assert balanced and rng == pytest.approx((N - 1) * 0.5 * np.log((1 + beta * h / 2) / (1 - beta * h / 2)),
                                              rel=1e-10)
+    assert rng == pp.pp_csr_balance(Acsr)[1]  # the context's D is the host call's
     A, R = oracle_balanced(Acsr, 10, nev, m, k, 20181806)
     assert res.status == pp.PP_OK and R.converged
     assert res.lam.size == R.lam.size
